@@ -1,0 +1,437 @@
+"""FP64 CPU oracle for the Kryging hot path (Majumder, Guan, Reich & Saibaba, arXiv 2012.13133).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or links
+this module: only the test suite, the package smoke check and the benchmark's
+CPU-baseline leg may use it.  It shares no code with the CUDA library; the two
+meet only through the seeded inputs of ``paper_2012_13133_gb300.inputs``.
+
+Everything here is plain, slow and FP64: dense covariance matrices and Cholesky
+where sizes allow, explicit DFT matrices on tiny grids, and library FFTs
+(scipy.fft) as a single step where sizes do not.  Each function names the
+passage of the paper it follows.
+
+Readings taken where the paper is silent (each one is listed in the design
+notes of the repository):
+  * grid cells are centred at ((i + 1/2)/n1, (j + 1/2)/n2) on the unit square;
+  * the circulant embedding has size M_d = next power of two >= 2 n_d (the paper
+    uses 2 n_d - 1), lags wrap to their minimal image and a lag of exactly M_d/2
+    averages the two images;
+  * the likelihood is the marginal Gaussian log-likelihood of the observed
+    cells with beta profiled by GLS (the paper's exact profile likelihood,
+    Eq. exact_plik, differs from it by 1/2 log det Gamma^{-1} plus a constant);
+  * the log-determinant is the stochastic Lanczos quadrature estimate (the
+    stochastic trace alternative of Sec. 3.3) with Rademacher probes drawn from
+    splitmix64 counters;
+  * the kriging variance is the simple-kriging variance (the quantity the
+    bootstrap of Sec. 3.5, Eq. bootstrap_uq, estimates).
+
+Parity of the paper's own tables is unpinned: they are replicate averages of
+unpublished random data and fix no value of this path.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+import scipy.special
+
+_WORKERS = max(1, int(os.environ.get("KRY_ORACLE_THREADS", os.cpu_count() or 1)))
+
+# --------------------------------------------------------------------------------------
+# Covariance model (Sec. 2, Matern correlation with sigma^2 outside; anisotropy per Sec. 2)
+# --------------------------------------------------------------------------------------
+
+
+def matern_bessel(r, nu):
+    """Matern correlation from its Bessel-K definition (Sec. 2):
+    2^(1-nu)/Gamma(nu) * (sqrt(2 nu) r)^nu * K_nu(sqrt(2 nu) r), r = d / range; 1 at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    x = math.sqrt(2.0 * nu) * r
+    out = np.ones_like(x)
+    pos = x > 0
+    xp = x[pos]
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        val = (2.0 ** (1.0 - nu) / scipy.special.gamma(nu)) * xp ** nu * scipy.special.kv(nu, xp)
+    val = np.where(np.isfinite(val), val, 0.0)
+    out[pos] = val
+    return out
+
+
+def matern(r, nu):
+    """Matern correlation; closed forms for nu = 1/2, 3/2, 5/2 (the half-integer
+    Bessel functions are elementary), the Bessel form otherwise."""
+    r = np.asarray(r, dtype=np.float64)
+    x = math.sqrt(2.0 * nu) * r
+    if nu == 0.5:
+        return np.exp(-x)
+    if nu == 1.5:
+        return (1.0 + x) * np.exp(-x)
+    if nu == 2.5:
+        return (1.0 + x + x * x / 3.0) * np.exp(-x)
+    return matern_bessel(r, nu)
+
+
+def scaled_distance(h1, h2, cov):
+    """d / range for lag (h1, h2): rotate by the anisotropy angle, stretch the
+    minor axis by the axis ratio (ratio 1 = Euclidean distance over range)."""
+    h1 = np.asarray(h1, dtype=np.float64)
+    h2 = np.asarray(h2, dtype=np.float64)
+    ca, sa = math.cos(cov.angle), math.sin(cov.angle)
+    u = ca * h1 + sa * h2
+    v = -sa * h1 + ca * h2
+    return np.sqrt(u * u + (cov.ratio * v) ** 2) / cov.range
+
+
+def covariance(h1, h2, cov):
+    """sigma^2 * rho(d) for lag (h1, h2), no nugget."""
+    return cov.sigma2 * matern(scaled_distance(h1, h2, cov), cov.nu)
+
+
+# --------------------------------------------------------------------------------------
+# Dense forms (model Eq. obs_mod with A = row selection; covariance of Sec. 2)
+# --------------------------------------------------------------------------------------
+
+
+def coords(n1, n2):
+    s1 = (np.arange(n1) + 0.5) / n1
+    s2 = (np.arange(n2) + 0.5) / n2
+    S1, S2 = np.meshgrid(s1, s2, indexing="ij")
+    return S1, S2
+
+
+def dense_sigma(sa, sb, cov):
+    """sigma^2 Sigma between site sets sa (m,2) and sb (k,2), no nugget."""
+    h1 = sa[:, None, 0] - sb[None, :, 0]
+    h2 = sa[:, None, 1] - sb[None, :, 1]
+    return covariance(h1, h2, cov)
+
+
+def observed_sites(n1, n2, mask):
+    S1, S2 = coords(n1, n2)
+    return np.stack([S1[mask], S2[mask]], axis=1)
+
+
+def dense_K(n1, n2, mask, cov):
+    """Marginal covariance of the observed cells, K = sigma^2 A Sigma A^T + tau^2 I (Eq. obs_mod)."""
+    s = observed_sites(n1, n2, mask)
+    K = dense_sigma(s, s, cov)
+    K[np.diag_indices_from(K)] += cov.tau2
+    return K
+
+
+# --------------------------------------------------------------------------------------
+# Circulant embedding of the BTTB covariance (Sec. 3, Sec. 3.3, Appendix A Eq. circ_diag)
+# --------------------------------------------------------------------------------------
+
+
+def embed_size(n):
+    """Smallest power of two >= 2 n."""
+    M = 1
+    while M < 2 * n:
+        M *= 2
+    return M
+
+
+def lag_covariance(n1, n2, M1, M2, cov):
+    """First row c of the block-circulant embedding on the M1 x M2 torus:
+    c[j1, j2] = sigma^2 rho(l1/n1, l2/n2) with l the minimal image of j
+    (j - M when j > M/2); at j = M/2 the two images +-M/2 are averaged."""
+    def images(M):
+        j = np.arange(M)
+        a = np.where(2 * j <= M, j, j - M)        # image with j = M/2 -> +M/2
+        b = np.where(2 * j < M, j, j - M)         # image with j = M/2 -> -M/2
+        return a.astype(np.float64), b.astype(np.float64)
+    a1, b1 = images(M1)
+    a2, b2 = images(M2)
+    dx1, dx2 = 1.0 / n1, 1.0 / n2
+    c = np.zeros((M1, M2))
+    for l1 in (a1, b1):
+        for l2 in (a2, b2):
+            c += covariance(l1[:, None] * dx1, l2[None, :] * dx2, cov)
+    return 0.25 * c
+
+
+def embedding_eigs(c):
+    """Eigenvalues of the block-circulant embedding: the 2-D DFT of its first row (Eq. circ_diag)."""
+    lam = scipy.fft.fft2(c, workers=_WORKERS)
+    return lam.real, float(np.max(np.abs(lam.imag)))
+
+
+def dft_matrix(M):
+    j = np.arange(M)
+    return np.exp(-2j * np.pi * np.outer(j, j) / M)
+
+
+def bttb_matvec_dft(n1, n2, M1, M2, lam, mask, v, tau2):
+    """K v by the circulant embedding with explicit DFT matrices (tiny grids only):
+    scatter A^T v onto the M1 x M2 torus, DFT, multiply by the eigenvalues,
+    inverse DFT, keep the grid, gather A, add the nugget."""
+    F1, F2 = dft_matrix(M1), dft_matrix(M2)
+    g = np.zeros((M1, M2))
+    sub = np.zeros((n1, n2))
+    sub[mask] = v
+    g[:n1, :n2] = sub
+    G = F1 @ g @ F2.T
+    r = (np.conj(F1) @ (lam * G) @ np.conj(F2).T) / (M1 * M2)
+    return r.real[:n1, :n2][mask] + tau2 * v
+
+
+def sigma_conv_fft(n1, n2, M1, M2, lam, grid_vals):
+    """(sigma^2 Sigma g) on the n1 x n2 grid for a grid vector g (batch in the leading axes), by FFT."""
+    g = np.asarray(grid_vals)
+    pad = np.zeros(g.shape[:-2] + (M1, M2))
+    pad[..., :n1, :n2] = g
+    out = scipy.fft.ifft2(lam * scipy.fft.fft2(pad, workers=_WORKERS), workers=_WORKERS)
+    return out.real[..., :n1, :n2]
+
+
+def bttb_matvec_fft(n1, n2, M1, M2, lam, mask, v, tau2):
+    """K v for v of shape (p,) or (nvec, p), by FFT (library FFT as one step)."""
+    v = np.asarray(v, dtype=np.float64)
+    squeeze = v.ndim == 1
+    V = v[None] if squeeze else v
+    g = np.zeros((V.shape[0], n1, n2))
+    g[:, mask] = V
+    out = sigma_conv_fft(n1, n2, M1, M2, lam, g)[:, mask] + tau2 * V
+    return out[0] if squeeze else out
+
+
+# --------------------------------------------------------------------------------------
+# Rademacher probes from splitmix64 counters (Steele, Lea & Flood 2014)
+# --------------------------------------------------------------------------------------
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(x):
+    """splitmix64 output function applied to state x (state advanced by the golden gamma first)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(x, dtype=np.uint64) + _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def rademacher_probe(seed, k, p):
+    """z_k[i] = +1 if bit 63 of splitmix64(seed XOR (k * 2^32 + i)) is 0, else -1."""
+    i = np.arange(p, dtype=np.uint64)
+    key = np.uint64(seed) ^ ((np.uint64(k) << np.uint64(32)) | i)
+    bit = splitmix64(key) >> np.uint64(63)
+    return np.where(bit == 0, 1.0, -1.0)
+
+
+# --------------------------------------------------------------------------------------
+# Stochastic Lanczos quadrature for log det K (Sec. 3.3, stochastic trace alternative)
+# --------------------------------------------------------------------------------------
+
+
+def lanczos(matvec, z, m):
+    """m steps of symmetric Lanczos from q1 = z/||z||, no reorthogonalisation
+    (the paper reorthogonalises nothing, Sec. 3.2).  Stops early when
+    beta_j < 1e-12 |alpha_1|.  Returns alpha (length k) and beta (length k-1)."""
+    q = z / np.linalg.norm(z)
+    q_prev = np.zeros_like(q)
+    b_prev = 0.0
+    alpha, beta = [], []
+    for j in range(m):
+        u = matvec(q)
+        a = float(q @ u)
+        w = u - a * q - b_prev * q_prev
+        alpha.append(a)
+        b = float(np.linalg.norm(w))
+        if j == m - 1:
+            break
+        if b < 1e-12 * abs(alpha[0]):
+            break
+        beta.append(b)
+        q_prev, q, b_prev = q, w / b, b
+    return np.array(alpha), np.array(beta)
+
+
+def gauss_quadrature_logdet(alpha, beta, znorm2):
+    """||z||^2 sum_j tau_j^2 log theta_j over the eigenpairs (theta_j, first
+    eigenvector components tau_j) of the Lanczos tridiagonal (Golub-Welsch)."""
+    if len(alpha) == 1:
+        return znorm2 * math.log(alpha[0])
+    theta, U = scipy.linalg.eigh_tridiagonal(alpha, beta)
+    return znorm2 * float(np.sum(U[0] ** 2 * np.log(theta)))
+
+
+def slq_logdet(matvec, p, nprobe, nsteps, seed, probes=None):
+    """SLQ estimate of log det K: mean over probes of the Gauss quadrature of
+    z^T log(K) z.  ``probes`` overrides the Rademacher probes (e.g. the unit
+    vectors, for which the sum over all p probes is exact up to quadrature error).
+    Returns (estimate, standard error, per-probe values)."""
+    vals = []
+    for k in range(nprobe):
+        z = rademacher_probe(seed, k, p) if probes is None else probes(k)
+        a, b = lanczos(matvec, z, nsteps)
+        vals.append(gauss_quadrature_logdet(a, b, float(z @ z)))
+    vals = np.array(vals)
+    se = float(np.std(vals, ddof=1) / math.sqrt(nprobe)) if nprobe > 1 else 0.0
+    return float(np.mean(vals)), se, vals
+
+
+# --------------------------------------------------------------------------------------
+# Conjugate gradients (replaces the O(n^3) solves, Sec. 3)
+# --------------------------------------------------------------------------------------
+
+
+def cg(matvec, b, tol=1e-10, maxit=100000):
+    """Plain CG from x0 = 0 until ||r|| <= tol ||b||.  Returns (x, iterations)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    bnorm = math.sqrt(float(b @ b))
+    if bnorm == 0.0:
+        return x, 0
+    for it in range(1, maxit + 1):
+        Ap = matvec(p)
+        a = rr / float(p @ Ap)
+        x += a * p
+        r -= a * Ap
+        rr_new = float(r @ r)
+        if math.sqrt(rr_new) <= tol * bnorm:
+            return x, it
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, maxit
+
+
+# --------------------------------------------------------------------------------------
+# Profile log-likelihood and kriging
+# --------------------------------------------------------------------------------------
+
+
+def gls_loglik(logdet, Kinv_y, Kinv_X, y, X):
+    """GLS beta and the marginal log-likelihood with beta profiled:
+    beta = (X^T K^-1 X)^-1 X^T K^-1 y, r = y - X beta,
+    l = -1/2 [log det K + r^T K^-1 r + p log 2 pi]."""
+    A = X.T @ Kinv_X
+    g = X.T @ Kinv_y
+    beta = np.linalg.solve(A, g)
+    quad = float(y @ Kinv_y - beta @ g)
+    p = y.shape[0]
+    ll = -0.5 * (logdet + quad + p * math.log(2.0 * math.pi))
+    return ll, beta, quad
+
+
+def loglik_dense(K, y, X):
+    """Marginal log-likelihood by Cholesky (exact log det)."""
+    L = scipy.linalg.cho_factor(K, lower=True)
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L[0]))))
+    Kinv_y = scipy.linalg.cho_solve(L, y)
+    Kinv_X = scipy.linalg.cho_solve(L, X)
+    ll, beta, quad = gls_loglik(logdet, Kinv_y, Kinv_X, y, X)
+    return dict(loglik=ll, beta=beta, logdet=logdet, quad=quad)
+
+
+def krige_dense(n1, n2, mask, cov, y, X, targets, X_t, beta=None):
+    """Universal-kriging mean at target sites (m,2) with covariates X_t, and the
+    simple-kriging variance sigma^2 - c_t^T K^-1 c_t (c_t = sigma^2 Sigma_{o,t}):
+    mu_t = X_t beta + c_t^T K^-1 (y - X beta)  (the paper's x-hat, Eq. act_xhat, plus the trend)."""
+    s = observed_sites(n1, n2, mask)
+    K = dense_K(n1, n2, mask, cov)
+    L = scipy.linalg.cho_factor(K, lower=True)
+    if beta is None:
+        beta = loglik_dense(K, y, X)["beta"]
+    w = scipy.linalg.cho_solve(L, y - X @ beta)
+    C = dense_sigma(np.asarray(targets), s, cov)          # (m, p)
+    mean = X_t @ beta + C @ w
+    var = cov.sigma2 - np.einsum("ij,ji->i", C, scipy.linalg.cho_solve(L, C.T))
+    return mean, var
+
+
+class FFTProblem:
+    """A masked grid problem with the FP64 circulant-embedding matvec (Sec. 3)."""
+
+    def __init__(self, n1, n2, mask, cov):
+        self.n1, self.n2, self.mask, self.cov = n1, n2, np.asarray(mask, bool), cov
+        self.M1, self.M2 = embed_size(n1), embed_size(n2)
+        c = lag_covariance(n1, n2, self.M1, self.M2, cov)
+        self.lam, self.imag = embedding_eigs(c)
+        self.c0 = c[0, 0]
+        self.p = int(self.mask.sum())
+
+    def matvec(self, v):
+        return bttb_matvec_fft(self.n1, self.n2, self.M1, self.M2, self.lam, self.mask, v, self.cov.tau2)
+
+    def sigma_at(self, v, cells):
+        """(sigma^2 Sigma A^T v) at linear cell indices ``cells`` (no nugget)."""
+        g = np.zeros((self.n1, self.n2))
+        g[self.mask] = v
+        return sigma_conv_fft(self.n1, self.n2, self.M1, self.M2, self.lam, g).ravel()[cells]
+
+    def solve(self, B, tol=1e-10):
+        B = np.asarray(B, dtype=np.float64)
+        if B.ndim == 1:
+            return cg(self.matvec, B, tol)
+        cols, its = zip(*(cg(self.matvec, B[:, j], tol) for j in range(B.shape[1])))
+        return np.stack(cols, axis=1), max(its)
+
+    def logdet(self, nprobe, nsteps, seed, probe_ids=None):
+        ids = range(nprobe) if probe_ids is None else probe_ids
+        vals = []
+        for k in ids:
+            z = rademacher_probe(seed, k, self.p)
+            a, b = lanczos(self.matvec, z, nsteps)
+            vals.append(gauss_quadrature_logdet(a, b, float(z @ z)))
+        vals = np.array(vals)
+        se = float(np.std(vals, ddof=1) / math.sqrt(len(vals))) if len(vals) > 1 else 0.0
+        return float(np.mean(vals)), se, vals
+
+    def profile_loglik(self, y, X, nprobe, nsteps, seed, tol=1e-10):
+        ld, se, _ = self.logdet(nprobe, nsteps, seed)
+        sol, _ = self.solve(np.column_stack([y, X]), tol)
+        ll, beta, quad = gls_loglik(ld, sol[:, 0], sol[:, 1:], y, X)
+        return dict(loglik=ll, beta=beta, logdet=ld, logdet_se=se, quad=quad)
+
+    def krige_cells(self, y, X, beta, cells, X_t, tol=1e-10):
+        w, _ = cg(self.matvec, y - X @ beta, tol)
+        return X_t @ beta + self.sigma_at(w, cells)
+
+
+# --------------------------------------------------------------------------------------
+# Circulant-embedding sampling (bootstrap of Sec. 3.5; negative-eigenvalue caveat of Sec. 3.6)
+# --------------------------------------------------------------------------------------
+
+
+def sample_embed_size(n1, n2, cov, max_doublings=3):
+    """Smallest power-of-two torus (>= 2n per axis, doubled up to ``max_doublings``
+    times) whose embedding eigenvalues satisfy min >= -1e-10 max."""
+    M1, M2 = embed_size(n1), embed_size(n2)
+    for _ in range(max_doublings + 1):
+        lam, _ = embedding_eigs(lag_covariance(n1, n2, M1, M2, cov))
+        if lam.min() >= -1e-10 * lam.max():
+            return M1, M2
+        M1, M2 = 2 * M1, 2 * M2
+    return M1 // 2, M2 // 2
+
+
+def sample_field(n1, n2, M1, M2, cov, xi):
+    """One Gaussian-process sample on the n1 x n2 grid: the real part of
+    FFT2( sqrt(max(Lambda, 0) / (M1 M2)) * (xi[0] + i xi[1]) ), cropped.  Small
+    negative eigenvalues are reset to zero (Sec. 3.6 caveat)."""
+    lam, _ = embedding_eigs(lag_covariance(n1, n2, M1, M2, cov))
+    lam = np.maximum(lam, 0.0)
+    z = np.sqrt(lam / (M1 * M2)) * (xi[0] + 1j * xi[1])
+    return scipy.fft.fft2(z, workers=_WORKERS).real[:n1, :n2]
+
+
+def make_data(n1, n2, mask, cov, beta, xi, eps):
+    """y = X beta + x(obs) + tau eps with x the circulant-embedding GP sample of
+    white noise ``xi`` (shape (2, M1, M2); Eq. obs_mod with A = row selection).
+    The noise is drawn by the caller from the shared seeded generators."""
+    M1, M2 = xi.shape[1], xi.shape[2]
+    x = sample_field(n1, n2, M1, M2, cov, xi)
+    S1, S2 = coords(n1, n2)
+    X = np.stack([np.ones(int(mask.sum())), S1[mask], S2[mask]], axis=1)
+    y = X @ np.asarray(beta, dtype=np.float64) + x[mask] + math.sqrt(cov.tau2) * eps
+    return y, X, x
