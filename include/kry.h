@@ -1,0 +1,199 @@
+/*
+ * kry.h -- C ABI of the Kryging hot path on one GB300 (sm_103a).
+ *
+ * Kryging (Majumder, Guan, Reich & Saibaba, arXiv 2012.13133) models gridded
+ * spatial data as y = X beta + A x + eps (Sec. 2, Eq. obs_mod) with a latent
+ * Gaussian process x ~ N(0, sigma^2 Sigma) under a Matern correlation (Sec. 2)
+ * and nugget eps ~ N(0, tau^2 I).  A is a row selection: the observation mask.
+ * The library computes, with hand-written CUDA kernels and no CPU fallback:
+ *
+ *   - the eigenvalues of the block-circulant embedding of the BTTB covariance
+ *     (Sec. 3 and Sec. 3.3; Appendix A, Eq. circ_diag);
+ *   - the marginal covariance matvec K v = sigma^2 A Sigma A^T v + tau^2 v by
+ *     scatter, 2-D FFT, eigenvalue multiply, inverse FFT, gather (Sec. 3);
+ *   - log det K by stochastic Lanczos quadrature (the stochastic trace
+ *     alternative named in Sec. 3.3);
+ *   - CG solves with K (the matvec-only solves of Sec. 3), the GLS profile
+ *     log-likelihood and kriging means and variances (Sec. 3.1, Eq. act_xhat;
+ *     Sec. 3.5);
+ *   - Gaussian-process samples by circulant embedding (Sec. 3.5 bootstrap;
+ *     the negative-eigenvalue caveat of Sec. 3.6).
+ *
+ * Conventions shared by every entry point:
+ *   Status     Every function returns kry_status; nothing throws across the
+ *              ABI.  On failure kry_last_error(ctx) holds a one-line message.
+ *              Arguments are validated before any launch.
+ *   Memory     The caller owns every data buffer it passes; "_dev" pointers are
+ *              device pointers on the context's device, others host pointers.
+ *              The library owns kry_ctx, kry_embed and their scratch, released
+ *              by kry_destroy / kry_embed_free.
+ *   Streams    All work is enqueued on the context's stream.  Calls that
+ *              return scalars through host pointers synchronise that stream;
+ *              kry_matvec does not.
+ *   Threads    A context is not thread-safe; use one context per host thread.
+ *   Layout     The grid is n1 x n2, row-major (row index i along the first
+ *              coordinate), cell (i, j) centred at ((i + 1/2) dx1, (j + 1/2) dx2).
+ *              Observed cells are numbered 0..p-1 in row-major order; a
+ *              "vector" is p values in that order.  Batches of vectors are
+ *              column-major with leading dimension ld >= p.
+ *   Precision  KRY_F32: FP32 vectors and FFTs, FP64 Krylov scalars (alpha,
+ *              beta, dot products, quadrature).  KRY_F64: FP64 throughout.
+ *              Solves always take and return FP64 vectors; with KRY_F32 they
+ *              run FP32 CG inside FP64 iterative refinement.
+ */
+#ifndef KRY_H
+#define KRY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KRY_OK = 0,
+    KRY_EINVAL = 1,       /* bad argument (sizes, parameters, null pointers) */
+    KRY_ENOMEM = 2,       /* device allocation failed */
+    KRY_ENOTPSD = 3,      /* embedding not positive semi-definite where that is required */
+    KRY_ENOCONV = 4,      /* CG reached maxit before rtol; partial results written */
+    KRY_ENAN = 5,         /* a reduction produced NaN/Inf */
+    KRY_ETIMEOUT = 6,     /* a bounded device wait gave up */
+    KRY_ECUDA = 7,        /* a CUDA runtime call failed */
+    KRY_EUNSUPPORTED = 8  /* valid request outside the supported sizes */
+} kry_status;
+
+typedef enum { KRY_F32 = 0, KRY_F64 = 1 } kry_prec;
+
+/* Regular grid on the unit square (Sec. 4 layout): n1 x n2 cells of size dx1 x dx2. */
+typedef struct {
+    int32_t n1, n2;
+    double dx1, dx2;
+} kry_grid;
+
+/* Covariance sigma2 * Matern_nu(d / range) + tau2 * I (Sec. 2).  d is the
+ * Euclidean lag after rotating by aniso_angle (radians, counter-clockwise
+ * from the first axis) and stretching the minor axis by aniso_ratio
+ * (geometric anisotropy, Sec. 2; aniso_ratio = 1 is isotropic). */
+typedef struct {
+    double sigma2, range, nu, tau2;
+    double aniso_angle, aniso_ratio;
+} kry_cov;
+
+/* Krylov settings.  nprobe Rademacher probes x nsteps Lanczos steps for the
+ * log-determinant; CG to relative residual rtol (maxit iterations at most) with
+ * up to `refine` FP64 refinement rounds when prec = KRY_F32. */
+typedef struct {
+    kry_prec prec;
+    int32_t nprobe, nsteps;
+    uint64_t seed;
+    double rtol;
+    int32_t maxit;
+    int32_t refine;
+} kry_opts;
+
+typedef struct kry_ctx kry_ctx;       /* opaque, library-owned */
+typedef struct kry_embed kry_embed;   /* opaque, library-owned */
+
+/* Create a context on CUDA device `device` using `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  *ctx is NULL on failure. */
+kry_status kry_create(kry_ctx** ctx, int device, void* cuda_stream);
+void kry_destroy(kry_ctx* ctx);
+/* Last error message of ctx ("" if none); valid until the next call on ctx. */
+const char* kry_last_error(const kry_ctx* ctx);
+
+/* Observation pattern A (Sec. 2: a subset of identity rows).  mask_dev holds
+ * n1*n2 bytes, row-major, nonzero = observed.  Builds the library's index
+ * lists on the device and returns the number of observed cells p in *p_out.
+ * Requires 4 <= n1, n2 <= 4096 and p >= 1.  Synchronises the stream. */
+kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_dev, int64_t* p_out);
+
+/* Eigenvalues of the block-circulant embedding of sigma2 * Sigma on the
+ * M1 x M2 torus, M_d = smallest power of two >= 2 n_d (Sec. 3.3; Eq. circ_diag).
+ * The lag covariance is evaluated in FP64 (closed forms for nu in {1/2, 3/2,
+ * 5/2}, Bessel K_nu otherwise), transformed by a 2-D FFT in FP64 and kept on
+ * the device in FP64 (and FP32 when prec = KRY_F32).  No eigenvalue is
+ * clamped: the matvec is exact whatever their sign (Sec. 3.6 caveat).
+ * *min_over_max receives min(Lambda) / max(Lambda) (may be NULL).  Uses the
+ * grid of the last kry_set_mask.  Synchronises the stream. */
+kry_status kry_embed_eigs(kry_ctx* ctx, const kry_cov* cov, kry_prec prec,
+                          kry_embed** out, double* min_over_max);
+void kry_embed_free(kry_embed* e);
+
+/* out = K v for nvec vectors (K = sigma2 A Sigma A^T + tau2 I, Sec. 3).  v_dev
+ * and out_dev are FP32 (prec KRY_F32) or FP64 (KRY_F64) arrays of nvec columns
+ * with leading dimension ld.  Asynchronous.  v_dev and out_dev must not overlap. */
+kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev,
+                      int32_t nvec, int64_t ld);
+
+/* Stochastic Lanczos quadrature estimate of log det K (Sec. 3.3, stochastic
+ * trace alternative): probe k has entries z_k[i] = +1 if bit 63 of
+ * splitmix64(seed XOR (k * 2^32 + i)) is 0, else -1; nsteps Lanczos steps
+ * from q1 = z/||z|| without reorthogonalisation (Sec. 3.2 reorthogonalises
+ * nothing), stopping early when beta_j < 1e-12 |alpha_1|; Gauss quadrature
+ * ||z||^2 sum_j tau_j^2 log theta_j of the tridiagonal.  *logdet = mean over
+ * probes, *stderr_out = standard error (NULL allowed), per_probe[nprobe] the
+ * per-probe values (host, NULL allowed).  Synchronises the stream. */
+kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps,
+                      uint64_t seed, double* logdet, double* stderr_out, double* per_probe);
+
+/* Solve K X = B for nrhs FP64 right-hand sides (column-major, leading
+ * dimension ld) by CG from X = 0 to ||B - K X|| <= rtol ||B|| per column.
+ * With KRY_F32 embeddings the CG runs in FP32 with FP64 scalars inside at
+ * most `refine` FP64 refinement rounds (true residual by the FP64 matvec).
+ * iters (host, may be NULL) receives the total CG iterations, relres (host,
+ * may be NULL) the largest final relative residual.  Returns KRY_ENOCONV,
+ * with X filled, when rtol was not reached.  Synchronises the stream. */
+kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev,
+                     int32_t nrhs, int64_t ld, double rtol, int32_t maxit, int32_t refine,
+                     int32_t* iters, double* relres);
+
+/* Marginal log-likelihood of the observed cells with beta profiled by GLS,
+ * for ntheta covariance settings:
+ *   beta = (X^T K^-1 X)^-1 X^T K^-1 y,  r = y - X beta,
+ *   loglik = -1/2 [log det K + r^T K^-1 r + p log 2 pi],
+ * log det K by kry_logdet's estimator (opts->nprobe, nsteps, seed), the solves
+ * by kry_solve (opts->rtol, maxit, refine).  It equals the paper's exact
+ * profile likelihood (Eq. exact_plik) minus 1/2 log det Gamma^-1 and a
+ * constant.  y_dev: p FP64; X_dev: p x ncov FP64 column-major (1 <= ncov <= 8).
+ * Host outputs: loglik[ntheta], beta[ntheta * ncov], logdet[ntheta],
+ * logdet_se[ntheta] (the last three may be NULL).  Synchronises the stream. */
+kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
+                              const kry_cov* thetas, int32_t ntheta, const kry_opts* opts,
+                              double* loglik, double* beta, double* logdet, double* logdet_se);
+
+/* Kriging at target cells and at off-grid sites with beta from GLS:
+ *   mean_t = X_t beta + sigma2 Sigma_{t,obs} K^-1 (y - X beta)
+ * (the paper's x-hat of Eq. act_xhat plus the trend), and optionally the
+ * simple-kriging variance sigma2 - sigma2^2 c_t^T K^-1 c_t at the target cells
+ * (the quantity the bootstrap of Sec. 3.5 estimates).
+ * cells_dev: ncell int64 row-major cell indices; Xc_dev: ncell x ncov FP64
+ * column-major; sites_dev: nsite x 2 FP64 row-major coordinates; Xs_dev: nsite x
+ * ncov.  Outputs (device, FP64): mean_cells_dev[ncell], mean_sites_dev[nsite],
+ * var_cells_dev[ncell] (NULL skips the variances).  beta_out (host, ncov, may be
+ * NULL).  Synchronises the stream. */
+kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts,
+                     const double* y_dev, const double* X_dev, int32_t ncov,
+                     const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,
+                     const double* sites_dev, const double* Xs_dev, int64_t nsite,
+                     double* mean_cells_dev, double* mean_sites_dev, double* var_cells_dev,
+                     double* beta_out);
+
+/* Circulant-embedding sample of the latent process on the n1 x n2 grid of the
+ * last kry_set_mask (Sec. 3.5 bootstrap): out = Re FFT2( sqrt(max(Lambda, 0) /
+ * (M1 M2)) * (xi_re + i xi_im) ) cropped to the grid, with the embedding on an
+ * M1 x M2 torus (powers of two, each >= 2 n_d and <= 8192).  xi_dev holds 2 *
+ * M1 * M2 FP64 normals (real plane, then imaginary plane); out_dev n1 * n2 FP64.
+ * Negative eigenvalues are reset to zero (Sec. 3.6 caveat).  Asynchronous. */
+kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
+                      const double* xi_dev, double* out_dev);
+
+/* Smallest torus for kry_sample: starting from M_d = smallest power of two
+ * >= 2 n_d, doubles both sides (at most 3 times, never past 8192) until
+ * min(Lambda) >= -1e-10 max(Lambda).  Returns KRY_ENOTPSD with the largest
+ * size tried if none qualifies.  Synchronises the stream. */
+kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRY_H */

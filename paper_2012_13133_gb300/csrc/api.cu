@@ -1,0 +1,514 @@
+// C ABI of the Kryging library (declared in include/kry.h): argument
+// validation, context and mask set-up, and the glue that sequences the
+// kernels of embed.cu, matvec.cu and krylov.cu.  No computation of the hot
+// path happens on the host beyond scalar bookkeeping.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kry_internal.cuh"
+
+namespace kry {
+void store_embedding(kry_ctx* ctx, kry_embed* e);
+template <typename T>
+void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+               int64_t ld_out, int nvec, double* dots, int nds);
+void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe);
+SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
+                double rtol, int maxit, int refine);
+GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet);
+void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_dev, double* w);
+void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, int64_t ncell, const double* Xc,
+                        int ncov, const double* beta_dev, double* mean, int* bad);
+void krige_launch_sites(kry_ctx* ctx, const kry_cov& cov, const double* sites, int64_t nsite, const double* Xs,
+                        int ncov, const double* beta_dev, const double* w, double* mean);
+bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
+                     double rtol, int maxit, int refine);
+}  // namespace kry
+
+void DevBuf::ensure(size_t bytes) {
+    if (bytes <= cap && p) return;
+    release();
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cap = 0;
+        (void)cudaGetLastError();
+        throw KryError{KRY_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                       cudaGetErrorString(e)};
+    }
+    cap = bytes;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+// ------------------------------------------------------------------ mask compaction
+
+// Observed cells per row (one block per row).
+__global__ void k_row_counts(const uint8_t* __restrict__ mask, int n2, int* __restrict__ counts) {
+    const int row = blockIdx.x;
+    int c = 0;
+    for (int j = threadIdx.x; j < n2; j += blockDim.x) c += mask[(int64_t)row * n2 + j] != 0;
+    __shared__ int red[32];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        counts[row] = s;
+    }
+}
+
+// Exclusive scan of the row counts into rowptr[0..n1] (one block, serial over warps).
+__global__ void k_rowptr(const int* __restrict__ counts, int n1, int* __restrict__ rowptr) {
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int i = 0; i < n1; ++i) {
+            rowptr[i] = s;
+            s += counts[i];
+        }
+        rowptr[n1] = s;
+    }
+}
+
+// Ordered compaction of one row: colidx and cellidx of its observed cells.
+__global__ void k_row_fill(const uint8_t* __restrict__ mask, int n2, const int* __restrict__ rowptr,
+                           int* __restrict__ colidx, int* __restrict__ cellidx) {
+    const int row = blockIdx.x;
+    __shared__ int wsum[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = rowptr[row];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j0 = 0; j0 < n2; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const bool f = (j < n2) && mask[(int64_t)row * n2 + j] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int k = 0; k < w; ++k) off += wsum[k];
+        const int pos = base + off + __popc(bal & ((1u << lane) - 1u));
+        if (f) {
+            colidx[pos] = j;
+            cellidx[pos] = row * n2 + j;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < nw; ++k) t += wsum[k];
+            base += t;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+
+static kry_status fail(kry_ctx* ctx, kry_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+template <class F>
+static kry_status guarded(kry_ctx* ctx, F&& f) {
+    if (!ctx) return KRY_EINVAL;
+    try {
+        KRY_CUDA(cudaSetDevice(ctx->device));
+        ctx->err.clear();
+        return f();
+    } catch (const KryError& e) {
+        ctx->err = e.msg;
+        return e.st;
+    } catch (const std::exception& e) {
+        ctx->err = e.what();
+        return KRY_ECUDA;
+    }
+}
+
+static void check_cov(const kry_cov* cov) {
+    KRY_REQUIRE(cov != nullptr, KRY_EINVAL, "cov is NULL");
+    KRY_REQUIRE(cov->sigma2 >= 0 && isfinite(cov->sigma2), KRY_EINVAL, "sigma2 must be finite and >= 0");
+    KRY_REQUIRE(cov->tau2 >= 0 && isfinite(cov->tau2), KRY_EINVAL, "tau2 must be finite and >= 0");
+    KRY_REQUIRE(cov->range > 0 && isfinite(cov->range), KRY_EINVAL, "range must be finite and > 0");
+    KRY_REQUIRE(cov->nu > 0 && cov->nu <= 8.0, KRY_EINVAL, "nu must be in (0, 8]");
+    KRY_REQUIRE(cov->aniso_ratio > 0 && isfinite(cov->aniso_ratio), KRY_EINVAL, "aniso_ratio must be > 0");
+    KRY_REQUIRE(isfinite(cov->aniso_angle), KRY_EINVAL, "aniso_angle must be finite");
+}
+
+static int pow2_at_least(int64_t x) {
+    int M = 1;
+    while (M < x) M *= 2;
+    return M;
+}
+
+static void require_mask(kry_ctx* ctx) {
+    KRY_REQUIRE(ctx->p > 0, KRY_EINVAL, "no observation mask set (kry_set_mask)");
+}
+
+static void check_embed(kry_ctx* ctx, const kry_embed* e) {
+    KRY_REQUIRE(e != nullptr, KRY_EINVAL, "embedding is NULL");
+    KRY_REQUIRE(e->ctx == ctx, KRY_EINVAL, "embedding belongs to another context");
+    KRY_REQUIRE(e->n1 == ctx->n1 && e->n2 == ctx->n2, KRY_EINVAL, "embedding grid differs from the mask grid");
+    require_mask(ctx);
+}
+
+static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
+    check_cov(cov);
+    require_mask(ctx);
+    KRY_REQUIRE(prec == KRY_F32 || prec == KRY_F64, KRY_EINVAL, "prec must be KRY_F32 or KRY_F64");
+    kry_embed* e = new kry_embed();
+    e->ctx = ctx;
+    e->n1 = ctx->n1;
+    e->n2 = ctx->n2;
+    e->M1 = pow2_at_least(2 * (int64_t)ctx->n1);
+    e->M2 = pow2_at_least(2 * (int64_t)ctx->n2);
+    e->cov = *cov;
+    e->prec = prec;
+    try {
+        kry::compute_eigs(ctx, *cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, e->M1, e->M2, &e->lam_min, &e->lam_max);
+        const size_t MM = (size_t)e->M1 * e->M2;
+        KRY_CUDA(cudaMalloc(&e->lam64T, MM * sizeof(double)));
+        if (prec == KRY_F32) KRY_CUDA(cudaMalloc(&e->lam32T, MM * sizeof(float)));
+        kry::store_embedding(ctx, e);
+    } catch (...) {
+        if (e->lam64T) cudaFree(e->lam64T);
+        if (e->lam32T) cudaFree(e->lam32T);
+        delete e;
+        throw;
+    }
+    return e;
+}
+
+static void free_embed(kry_embed* e) {
+    if (!e) return;
+    if (e->lam64T) cudaFree(e->lam64T);
+    if (e->lam32T) cudaFree(e->lam32T);
+    delete e;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
+    if (!out) return KRY_EINVAL;
+    *out = nullptr;
+    kry_ctx* ctx = new kry_ctx();
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    kry_status st = guarded(ctx, [&]() -> kry_status {
+        int ndev = 0;
+        KRY_CUDA(cudaGetDeviceCount(&ndev));
+        KRY_REQUIRE(device >= 0 && device < ndev, KRY_EINVAL, "no such CUDA device");
+        KRY_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+        KRY_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+        KRY_CUDA(cudaMallocHost(&ctx->host_pinned, 4096 * sizeof(double)));
+        kry::init_twiddles(ctx);
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        return KRY_OK;
+    });
+    if (st != KRY_OK) {
+        fprintf(stderr, "kry_create: %s\n", ctx->err.c_str());
+        kry_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return KRY_OK;
+}
+
+void kry_destroy(kry_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->slab32,
+                      &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& b : ctx->work) b.release();
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    delete ctx;
+}
+
+const char* kry_last_error(const kry_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_dev, int64_t* p_out) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_REQUIRE(grid && mask_dev, KRY_EINVAL, "grid and mask_dev must not be NULL");
+        KRY_REQUIRE(grid->n1 >= 4 && grid->n2 >= 4, KRY_EUNSUPPORTED, "grid sides must be >= 4");
+        KRY_REQUIRE(grid->n1 <= KRY_MAX_N && grid->n2 <= KRY_MAX_N, KRY_EUNSUPPORTED, "grid sides must be <= 4096");
+        KRY_REQUIRE(grid->dx1 > 0 && grid->dx2 > 0, KRY_EINVAL, "cell sizes must be > 0");
+        const int n1 = grid->n1, n2 = grid->n2;
+        ctx->p = 0;
+        ctx->rowptr.ensure((size_t)(n1 + 1) * sizeof(int));
+        ctx->colidx.ensure((size_t)n1 * n2 * sizeof(int));
+        ctx->cellidx.ensure((size_t)n1 * n2 * sizeof(int));
+        ctx->red.ensure((size_t)(n1 + 1) * sizeof(int));
+        int* counts = ctx->red.as<int>();
+        k_row_counts<<<n1, 256, 0, ctx->stream>>>(mask_dev, n2, counts);
+        KRY_CHECK_LAUNCH();
+        k_rowptr<<<1, 32, 0, ctx->stream>>>(counts, n1, ctx->rowptr.as<int>());
+        KRY_CHECK_LAUNCH();
+        k_row_fill<<<n1, 256, 0, ctx->stream>>>(mask_dev, n2, ctx->rowptr.as<int>(), ctx->colidx.as<int>(),
+                                                ctx->cellidx.as<int>());
+        KRY_CHECK_LAUNCH();
+        int* hp = reinterpret_cast<int*>(ctx->host_pinned);
+        KRY_CUDA(cudaMemcpyAsync(hp, ctx->rowptr.as<int>() + n1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int64_t p = hp[0];
+        KRY_REQUIRE(p >= 1, KRY_EINVAL, "mask has no observed cell");
+        ctx->n1 = n1;
+        ctx->n2 = n2;
+        ctx->dx1 = grid->dx1;
+        ctx->dx2 = grid->dx2;
+        ctx->p = p;
+        if (p_out) *p_out = p;
+        return KRY_OK;
+    });
+}
+
+kry_status kry_embed_eigs(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, kry_embed** out, double* min_over_max) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_REQUIRE(out != nullptr, KRY_EINVAL, "out is NULL");
+        *out = nullptr;
+        kry_embed* e = make_embed(ctx, cov, prec);
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (min_over_max) *min_over_max = (e->lam_max != 0.0) ? e->lam_min / e->lam_max : 0.0;
+        *out = e;
+        return KRY_OK;
+    });
+}
+
+void kry_embed_free(kry_embed* e) {
+    if (!e) return;
+    cudaSetDevice(e->ctx->device);
+    cudaStreamSynchronize(e->ctx->stream);
+    free_embed(e);
+}
+
+kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev, int32_t nvec, int64_t ld) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_embed(ctx, e);
+        KRY_REQUIRE(v_dev && out_dev, KRY_EINVAL, "v_dev and out_dev must not be NULL");
+        KRY_REQUIRE(nvec >= 0 && ld >= ctx->p, KRY_EINVAL, "need nvec >= 0 and ld >= p");
+        if (nvec == 0) return KRY_OK;
+        if (e->prec == KRY_F64)
+            kry::matvec_ex<double>(ctx, e, static_cast<const double*>(v_dev), ld, nullptr, static_cast<double*>(out_dev),
+                                   ld, nvec, nullptr, 0);
+        else
+            kry::matvec_ex<float>(ctx, e, static_cast<const float*>(v_dev), ld, nullptr, static_cast<float*>(out_dev),
+                                  ld, nvec, nullptr, 0);
+        return KRY_OK;
+    });
+}
+
+static void mean_se(const std::vector<double>& v, double* mean, double* se) {
+    const int n = (int)v.size();
+    double s = 0.0;
+    for (double x : v) s += x;
+    const double m = s / n;
+    double q = 0.0;
+    for (double x : v) q += (x - m) * (x - m);
+    *mean = m;
+    if (se) *se = (n > 1) ? sqrt(q / (n - 1) / n) : 0.0;
+}
+
+kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps, uint64_t seed, double* logdet,
+                      double* stderr_out, double* per_probe) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_embed(ctx, e);
+        KRY_REQUIRE(logdet != nullptr, KRY_EINVAL, "logdet is NULL");
+        KRY_REQUIRE(nprobe >= 1 && nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
+        std::vector<double> vals(nprobe);
+        kry::logdet(ctx, e, nprobe, nsteps, seed, vals.data());
+        double se = 0.0;
+        mean_se(vals, logdet, &se);
+        if (stderr_out) *stderr_out = se;
+        if (per_probe) memcpy(per_probe, vals.data(), nprobe * sizeof(double));
+        for (double v : vals)
+            if (!isfinite(v)) return fail(ctx, KRY_ENAN, "log-det quadrature produced NaN/Inf");
+        return KRY_OK;
+    });
+}
+
+kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev, int32_t nrhs, int64_t ld,
+                     double rtol, int32_t maxit, int32_t refine, int32_t* iters, double* relres) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_embed(ctx, e);
+        KRY_REQUIRE(B_dev && X_dev, KRY_EINVAL, "B_dev and X_dev must not be NULL");
+        KRY_REQUIRE(nrhs >= 1 && nrhs <= 1024 && ld >= ctx->p, KRY_EINVAL, "need 1 <= nrhs <= 1024 and ld >= p");
+        KRY_REQUIRE(rtol > 0 && maxit >= 1 && refine >= 0, KRY_EINVAL, "need rtol > 0, maxit >= 1, refine >= 0");
+        kry::SolveInfo si = kry::solve(ctx, e, B_dev, ld, X_dev, ld, nrhs, rtol, maxit, refine);
+        if (iters) *iters = si.iters;
+        if (relres) *relres = si.relres;
+        if (!isfinite(si.relres)) return fail(ctx, KRY_ENAN, "CG residual is NaN/Inf");
+        if (!si.converged) return fail(ctx, KRY_ENOCONV, "CG did not reach rtol");
+        return KRY_OK;
+    });
+}
+
+static void check_opts(const kry_opts* o) {
+    KRY_REQUIRE(o != nullptr, KRY_EINVAL, "opts is NULL");
+    KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64, KRY_EINVAL, "opts->prec invalid");
+    KRY_REQUIRE(o->nprobe >= 1 && o->nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
+    KRY_REQUIRE(o->rtol > 0 && o->maxit >= 1 && o->refine >= 0, KRY_EINVAL, "need rtol > 0, maxit >= 1, refine >= 0");
+}
+
+// [y, X] packed into one (p x (ncov+1)) FP64 block and its solve Z = K^-1 [y, X].
+static kry::SolveInfo solve_yx(kry_ctx* ctx, const kry_embed* e, const double* y, const double* X, int ncov,
+                               const kry_opts* o, double** V_out, double** Z_out) {
+    const int64_t p = ctx->p;
+    const int nc = ncov + 1;
+    ctx->zbuf.ensure((size_t)2 * nc * p * sizeof(double));
+    double* V = ctx->zbuf.as<double>();
+    double* Z = V + (size_t)nc * p;
+    KRY_CUDA(cudaMemcpyAsync(V, y, p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    KRY_CUDA(cudaMemcpyAsync(V + p, X, (size_t)ncov * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    *V_out = V;
+    *Z_out = Z;
+    return kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit, o->refine);
+}
+
+kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
+                              const kry_cov* thetas, int32_t ntheta, const kry_opts* opts, double* loglik,
+                              double* beta, double* logdet, double* logdet_se) {
+    return guarded(ctx, [&]() -> kry_status {
+        require_mask(ctx);
+        check_opts(opts);
+        KRY_REQUIRE(y_dev && X_dev && thetas && loglik, KRY_EINVAL, "y_dev, X_dev, thetas, loglik must not be NULL");
+        KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
+        KRY_REQUIRE(ntheta >= 1, KRY_EINVAL, "ntheta must be >= 1");
+        for (int t = 0; t < ntheta; ++t) check_cov(&thetas[t]);
+        kry_status worst = KRY_OK;
+        for (int t = 0; t < ntheta; ++t) {
+            kry_embed* e = make_embed(ctx, &thetas[t], opts->prec);
+            try {
+                std::vector<double> vals(opts->nprobe);
+                kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+                double ld = 0, se = 0;
+                mean_se(vals, &ld, &se);
+                double *V, *Z;
+                kry::SolveInfo si = solve_yx(ctx, e, y_dev, X_dev, ncov, opts, &V, &Z);
+                kry::GlsResult g = kry::gls(ctx, V, Z, ncov, ld);
+                loglik[t] = g.loglik;
+                if (beta)
+                    for (int c = 0; c < ncov; ++c) beta[(size_t)t * ncov + c] = g.beta[c];
+                if (logdet) logdet[t] = ld;
+                if (logdet_se) logdet_se[t] = se;
+                if (!isfinite(g.loglik) || !g.ok) worst = KRY_ENAN;
+                else if (!si.converged && worst == KRY_OK) worst = KRY_ENOCONV;
+            } catch (...) {
+                free_embed(e);
+                throw;
+            }
+            free_embed(e);
+        }
+        if (worst == KRY_ENAN) return fail(ctx, worst, "log-likelihood is NaN/Inf or X^T K^-1 X is singular");
+        if (worst == KRY_ENOCONV) return fail(ctx, worst, "CG did not reach rtol for some theta");
+        return KRY_OK;
+    });
+}
+
+kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, const double* y_dev, const double* X_dev,
+                     int32_t ncov, const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,
+                     const double* sites_dev, const double* Xs_dev, int64_t nsite, double* mean_cells_dev,
+                     double* mean_sites_dev, double* var_cells_dev, double* beta_out) {
+    return guarded(ctx, [&]() -> kry_status {
+        require_mask(ctx);
+        check_opts(opts);
+        check_cov(cov);
+        KRY_REQUIRE(y_dev && X_dev, KRY_EINVAL, "y_dev and X_dev must not be NULL");
+        KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
+        KRY_REQUIRE(ncell >= 0 && nsite >= 0, KRY_EINVAL, "ncell and nsite must be >= 0");
+        KRY_REQUIRE(ncell == 0 || (cells_dev && Xc_dev && mean_cells_dev), KRY_EINVAL,
+                    "cells_dev, Xc_dev and mean_cells_dev are required when ncell > 0");
+        KRY_REQUIRE(nsite == 0 || (sites_dev && Xs_dev && mean_sites_dev), KRY_EINVAL,
+                    "sites_dev, Xs_dev and mean_sites_dev are required when nsite > 0");
+        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry_status st = KRY_OK;
+        try {
+            double *V, *Z;
+            kry::SolveInfo si = solve_yx(ctx, e, y_dev, X_dev, ncov, opts, &V, &Z);
+            kry::GlsResult g = kry::gls(ctx, V, Z, ncov, 0.0);
+            if (beta_out)
+                for (int c = 0; c < ncov; ++c) beta_out[c] = g.beta[c];
+            const int64_t p = ctx->p;
+            const int64_t N = (int64_t)ctx->n1 * ctx->n2;
+            ctx->gbuf.ensure((size_t)(N + p + KRY_MAX_COV + 1) * sizeof(double));
+            double* grid = ctx->gbuf.as<double>();
+            double* w = grid + N;
+            double* bdev = w + p;
+            int* bad = reinterpret_cast<int*>(bdev + KRY_MAX_COV);
+            KRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+            KRY_CUDA(cudaMemcpyAsync(bdev, g.beta, ncov * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            kry::resid_weights(ctx, Z, ncov, bdev, w);
+            if (ncell > 0) {
+                // sigma2 Sigma A^T w on every grid cell (FP64 FFT path, no nugget)
+                kry::sigma_to_grid64(ctx, e, w, grid, 1, p);
+                kry::krige_launch_cells(ctx, grid, cells_dev, ncell, Xc_dev, ncov, bdev, mean_cells_dev, bad);
+            }
+            kry::krige_launch_sites(ctx, *cov, sites_dev, nsite, Xs_dev, ncov, bdev, w, mean_sites_dev);
+            bool vok = true;
+            if (var_cells_dev && ncell > 0)
+                vok = kry::krige_variances(ctx, e, cells_dev, ncell, var_cells_dev, opts->rtol, opts->maxit,
+                                           opts->refine);
+            int* hbad = reinterpret_cast<int*>(ctx->host_pinned);
+            KRY_CUDA(cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+            if (*hbad) st = fail(ctx, KRY_EINVAL, "a target cell index lies outside the grid (its mean is NaN)");
+            else if (!g.ok) st = fail(ctx, KRY_ENAN, "X^T K^-1 X is singular");
+            else if (!si.converged || !vok) st = fail(ctx, KRY_ENOCONV, "CG did not reach rtol");
+        } catch (...) {
+            free_embed(e);
+            throw;
+        }
+        free_embed(e);
+        return st;
+    });
+}
+
+kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_cov(cov);
+        require_mask(ctx);
+        KRY_REQUIRE(M1 && M2, KRY_EINVAL, "M1 and M2 must not be NULL");
+        int m1 = pow2_at_least(2 * (int64_t)ctx->n1), m2 = pow2_at_least(2 * (int64_t)ctx->n2);
+        for (int d = 0; d <= 3; ++d) {
+            if (m1 > KRY_MAX_M || m2 > KRY_MAX_M) break;
+            double lo, hi;
+            kry::compute_eigs(ctx, *cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, m1, m2, &lo, &hi);
+            *M1 = m1;
+            *M2 = m2;
+            if (lo >= -1e-10 * hi) return KRY_OK;
+            m1 *= 2;
+            m2 *= 2;
+        }
+        return fail(ctx, KRY_ENOTPSD, "no embedding up to the size limit is positive semi-definite");
+    });
+}
+
+kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2, const double* xi_dev,
+                      double* out_dev) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_cov(cov);
+        require_mask(ctx);
+        KRY_REQUIRE(xi_dev && out_dev, KRY_EINVAL, "xi_dev and out_dev must not be NULL");
+        KRY_REQUIRE(M1 >= 2 * ctx->n1 && M2 >= 2 * ctx->n2 && M1 <= KRY_MAX_M && M2 <= KRY_MAX_M &&
+                        (M1 & (M1 - 1)) == 0 && (M2 & (M2 - 1)) == 0,
+                    KRY_EINVAL, "M1, M2 must be powers of two with 2 n_d <= M_d <= 8192");
+        kry::sample_field(ctx, *cov, M1, M2, xi_dev, out_dev);
+        return KRY_OK;
+    });
+}
+
+}  // extern "C"

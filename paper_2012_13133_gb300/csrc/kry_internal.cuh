@@ -1,0 +1,146 @@
+// Internal declarations of the Kryging CUDA library: context and embedding
+// objects, scratch buffers, error handling and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kry.h"
+
+// Largest FFT length along one axis and the size of the shared twiddle table
+// W[k] = exp(-2 pi i k / KRY_TWN).  Every power-of-two length L <= KRY_TWN
+// indexes it with stride KRY_TWN / L.
+#define KRY_TWN 8192
+#define KRY_MAX_M 8192
+#define KRY_MAX_N 4096
+#define KRY_MAX_COV 8
+
+// ------------------------------------------------------------------ errors
+
+struct KryError {
+    kry_status st;
+    std::string msg;
+};
+
+#define KRY_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            throw KryError{KRY_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define KRY_CHECK_LAUNCH() KRY_CUDA(cudaGetLastError())
+
+#define KRY_REQUIRE(cond, status, text)        \
+    do {                                       \
+        if (!(cond)) throw KryError{status, text}; \
+    } while (0)
+
+// ------------------------------------------------------------------ device buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    void ensure(size_t bytes);   // grows (never shrinks); contents are not kept
+    void release();
+    template <typename T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Matvec launch schedule: elements per thread in the row passes and the
+// column pass, rows per CTA in the row passes, columns per CTA in the column
+// pass (= the column-tile width of the intermediate slab), and the number of
+// complex vector pairs per batch.
+struct MvSched {
+    int ept_row = 8;
+    int rows_per_cta = 1;
+    int ept_col = 8;
+    int cols_per_cta = 4;
+    int pairs_per_batch = 0;   // 0 = all pairs at once
+};
+
+struct kry_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // observation pattern
+    int n1 = 0, n2 = 0;
+    double dx1 = 0, dx2 = 0;
+    int64_t p = 0;
+    DevBuf rowptr;   // int32 [n1 + 1]: first observed index of each row
+    DevBuf colidx;   // int32 [p]: column of each observed cell
+    DevBuf cellidx;  // int32 [p]: row-major cell index of each observed cell
+
+    // shared twiddle tables, W[k] = exp(-2 pi i k / KRY_TWN)
+    DevBuf tw32, tw64;
+
+    // scratch
+    DevBuf slab32, slab64;        // FFT intermediates
+    DevBuf work[12];              // Krylov vectors and partials
+    DevBuf scal;                  // FP64 Krylov scalars
+    DevBuf eig_c, eig_z;          // eigenvalue computation
+    DevBuf red;                   // reduction partials
+    DevBuf tolbuf, kxbuf;         // CG tolerances, FP64 residual matvec output
+    DevBuf cbuf, sbuf;            // kriging-variance right-hand sides and solutions
+    DevBuf zbuf, gbuf;            // [y, X] and its solve; kriging grid and weights
+    double* host_pinned = nullptr;   // pinned host scratch (4096 doubles)
+    int num_sms = 0;
+    int max_smem_optin = 0;
+
+    MvSched sched32, sched64;
+};
+
+struct kry_embed {
+    kry_ctx* ctx = nullptr;
+    int n1 = 0, n2 = 0, M1 = 0, M2 = 0;
+    kry_cov cov{};
+    kry_prec prec = KRY_F32;
+    // eigenvalues transposed to [M2][M1] (column-pass order) and scaled by
+    // 1 / (M1 M2), FP64 always and FP32 when prec = KRY_F32
+    double* lam64T = nullptr;
+    float* lam32T = nullptr;
+    double lam_min = 0, lam_max = 0;
+};
+
+// ------------------------------------------------------------------ internal entry points
+
+namespace kry {
+
+void init_twiddles(kry_ctx* ctx);
+
+// Eigenvalues Lambda = FFT2(c) of the embedding on M1 x M2 (natural order,
+// unscaled, FP64) into ctx->eig_c; returns min and max.
+void compute_eigs(kry_ctx* ctx, const kry_cov& cov, int n1, int n2, double dx1, double dx2,
+                  int M1, int M2, double* lam_min, double* lam_max);
+
+// Matvec passes.  vin/vout: real vectors (T) with leading dimension ld.
+// Mode PLAIN: vout = K vin.
+template <typename T>
+void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld,
+            double tau2_scale);
+
+// Sigma (no nugget) applied to observed values, evaluated at every grid cell:
+// out_grid[n1*n2] per vector (FP64 only; used for kriging).
+void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double* out_grid, int nvec,
+                     int64_t ld);
+
+void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out);
+
+int smem_limit(kry_ctx* ctx);
+
+struct SolveInfo {
+    int iters = 0;
+    double relres = 0.0;
+    bool converged = false;
+};
+
+struct GlsResult {
+    double loglik, quad;
+    double beta[KRY_MAX_COV];
+    bool ok;
+};
+
+}  // namespace kry

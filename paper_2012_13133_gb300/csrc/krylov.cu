@@ -1,0 +1,806 @@
+// Krylov loops on the covariance matvec:
+//   * stochastic Lanczos quadrature for log det K (Sec. 3.3 names stochastic
+//     trace estimation as the alternative to the circulant log-det);
+//   * conjugate gradients for K X = B with FP64 iterative refinement (the
+//     matvec-only solves that replace the O(n^3) inversions of Sec. 3);
+//   * GLS beta and the profile log-likelihood; kriging means (the paper's
+//     x-hat, Eq. act_xhat, by Woodbury) and simple-kriging variances (the
+//     quantity the bootstrap of Sec. 3.5 estimates).
+//
+// Vectors are FP32 (or FP64 for FP64 embeddings); every dot product is
+// accumulated in FP64 per block and reduced in a fixed order by one small
+// kernel, so results do not depend on scheduling.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fft.cuh"
+#include "kry_internal.cuh"
+#include "matern.cuh"
+
+namespace kry {
+
+template <typename T>
+void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+               int64_t ld_out, int nvec, double* dots, int nds);
+int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl);
+
+static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
+
+// ------------------------------------------------------------------ probes
+
+// splitmix64 output function (Steele, Lea & Flood 2014) of state x.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_probes(T* __restrict__ W, int64_t p, int nprobe, int probe0, uint64_t seed) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = seed ^ (((uint64_t)(probe0 + k) << 32) | (uint64_t)i);
+        W[(int64_t)k * p + i] = (splitmix64(key) >> 63) ? (T)-1 : (T)1;
+    }
+}
+
+// ------------------------------------------------------------------ block reduction helper
+
+template <int N>
+__device__ __forceinline__ void block_sum_store(double (&v)[N], double* out, int64_t out_stride) {
+    __shared__ double red[N][32];
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < N; ++a) red[a][w] = v[a];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            double s = 0.0;
+            for (int k = 0; k < nw; ++k) s += red[a][k];
+            out[a * out_stride] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Lanczos
+
+struct LanczosState {
+    double* s_cur;    // [nprobe] scale of the current vector: q_j = s_cur * W_cur
+    double* s_prev;   // [nprobe]
+    double* alpha;    // [nprobe][nsteps]
+    double* beta;     // [nprobe][nsteps]
+    int* m_eff;       // [nprobe] Lanczos steps kept (early stop on breakdown)
+};
+
+__global__ void k_lanczos_init(LanczosState S, int nprobe, int nsteps, double s0) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprobe) return;
+    S.s_cur[k] = s0;
+    S.s_prev[k] = 0.0;
+    S.m_eff[k] = nsteps;
+}
+
+// alpha_j = sum of the block partials of q_j^T K q_j (fixed order).
+__global__ void k_lanczos_alpha(LanczosState S, const double* __restrict__ part, int nblk, int nprobe, int nsteps,
+                                int j) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprobe) return;
+    double a = 0.0;
+    for (int b = 0; b < nblk; ++b) a += part[(int64_t)k * nblk + b];
+    S.alpha[(int64_t)k * nsteps + j] = a;
+}
+
+// w_next = U - alpha_j s_cur W_cur - beta_{j-1} s_prev W_prev;  partial ||w_next||^2.
+template <typename T>
+__global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ Wc, const T* __restrict__ Wp,
+                                 T* __restrict__ Wn, int64_t p, LanczosState S, int nsteps, int j,
+                                 double* __restrict__ part) {
+    const int k = blockIdx.y;
+    const double a = S.alpha[(int64_t)k * nsteps + j];
+    const T ca = (T)(a * S.s_cur[k]);
+    const T cb = (T)((j > 0 ? S.beta[(int64_t)k * nsteps + j - 1] : 0.0) * S.s_prev[k]);
+    const int64_t off = (int64_t)k * p;
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const T w = U[off + i] - ca * Wc[off + i] - cb * Wp[off + i];
+        Wn[off + i] = w;
+        acc[0] += (double)w * (double)w;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+// beta_j = ||w_next||; early stop when beta_j < 1e-12 |alpha_1|; rescale.
+__global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, int nblk, int nprobe, int nsteps,
+                               int j) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprobe) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+    const double bj = sqrt(s);
+    const bool stopped = S.m_eff[k] < nsteps;
+    if (!stopped && bj < 1e-12 * fabs(S.alpha[(int64_t)k * nsteps])) S.m_eff[k] = j + 1;
+    const bool now_stopped = S.m_eff[k] < nsteps;
+    S.beta[(int64_t)k * nsteps + j] = now_stopped ? 0.0 : bj;
+    S.s_prev[k] = S.s_cur[k];
+    S.s_cur[k] = now_stopped ? 0.0 : 1.0 / bj;
+}
+
+// Gauss quadrature of z^T log(K) z from the Lanczos tridiagonal: implicit QL
+// iterations with Wilkinson shifts (Bowdler, Martin, Reinsch & Wilkinson,
+// "The QR and QL algorithms for symmetric matrices", Numer. Math. 1968),
+// rotating only the first row of the eigenvector matrix (Golub & Welsch 1969).
+#define KRY_MAX_STEPS 256
+__global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, double znorm2, double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprobe) return;
+    const int n = S.m_eff[k];
+    double d[KRY_MAX_STEPS], e[KRY_MAX_STEPS], z[KRY_MAX_STEPS];
+    for (int i = 0; i < n; ++i) {
+        d[i] = S.alpha[(int64_t)k * nsteps + i];
+        e[i] = (i < n - 1) ? S.beta[(int64_t)k * nsteps + i] : 0.0;
+        z[i] = (i == 0) ? 1.0 : 0.0;
+    }
+    const double eps = 2.220446049250313e-16;
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter < 100; ++iter) {
+            int m = l;
+            for (; m < n - 1; ++m) {
+                const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(e[m]) <= eps * dd) break;
+            }
+            if (m == l) break;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            double s = 1.0, c = 1.0, pp = 0.0;
+            bool deflated = false;
+            for (int i = m - 1; i >= l; --i) {
+                const double f = s * e[i];
+                const double b = c * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= pp;
+                    e[m] = 0.0;
+                    deflated = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - pp;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                pp = s * r;
+                d[i + 1] = g + pp;
+                g = c * r - b;
+                const double zf = z[i + 1];
+                z[i + 1] = s * z[i] + c * zf;
+                z[i] = c * z[i] - s * zf;
+            }
+            if (deflated) continue;
+            d[l] -= pp;
+            e[l] = g;
+            e[m] = 0.0;
+        }
+    }
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc += z[i] * z[i] * log(d[i]);
+    out[k] = znorm2 * acc;
+}
+
+template <typename T>
+static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed,
+                           double* per_probe) {
+    const bool dbl = sizeof(T) == 8;
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    const int nblkC = matvec_num_partials(ctx, e, dbl);
+    const size_t vbytes = (size_t)nprobe * p * sizeof(T);
+    for (int b = 0; b < 4; ++b) ctx->work[b].ensure(vbytes);
+    T* U = ctx->work[0].as<T>();
+    T* W[3] = {ctx->work[1].as<T>(), ctx->work[2].as<T>(), ctx->work[3].as<T>()};
+    const int nred = std::max(nblkC, RED_BLOCKS);
+    ctx->work[4].ensure((size_t)nprobe * nred * sizeof(double));
+    double* part = ctx->work[4].as<double>();
+    ctx->scal.ensure((size_t)nprobe * (2 * nsteps + 4) * sizeof(double) + nprobe * sizeof(double));
+    double* sc = ctx->scal.as<double>();
+    LanczosState S;
+    S.s_cur = sc;
+    S.s_prev = sc + nprobe;
+    S.alpha = sc + 2 * nprobe;
+    S.beta = S.alpha + (size_t)nprobe * nsteps;
+    double* res = S.beta + (size_t)nprobe * nsteps;
+    ctx->work[5].ensure((size_t)nprobe * sizeof(int));
+    S.m_eff = ctx->work[5].as<int>();
+
+    const int tb = 256;
+    k_lanczos_init<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, nprobe, nsteps, 1.0 / sqrt((double)p));
+    KRY_CHECK_LAUNCH();
+    dim3 gp((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nprobe);
+    k_probes<T><<<gp, 256, 0, st>>>(W[0], p, nprobe, 0, seed);
+    KRY_CHECK_LAUNCH();
+    int ip = 2, ic = 0, in = 1;   // W indices: previous, current, next
+    for (int j = 0; j < nsteps; ++j) {
+        matvec_ex<T>(ctx, e, W[ic], p, S.s_cur, U, p, nprobe, part, nblkC);
+        k_lanczos_alpha<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nprobe, nsteps, j);
+        KRY_CHECK_LAUNCH();
+        if (j == nsteps - 1) break;
+        dim3 gu(RED_BLOCKS, nprobe);
+        k_lanczos_update<T><<<gu, 256, 0, st>>>(U, W[ic], W[ip], W[in], p, S, nsteps, j, part);
+        KRY_CHECK_LAUNCH();
+        k_lanczos_beta<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, part, RED_BLOCKS, nprobe, nsteps, j);
+        KRY_CHECK_LAUNCH();
+        const int t = ip;
+        ip = ic;
+        ic = in;
+        in = t;
+    }
+    k_quadrature<<<(nprobe + 63) / 64, 64, 0, st>>>(S, nprobe, nsteps, (double)p, res);
+    KRY_CHECK_LAUNCH();
+    KRY_CUDA(cudaMemcpyAsync(per_probe, res, nprobe * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KRY_CUDA(cudaStreamSynchronize(st));
+}
+
+void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe) {
+    KRY_REQUIRE(nsteps >= 1 && nsteps <= KRY_MAX_STEPS, KRY_EINVAL, "nsteps must be in [1, 256]");
+    KRY_REQUIRE(nprobe >= 1, KRY_EINVAL, "nprobe must be >= 1");
+    if (e->prec == KRY_F64)
+        lanczos_logdet<double>(ctx, e, nprobe, nsteps, seed, per_probe);
+    else
+        lanczos_logdet<float>(ctx, e, nprobe, nsteps, seed, per_probe);
+}
+
+// ------------------------------------------------------------------ CG
+
+struct CgState {
+    double* rr;      // [nrhs] r^T r
+    double* alpha;   // [nrhs]
+    double* beta;    // [nrhs]
+    double* thr2;    // [nrhs] convergence threshold on r^T r
+    int* done;       // [nrhs]
+    int* iters;      // [nrhs]
+    int* ndone;      // [1]
+};
+
+// x = 0, r = b (converted), p = r; partial ||r||^2.
+template <typename T>
+__global__ void k_cg_start(const double* __restrict__ B, int64_t ldb, T* __restrict__ X, T* __restrict__ R,
+                           T* __restrict__ P, int64_t p, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    const int64_t off = (int64_t)k * p;
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const T b = (T)B[(int64_t)k * ldb + i];
+        X[off + i] = (T)0;
+        R[off + i] = b;
+        P[off + i] = b;
+        acc[0] += (double)b * (double)b;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+__global__ void k_cg_init_scalars(CgState S, const double* __restrict__ part, int nblk, int nrhs,
+                                  const double* __restrict__ tol) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+    S.rr[k] = s;
+    S.thr2[k] = tol[k] * tol[k] * s;
+    S.done[k] = (s == 0.0 || s <= S.thr2[k]) ? 1 : 0;
+    S.iters[k] = 0;
+    S.alpha[k] = 0.0;
+    S.beta[k] = 0.0;
+    if (k == 0) *S.ndone = 0;
+}
+
+__global__ void k_cg_alpha(CgState S, const double* __restrict__ part, int nblk, int nrhs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    double pq = 0.0;
+    for (int b = 0; b < nblk; ++b) pq += part[(int64_t)k * nblk + b];
+    S.alpha[k] = (S.done[k] || pq == 0.0) ? 0.0 : S.rr[k] / pq;
+}
+
+// x += alpha p, r -= alpha q; partial ||r||^2.
+template <typename T>
+__global__ void k_cg_update(T* __restrict__ X, T* __restrict__ R, const T* __restrict__ P, const T* __restrict__ Q,
+                            int64_t p, CgState S, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    const int64_t off = (int64_t)k * p;
+    const T a = (T)S.alpha[k];
+    const bool act = !S.done[k];
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        T r = R[off + i];
+        if (act) {
+            X[off + i] += a * P[off + i];
+            r -= a * Q[off + i];
+            R[off + i] = r;
+        }
+        acc[0] += (double)r * (double)r;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+__global__ void k_cg_beta(CgState S, const double* __restrict__ part, int nblk, int nrhs, int maxit) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrhs && !S.done[k]) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+        S.iters[k] += 1;
+        S.beta[k] = s / S.rr[k];
+        S.rr[k] = s;
+        if (s <= S.thr2[k] || !(s == s) || S.iters[k] >= maxit) {
+            S.done[k] = 1;
+            S.beta[k] = 0.0;
+        }
+    } else if (k < nrhs) {
+        S.beta[k] = 0.0;
+    }
+    __syncthreads();
+    if (k == 0) {
+        int nd = 0;
+        for (int i = 0; i < nrhs; ++i) nd += S.done[i];
+        *S.ndone = nd;
+    }
+}
+
+template <typename T>
+__global__ void k_cg_pupdate(T* __restrict__ P, const T* __restrict__ R, int64_t p, CgState S) {
+    const int k = blockIdx.y;
+    if (S.done[k]) return;
+    const int64_t off = (int64_t)k * p;
+    const T b = (T)S.beta[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        P[off + i] = R[off + i] + b * P[off + i];
+}
+
+// Inner CG in precision T on nrhs right-hand sides B (FP64, leading dim ldb),
+// tolerances tol[k] relative to ||B_k||.  Solution X (T, leading dim p) in
+// ctx->work[6].  Returns the largest iteration count.
+template <typename T>
+static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, int nrhs, const double* tol_dev,
+                    int maxit, T** X_out) {
+    const bool dbl = sizeof(T) == 8;
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    const size_t vb = (size_t)nrhs * p * sizeof(T);
+    ctx->work[6].ensure(vb);
+    ctx->work[7].ensure(vb);
+    ctx->work[8].ensure(vb);
+    ctx->work[9].ensure(vb);
+    T* X = ctx->work[6].as<T>();
+    T* R = ctx->work[7].as<T>();
+    T* P = ctx->work[8].as<T>();
+    T* Q = ctx->work[9].as<T>();
+    const int nblkC = matvec_num_partials(ctx, e, dbl);
+    ctx->work[10].ensure((size_t)nrhs * std::max(nblkC, RED_BLOCKS) * sizeof(double));
+    double* part = ctx->work[10].as<double>();
+    ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);
+    char* sb = ctx->work[11].as<char>();
+    CgState S;
+    S.rr = reinterpret_cast<double*>(sb);
+    S.alpha = S.rr + nrhs;
+    S.beta = S.alpha + nrhs;
+    S.thr2 = S.beta + nrhs;
+    S.done = reinterpret_cast<int*>(S.thr2 + nrhs);
+    S.iters = S.done + nrhs;
+    S.ndone = S.iters + nrhs;
+
+    dim3 gv(RED_BLOCKS, nrhs);
+    const int tb = 128;
+    k_cg_start<T><<<gv, 256, 0, st>>>(B, ldb, X, R, P, p, part);
+    KRY_CHECK_LAUNCH();
+    k_cg_init_scalars<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, RED_BLOCKS, nrhs, tol_dev);
+    KRY_CHECK_LAUNCH();
+    int* hdone = reinterpret_cast<int*>(ctx->host_pinned);
+    int it = 0;
+    const int poll = 8;
+    for (; it < maxit; ++it) {
+        matvec_ex<T>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC);
+        k_cg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
+        KRY_CHECK_LAUNCH();
+        k_cg_update<T><<<gv, 256, 0, st>>>(X, R, P, Q, p, S, part);
+        KRY_CHECK_LAUNCH();
+        k_cg_beta<<<1, std::max(32, ((nrhs + 31) / 32) * 32), 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
+        KRY_CHECK_LAUNCH();
+        k_cg_pupdate<T><<<gv, 256, 0, st>>>(P, R, p, S);
+        KRY_CHECK_LAUNCH();
+        if ((it + 1) % poll == 0) {
+            KRY_CUDA(cudaMemcpyAsync(hdone, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
+            KRY_CUDA(cudaStreamSynchronize(st));
+            if (*hdone >= nrhs) {
+                ++it;
+                break;
+            }
+        }
+    }
+    std::vector<int> its(nrhs);
+    KRY_CUDA(cudaMemcpyAsync(hdone, S.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KRY_CUDA(cudaStreamSynchronize(st));
+    int mx = 0;
+    for (int k = 0; k < nrhs; ++k) mx = std::max(mx, hdone[k]);
+    *X_out = X;
+    return mx;
+}
+
+// X64 += (double) D; R64 = B - K X64 (FP64 matvec) and per-column norms.
+template <typename T>
+__global__ void k_accum(double* __restrict__ X, int64_t ldx, const T* __restrict__ D, int64_t p) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)k * ldx + i] += (double)D[(int64_t)k * p + i];
+}
+
+__global__ void k_residual(const double* __restrict__ B, int64_t ldb, const double* __restrict__ KX,
+                           double* __restrict__ R, int64_t p, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const double b = B[(int64_t)k * ldb + i];
+        const double r = b - KX[(int64_t)k * p + i];
+        R[(int64_t)k * p + i] = r;
+        acc[0] += r * r;
+        acc[1] += b * b;
+    }
+    block_sum_store<2>(acc, part + ((int64_t)k * gridDim.x + blockIdx.x) * 2, 1);
+}
+
+__global__ void k_norms_final(const double* __restrict__ part, int nblk, int nrhs, double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < nblk; ++j) {
+        a += part[((int64_t)k * nblk + j) * 2];
+        b += part[((int64_t)k * nblk + j) * 2 + 1];
+    }
+    out[2 * k] = sqrt(a);
+    out[2 * k + 1] = sqrt(b);
+}
+
+__global__ void k_set(double* x, int64_t n, double v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+__global__ void k_zero_cols(double* __restrict__ X, int64_t ldx, int64_t p) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)k * ldx + i] = 0.0;
+}
+
+template <typename T>
+void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+               int64_t ld_out, int nvec, double* dots, int nds);
+
+// FP64 true residual R = B - K X; returns per-column (||R||, ||B||) on the host.
+static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm) {
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    // KX = K X (FP64 matvec); X has leading dimension ldx
+    matvec_ex<double>(ctx, e, X, ldx, nullptr, KX, p, nrhs, nullptr, 0);
+    ctx->red.ensure((size_t)nrhs * RED_BLOCKS * 2 * sizeof(double) + (size_t)nrhs * 2 * sizeof(double));
+    double* part = ctx->red.as<double>();
+    double* fin = part + (size_t)nrhs * RED_BLOCKS * 2;
+    dim3 gv(RED_BLOCKS, nrhs);
+    k_residual<<<gv, 256, 0, st>>>(B, ldb, KX, R, p, part);
+    KRY_CHECK_LAUNCH();
+    k_norms_final<<<(nrhs + 127) / 128, 128, 0, st>>>(part, RED_BLOCKS, nrhs, fin);
+    KRY_CHECK_LAUNCH();
+    nrm.resize(2 * nrhs);
+    KRY_CUDA(cudaMemcpyAsync(nrm.data(), fin, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KRY_CUDA(cudaStreamSynchronize(st));
+}
+
+SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
+                double rtol, int maxit, int refine) {
+    SolveInfo info;
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    KRY_REQUIRE(nrhs >= 1, KRY_EINVAL, "nrhs must be >= 1");
+    KRY_REQUIRE(rtol > 0 && maxit >= 1, KRY_EINVAL, "rtol must be > 0 and maxit >= 1");
+    dim3 gv(RED_BLOCKS, nrhs);
+    // host-side per-column inner tolerances
+    DevBuf& tolbuf = ctx->tolbuf;
+    tolbuf.ensure(nrhs * sizeof(double));
+    std::vector<double> tol_h(nrhs);
+    if (e->prec == KRY_F64) {
+        for (int k = 0; k < nrhs; ++k) tol_h[k] = rtol;
+        KRY_CUDA(cudaMemcpyAsync(tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+        double* Xd;
+        info.iters = cg_inner<double>(ctx, e, B, ldb, nrhs, tolbuf.as<double>(), maxit, &Xd);
+        KRY_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, p * sizeof(double), p * sizeof(double), nrhs,
+                                   cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_zero_cols<<<gv, 256, 0, st>>>(X, ldx, p);
+        KRY_CHECK_LAUNCH();
+    }
+    // FP64 refinement rounds (FP32 embeddings) / final residual (FP64)
+    DevBuf& Rb = ctx->work[4];
+    DevBuf& kxbuf = ctx->kxbuf;
+    kxbuf.ensure((size_t)nrhs * p * sizeof(double));
+    std::vector<double> nrm;
+    const int rounds = (e->prec == KRY_F64) ? 0 : std::max(1, refine + 1);
+    Rb.ensure((size_t)nrhs * p * sizeof(double));
+    double* R = Rb.as<double>();
+    if (e->prec == KRY_F64) {
+        true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
+    } else {
+        // start: R = B, norms
+        true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
+        for (int round = 0; round < rounds; ++round) {
+            bool all = true;
+            for (int k = 0; k < nrhs; ++k) {
+                const double rn = nrm[2 * k], bn = nrm[2 * k + 1];
+                const double rel = bn > 0 ? rn / bn : 0.0;
+                if (rel > rtol) all = false;
+                // inner tolerance relative to the current residual
+                tol_h[k] = (rn > 0) ? std::max(0.5 * rtol * bn / rn, 2e-6) : 1.0;
+            }
+            if (all) break;
+            KRY_CUDA(cudaMemcpyAsync(tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+            float* D;
+            info.iters += cg_inner<float>(ctx, e, R, p, nrhs, tolbuf.as<double>(), maxit, &D);
+            k_accum<float><<<gv, 256, 0, st>>>(X, ldx, D, p);
+            KRY_CHECK_LAUNCH();
+            true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
+        }
+    }
+    info.relres = 0.0;
+    for (int k = 0; k < nrhs; ++k) {
+        const double bn = nrm[2 * k + 1];
+        info.relres = std::max(info.relres, bn > 0 ? nrm[2 * k] / bn : 0.0);
+    }
+    info.converged = info.relres <= rtol * (1.0 + 1e-9);
+    return info;
+}
+
+// ------------------------------------------------------------------ GLS and the log-likelihood
+
+// G[a][b] = V_a^T Z_b for the (ncov+1) columns V = [y, X] and Z = K^-1 V.
+__global__ void k_gram(const double* __restrict__ V, int64_t ldv, const double* __restrict__ Z, int64_t ldz,
+                       int64_t p, int nc, double* __restrict__ part) {
+    const int a = blockIdx.y / nc, b = blockIdx.y % nc;
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += V[(int64_t)a * ldv + i] * Z[(int64_t)b * ldz + i];
+    block_sum_store<1>(acc, part + (int64_t)blockIdx.y * gridDim.x + blockIdx.x, 0);
+}
+
+// beta = (X^T K^-1 X)^-1 X^T K^-1 y by Cholesky of the ncov x ncov matrix;
+// quad = y^T K^-1 y - beta^T X^T K^-1 y; loglik = -1/2 (logdet + quad + p log 2 pi).
+__global__ void k_gls(const double* __restrict__ part, int nblk, int ncov, int64_t p, double logdet,
+                      double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int nc = ncov + 1;
+    double G[KRY_MAX_COV + 1][KRY_MAX_COV + 1];
+    for (int a = 0; a < nc; ++a)
+        for (int b = 0; b < nc; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < nblk; ++j) s += part[(int64_t)(a * nc + b) * nblk + j];
+            G[a][b] = s;
+        }
+    // symmetrise (V^T K^-1 V is symmetric in exact arithmetic)
+    double A[KRY_MAX_COV][KRY_MAX_COV], g[KRY_MAX_COV], L[KRY_MAX_COV][KRY_MAX_COV];
+    for (int a = 0; a < ncov; ++a) {
+        g[a] = 0.5 * (G[a + 1][0] + G[0][a + 1]);
+        for (int b = 0; b < ncov; ++b) A[a][b] = 0.5 * (G[a + 1][b + 1] + G[b + 1][a + 1]);
+    }
+    int ok = 1;
+    for (int j = 0; j < ncov; ++j) {
+        double s = A[j][j];
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0)) {
+            ok = 0;
+            s = 1e-300;
+        }
+        L[j][j] = sqrt(s);
+        for (int i = j + 1; i < ncov; ++i) {
+            double t = A[i][j];
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    double w[KRY_MAX_COV], beta[KRY_MAX_COV];
+    for (int i = 0; i < ncov; ++i) {
+        double t = g[i];
+        for (int k = 0; k < i; ++k) t -= L[i][k] * w[k];
+        w[i] = t / L[i][i];
+    }
+    for (int i = ncov - 1; i >= 0; --i) {
+        double t = w[i];
+        for (int k = i + 1; k < ncov; ++k) t -= L[k][i] * beta[k];
+        beta[i] = t / L[i][i];
+    }
+    double quad = G[0][0];
+    for (int i = 0; i < ncov; ++i) quad -= beta[i] * g[i];
+    const double ll = -0.5 * (logdet + quad + (double)p * 1.8378770664093454836);
+    out[0] = ll;
+    out[1] = quad;
+    out[2] = ok ? 0.0 : 1.0;
+    for (int i = 0; i < ncov; ++i) out[3 + i] = beta[i];
+}
+
+// V = [y, X] (p x (ncov+1), ld p) and Z = K^-1 V already solved.
+GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet) {
+    const int64_t p = ctx->p;
+    const int nc = ncov + 1;
+    cudaStream_t st = ctx->stream;
+    ctx->red.ensure((size_t)nc * nc * RED_BLOCKS * sizeof(double) + 64 * sizeof(double));
+    double* part = ctx->red.as<double>();
+    double* out = part + (size_t)nc * nc * RED_BLOCKS;
+    dim3 g(RED_BLOCKS, nc * nc);
+    k_gram<<<g, 256, 0, st>>>(V, p, Z, p, p, nc, part);
+    KRY_CHECK_LAUNCH();
+    k_gls<<<1, 32, 0, st>>>(part, RED_BLOCKS, ncov, p, logdet, out);
+    KRY_CHECK_LAUNCH();
+    KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, out, (3 + ncov) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KRY_CUDA(cudaStreamSynchronize(st));
+    GlsResult r;
+    r.loglik = ctx->host_pinned[0];
+    r.quad = ctx->host_pinned[1];
+    r.ok = ctx->host_pinned[2] == 0.0;
+    for (int i = 0; i < ncov; ++i) r.beta[i] = ctx->host_pinned[3 + i];
+    return r;
+}
+
+// ------------------------------------------------------------------ kriging helpers
+
+// w = Z[:,0] - Z[:,1:] beta  (K^-1 (y - X beta) without another solve).
+__global__ void k_resid_weights(const double* __restrict__ Z, int64_t p, int ncov, const double* __restrict__ beta,
+                                double* __restrict__ w) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = Z[i];
+        for (int c = 0; c < ncov; ++c) v -= Z[(int64_t)(c + 1) * p + i] * beta[c];
+        w[i] = v;
+    }
+}
+
+// mean[t] = X_t beta + grid[cells[t]]; a cell index outside [0, N) gives NaN
+// and raises *bad.
+__global__ void k_krige_cells(const double* __restrict__ grid, int64_t N, const int64_t* __restrict__ cells,
+                              int64_t ncell, const double* __restrict__ Xc, int ncov, const double* __restrict__ beta,
+                              double* __restrict__ mean, int* __restrict__ bad) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = cells[t];
+        if (cell < 0 || cell >= N) {
+            mean[t] = __longlong_as_double(0x7ff8000000000000ll);
+            *bad = 1;
+            continue;
+        }
+        double m = grid[cell];
+        for (int c = 0; c < ncov; ++c) m += Xc[(int64_t)c * ncell + t] * beta[c];
+        mean[t] = m;
+    }
+}
+
+struct CovPar {
+    double sigma2, inv_range, nu, ca, sa, ratio, dx1, dx2;
+};
+
+// mean[s] = X_s beta + sum_o sigma2 rho(site_s - cell_o) w_o  (one block per site).
+__global__ void k_krige_sites(const double* __restrict__ sites, int64_t nsite, const double* __restrict__ Xs, int ncov,
+                              const double* __restrict__ beta, const double* __restrict__ w,
+                              const int* __restrict__ cellidx, int64_t p, int n2, CovPar cp,
+                              double* __restrict__ mean) {
+    const int64_t s = blockIdx.x;
+    if (s >= nsite) return;
+    const double x1 = sites[2 * s], x2 = sites[2 * s + 1];
+    double acc[1] = {0.0};
+    for (int64_t q = threadIdx.x; q < p; q += blockDim.x) {
+        const int cell = cellidx[q];
+        const int i = cell / n2, j = cell - (cell / n2) * n2;
+        const double h1 = x1 - (i + 0.5) * cp.dx1, h2 = x2 - (j + 0.5) * cp.dx2;
+        const double r = kry_scaled_dist(h1, h2, cp.ca, cp.sa, cp.ratio, cp.inv_range);
+        acc[0] += cp.sigma2 * kry_matern(r, cp.nu) * w[q];
+    }
+    __shared__ double tot;
+    block_sum_store<1>(acc, &tot, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = tot;
+        for (int c = 0; c < ncov; ++c) m += Xs[(int64_t)c * nsite + s] * beta[c];
+        mean[s] = m;
+    }
+}
+
+// Columns of sigma2 Sigma_{obs, t} for a batch of target cells: C[k][q].
+// Target cells are clamped into the grid (k_krige_cells flags bad indices).
+__global__ void k_cross_cols(const int64_t* __restrict__ cells, int64_t t0, const int* __restrict__ cellidx, int64_t p,
+                             int n2, int64_t N, CovPar cp, double* __restrict__ C) {
+    const int k = blockIdx.y;
+    const int64_t t = min(max(cells[t0 + k], (int64_t)0), N - 1);
+    const int ti = (int)(t / n2), tj = (int)(t - (t / n2) * n2);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x) {
+        const int cell = cellidx[q];
+        const int i = cell / n2, j = cell - (cell / n2) * n2;
+        const double r = kry_scaled_dist((i - ti) * cp.dx1, (j - tj) * cp.dx2, cp.ca, cp.sa, cp.ratio, cp.inv_range);
+        C[(int64_t)k * p + q] = cp.sigma2 * kry_matern(r, cp.nu);
+    }
+}
+
+// var[t0 + k] = sigma2 - C_k^T S_k.
+__global__ void k_var_final(const double* __restrict__ C, const double* __restrict__ Sx, int64_t p, double sigma2,
+                            double* __restrict__ var, int64_t t0) {
+    const int k = blockIdx.x;
+    double acc[1] = {0.0};
+    for (int64_t q = threadIdx.x; q < p; q += blockDim.x) acc[0] += C[(int64_t)k * p + q] * Sx[(int64_t)k * p + q];
+    __shared__ double tot;
+    block_sum_store<1>(acc, &tot, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) var[t0 + k] = sigma2 - tot;
+}
+
+CovPar cov_par(const kry_cov& cov, double dx1, double dx2) {
+    CovPar c;
+    c.sigma2 = cov.sigma2;
+    c.inv_range = 1.0 / cov.range;
+    c.nu = cov.nu;
+    c.ca = cos(cov.aniso_angle);
+    c.sa = sin(cov.aniso_angle);
+    c.ratio = cov.aniso_ratio;
+    c.dx1 = dx1;
+    c.dx2 = dx2;
+    return c;
+}
+
+void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, int64_t ncell, const double* Xc,
+                        int ncov, const double* beta_dev, double* mean, int* bad) {
+    if (ncell <= 0) return;
+    k_krige_cells<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        grid, (int64_t)ctx->n1 * ctx->n2, cells, ncell, Xc, ncov, beta_dev, mean, bad);
+    KRY_CHECK_LAUNCH();
+}
+
+void krige_launch_sites(kry_ctx* ctx, const kry_cov& cov, const double* sites, int64_t nsite, const double* Xs,
+                        int ncov, const double* beta_dev, const double* w, double* mean) {
+    if (nsite <= 0) return;
+    k_krige_sites<<<(unsigned)nsite, 256, 0, ctx->stream>>>(sites, nsite, Xs, ncov, beta_dev, w,
+                                                           ctx->cellidx.as<int>(), ctx->p, ctx->n2,
+                                                           cov_par(cov, ctx->dx1, ctx->dx2), mean);
+    KRY_CHECK_LAUNCH();
+}
+
+void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_dev, double* w) {
+    k_resid_weights<<<(unsigned)std::min<int64_t>((ctx->p + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        Z, ctx->p, ncov, beta_dev, w);
+    KRY_CHECK_LAUNCH();
+}
+
+// Simple-kriging variances at target cells, nb targets per batch of solves.
+bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
+                     double rtol, int maxit, int refine) {
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    const int nb = 32;
+    DevBuf& cbuf = ctx->cbuf;
+    DevBuf& sbuf = ctx->sbuf;
+    cbuf.ensure((size_t)nb * p * sizeof(double));
+    sbuf.ensure((size_t)nb * p * sizeof(double));
+    bool ok = true;
+    const CovPar cp = cov_par(e->cov, ctx->dx1, ctx->dx2);
+    for (int64_t t0 = 0; t0 < ncell; t0 += nb) {
+        const int k = (int)std::min<int64_t>(nb, ncell - t0);
+        dim3 g((unsigned)std::min<int64_t>((p + 255) / 256, 1024), k);
+        k_cross_cols<<<g, 256, 0, st>>>(cells, t0, ctx->cellidx.as<int>(), p, ctx->n2, (int64_t)ctx->n1 * ctx->n2, cp,
+                                         cbuf.as<double>());
+        KRY_CHECK_LAUNCH();
+        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit, refine);
+        ok = ok && si.converged;
+        k_var_final<<<k, 256, 0, st>>>(cbuf.as<double>(), sbuf.as<double>(), p, e->cov.sigma2, var, t0);
+        KRY_CHECK_LAUNCH();
+    }
+    return ok;
+}
+
+}  // namespace kry

@@ -1,0 +1,381 @@
+// BTTB covariance matvec by circulant embedding (Sec. 3: Sigma is symmetric
+// BTTB, stored through one row and applied in O(n log n) with FFTs; the
+// embedding's eigenvalues diagonalise it, Appendix A Eq. circ_diag):
+//
+//   K v = A F^-1 ( Lambda .* F ( A^T v ) ) + tau^2 v
+//
+// on the M1 x M2 torus, A the observation mask.  Two real vectors travel as
+// the real and imaginary parts of one complex field; that is exact because
+// Lambda is real and even.  The 2-D transform is split into three kernels:
+//
+//   pass A  per grid row i < n1: scatter the observed values of the row into
+//           a zero row of length M2 in shared memory, forward FFT, store the
+//           row into the intermediate slab (n1 x M2 complex per pair);
+//   pass B  per tile of C columns: load the n1 nonzero rows of each column,
+//           forward FFT of length M1, multiply by Lambda (scaled by
+//           1/(M1 M2)), inverse FFT, store the first n1 rows back;
+//   pass C  per grid row: inverse FFT of length M2, gather the observed
+//           columns, add the nugget term, and (optionally) accumulate the
+//           FP64 dot product of input and output for the Krylov loops.
+//
+// The slab is laid out in column tiles, slab[pair][tile][i][c] with
+// c < C, so that pass B reads and writes one contiguous block per CTA and
+// passes A and C touch G*C contiguous elements per tile for G rows per CTA.
+#include <algorithm>
+
+#include "fft.cuh"
+#include "kry_internal.cuh"
+
+namespace kry {
+
+// ------------------------------------------------------------------ pass A
+
+template <typename T, int EPT, int G>
+__global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_a(const T* __restrict__ vin, int64_t ld, const double* __restrict__ scale,
+                                                 int nvec, int pair0, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ colidx, int n1, int M2, int C,
+                                                 typename cx_of<T>::type* __restrict__ slab, const void* tw32,
+                                                 const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    const int L = M2;
+    const int stride = L + 1;
+    const int LT = L / EPT;
+    const int g = threadIdx.x / LT;
+    const int tl = threadIdx.x - g * LT;
+    const int row0 = blockIdx.x * G;
+    const int row = row0 + g;
+    const int pair = pair0 + blockIdx.y;
+    const int va = 2 * pair, vb = 2 * pair + 1;
+    const bool has_b = vb < nvec;
+    Cx* rb = buf + g * stride;
+
+    for (int k = tl; k < L; k += LT) rb[k] = cmk<Cx>((T)0, (T)0);
+    __syncthreads();
+    if (row < n1) {
+        const T sa = scale ? (T)scale[va] : (T)1;
+        const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
+        const T* pa = vin + (int64_t)va * ld;
+        const T* pb = vin + (int64_t)vb * ld;
+        const int q1 = rowptr[row + 1];
+        for (int q = rowptr[row] + tl; q < q1; q += LT) {
+            const int c = colidx[q];
+            const T a = pa[q] * sa;
+            const T b = has_b ? pb[q] * sb : (T)0;
+            rb[c] = cmk<Cx>(a, b);
+        }
+    }
+    __syncthreads();
+    fft_smem<Cx, false, EPT>(rb, L, tl, twiddles<T>(tw32, tw64));
+
+    // store: slab[pair][tile][row][c]
+    Cx* out = slab + (int64_t)blockIdx.y * n1 * M2;
+    const int GC = G * C;
+    for (int e = threadIdx.x; e < G * L; e += blockDim.x) {
+        const int tile = e / GC;
+        const int rem = e - tile * GC;
+        const int gg = rem / C;
+        const int c = rem - gg * C;
+        const int r = row0 + gg;
+        if (r < n1) out[(int64_t)tile * n1 * C + (int64_t)r * C + c] = buf[gg * stride + tile * C + c];
+    }
+}
+
+// ------------------------------------------------------------------ pass B
+
+template <typename T, int EPT, int CC>
+__global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_b(typename cx_of<T>::type* __restrict__ slab, const T* __restrict__ lamT,
+                                                 int n1, int M1, int M2, const void* tw32, const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    const int L = M1;
+    const int stride = L + 1;
+    const int LT = L / EPT;
+    const int g = threadIdx.x / LT;
+    const int tl = threadIdx.x - g * LT;
+    const int tile = blockIdx.x;
+    Cx* blk = slab + (int64_t)blockIdx.y * n1 * M2 + (int64_t)tile * n1 * CC;
+
+    const int nload = n1 * CC;
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+        const int i = e / CC;
+        const int c = e - i * CC;
+        buf[c * stride + i] = blk[e];
+    }
+    for (int e = threadIdx.x; e < (L - n1) * CC; e += blockDim.x) {
+        const int c = e / (L - n1);
+        const int i = n1 + (e - c * (L - n1));
+        buf[c * stride + i] = cmk<Cx>((T)0, (T)0);
+    }
+    __syncthreads();
+    Cx* cb = buf + g * stride;
+    const Cx* tw = twiddles<T>(tw32, tw64);
+    fft_smem<Cx, false, EPT>(cb, L, tl, tw);
+    const T* lam = lamT + (int64_t)(tile * CC + g) * L;
+    for (int k = tl; k < L; k += LT) {
+        const T l = lam[k];
+        Cx z = cb[k];
+        cb[k] = cmk<Cx>(z.x * l, z.y * l);
+    }
+    __syncthreads();
+    fft_smem<Cx, true, EPT>(cb, L, tl, tw);
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+        const int i = e / CC;
+        const int c = e - i * CC;
+        blk[e] = buf[c * stride + i];
+    }
+}
+
+// ------------------------------------------------------------------ pass C
+
+// MODE 0: gather the observed cells, add tau2 * (scaled input), optional dot.
+// MODE 1: write every grid cell (n1 x n2 row-major) per vector, no nugget.
+template <typename T, int EPT, int G, int MODE>
+__global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typename cx_of<T>::type* __restrict__ slab, const T* __restrict__ vin,
+                                                 int64_t ld_in, const double* __restrict__ scale, T* __restrict__ vout,
+                                                 int64_t ld_out, int nvec, int pair0, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ colidx, int n1, int n2, int M2, int C,
+                                                 double tau2, double* __restrict__ dots, int ndot_stride,
+                                                 const void* tw32, const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    __shared__ double red[2][32];
+    const int L = M2;
+    const int stride = L + 1;
+    const int LT = L / EPT;
+    const int g = threadIdx.x / LT;
+    const int tl = threadIdx.x - g * LT;
+    const int row0 = blockIdx.x * G;
+    const int pair = pair0 + blockIdx.y;
+    const int va = 2 * pair, vb = 2 * pair + 1;
+    const bool has_b = vb < nvec;
+
+    const Cx* in = slab + (int64_t)blockIdx.y * n1 * M2;
+    const int GC = G * C;
+    for (int e = threadIdx.x; e < G * L; e += blockDim.x) {
+        const int tile = e / GC;
+        const int rem = e - tile * GC;
+        const int gg = rem / C;
+        const int c = rem - gg * C;
+        const int r = row0 + gg;
+        buf[gg * stride + tile * C + c] =
+            (r < n1) ? in[(int64_t)tile * n1 * C + (int64_t)r * C + c] : cmk<Cx>((T)0, (T)0);
+    }
+    __syncthreads();
+    Cx* rb = buf + g * stride;
+    fft_smem<Cx, true, EPT>(rb, L, tl, twiddles<T>(tw32, tw64));
+
+    const int row = row0 + g;
+    double da = 0.0, db = 0.0;
+    if (row < n1) {
+        if (MODE == 0) {
+            const T sa = scale ? (T)scale[va] : (T)1;
+            const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
+            const T t2 = (T)tau2;
+            const T* pa = vin + (int64_t)va * ld_in;
+            const T* pb = vin + (int64_t)vb * ld_in;
+            T* oa = vout + (int64_t)va * ld_out;
+            T* ob = vout + (int64_t)vb * ld_out;
+            const int q1 = rowptr[row + 1];
+            for (int q = rowptr[row] + tl; q < q1; q += LT) {
+                const Cx z = rb[colidx[q]];
+                const T xa = pa[q] * sa;
+                const T ya = z.x + t2 * xa;
+                oa[q] = ya;
+                da += (double)xa * (double)ya;
+                if (has_b) {
+                    const T xb = pb[q] * sb;
+                    const T yb = z.y + t2 * xb;
+                    ob[q] = yb;
+                    db += (double)xb * (double)yb;
+                }
+            }
+        } else {
+            T* oa = vout + (int64_t)va * ld_out + (int64_t)row * n2;
+            T* ob = vout + (int64_t)vb * ld_out + (int64_t)row * n2;
+            for (int j = tl; j < n2; j += LT) {
+                const Cx z = rb[j];
+                oa[j] = z.x;
+                if (has_b) ob[j] = z.y;
+            }
+        }
+    }
+    if (MODE == 0 && dots != nullptr) {
+        // block reduction of (da, db) in a fixed order
+        for (int o = 16; o > 0; o >>= 1) {
+            da += __shfl_down_sync(0xffffffffu, da, o);
+            db += __shfl_down_sync(0xffffffffu, db, o);
+        }
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            red[0][w] = da;
+            red[1][w] = db;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sa = 0.0, sb = 0.0;
+            const int nw = blockDim.x >> 5;
+            for (int k = 0; k < nw; ++k) {
+                sa += red[0][k];
+                sb += red[1][k];
+            }
+            dots[(int64_t)va * ndot_stride + blockIdx.x] = sa;
+            if (has_b) dots[(int64_t)vb * ndot_stride + blockIdx.x] = sb;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static size_t cx_size(bool dbl) { return dbl ? sizeof(double2) : sizeof(float2); }
+
+int smem_limit(kry_ctx* ctx) { return ctx->max_smem_optin; }
+
+template <typename T>
+struct MvLaunch {
+    using Cx = typename cx_of<T>::type;
+
+    template <int EPT, int G>
+    static void a(dim3 grid, int threads, size_t smem, cudaStream_t s, const T* vin, int64_t ld, const double* scale,
+                  int nvec, int pair0, const int* rowptr, const int* colidx, int n1, int M2, int C, Cx* slab,
+                  const void* tw32, const void* tw64) {
+        auto k = k_pass_a<T, EPT, G>;
+        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, threads, smem, s>>>(vin, ld, scale, nvec, pair0, rowptr, colidx, n1, M2, C, slab, tw32, tw64);
+        KRY_CHECK_LAUNCH();
+    }
+    template <int EPT, int CC>
+    static void b(dim3 grid, int threads, size_t smem, cudaStream_t s, Cx* slab, const T* lamT, int n1, int M1, int M2,
+                  const void* tw32, const void* tw64) {
+        auto k = k_pass_b<T, EPT, CC>;
+        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, threads, smem, s>>>(slab, lamT, n1, M1, M2, tw32, tw64);
+        KRY_CHECK_LAUNCH();
+    }
+    template <int EPT, int G, int MODE>
+    static void c(dim3 grid, int threads, size_t smem, cudaStream_t s, const Cx* slab, const T* vin, int64_t ld_in,
+                  const double* scale, T* vout, int64_t ld_out, int nvec, int pair0, const int* rowptr,
+                  const int* colidx, int n1, int n2, int M2, int C, double tau2, double* dots, int nds,
+                  const void* tw32, const void* tw64) {
+        auto k = k_pass_c<T, EPT, G, MODE>;
+        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<grid, threads, smem, s>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2,
+                                      C, tau2, dots, nds, tw32, tw64);
+        KRY_CHECK_LAUNCH();
+    }
+};
+
+#define KRY_DISPATCH_EG(EPTV, GV, CALL)                                               \
+    do {                                                                              \
+        if (EPTV == 8) {                                                              \
+            if (GV == 1) { constexpr int E_ = 8, G_ = 1; CALL; }                       \
+            else if (GV == 2) { constexpr int E_ = 8, G_ = 2; CALL; }                  \
+            else if (GV == 4) { constexpr int E_ = 8, G_ = 4; CALL; }                  \
+            else if (GV == 8) { constexpr int E_ = 8, G_ = 8; CALL; }                  \
+            else throw KryError{KRY_EUNSUPPORTED, "bad group count"};                \
+        } else if (EPTV == 16) {                                                      \
+            if (GV == 1) { constexpr int E_ = 16, G_ = 1; CALL; }                      \
+            else if (GV == 2) { constexpr int E_ = 16, G_ = 2; CALL; }                 \
+            else if (GV == 4) { constexpr int E_ = 16, G_ = 4; CALL; }                 \
+            else if (GV == 8) { constexpr int E_ = 16, G_ = 8; CALL; }                 \
+            else throw KryError{KRY_EUNSUPPORTED, "bad group count"};                \
+        } else                                                                        \
+            throw KryError{KRY_EUNSUPPORTED, "bad elements per thread"};              \
+    } while (0)
+
+// Pick a schedule that fits shared memory and the 1024-thread block limit.
+static MvSched pick_sched(kry_ctx* ctx, const MvSched& want, int M1, int M2, bool dbl) {
+    MvSched s = want;
+    const size_t cs = cx_size(dbl);
+    const size_t lim = (size_t)ctx->max_smem_optin;
+    auto fix = [&](int& ept, int& grp, int L) {
+        if (ept != 8 && ept != 16) ept = 8;
+        if (L < ept) ept = 8;
+        if (L / ept > 1024) ept = 16;
+        const int maxthr = (ept >= 16) ? 512 : 1024;
+        while (grp > 1 && ((size_t)grp * (L + 1) * cs > lim || grp * (L / ept) > maxthr)) grp /= 2;
+    };
+    fix(s.ept_row, s.rows_per_cta, M2);
+    fix(s.ept_col, s.cols_per_cta, M1);
+    return s;
+}
+
+template <typename T>
+static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode) {
+    using Cx = typename cx_of<T>::type;
+    const bool dbl = sizeof(T) == 8;
+    const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
+    MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, M1, M2, dbl);
+    const int npairs = (nvec + 1) / 2;
+    int ppb = s.pairs_per_batch > 0 ? std::min(s.pairs_per_batch, npairs) : npairs;
+    const size_t slab_pair = (size_t)n1 * M2 * cx_size(dbl);
+    DevBuf& sb = dbl ? ctx->slab64 : ctx->slab32;
+    sb.ensure(slab_pair * ppb);
+    Cx* slab = sb.as<Cx>();
+    const T* lamT = dbl ? reinterpret_cast<const T*>(e->lam64T) : reinterpret_cast<const T*>(e->lam32T);
+    const int C = s.cols_per_cta;
+    const int G = s.rows_per_cta;
+    const int* rowptr = ctx->rowptr.as<int>();
+    const int* colidx = ctx->colidx.as<int>();
+    const void* tw32 = ctx->tw32.p;
+    const void* tw64 = ctx->tw64.p;
+    cudaStream_t st = ctx->stream;
+    const int thrA = G * (M2 / s.ept_row);
+    const size_t smA = (size_t)G * (M2 + 1) * cx_size(dbl);
+    const int thrB = C * (M1 / s.ept_col);
+    const size_t smB = (size_t)C * (M1 + 1) * cx_size(dbl);
+    const int nbx = (n1 + G - 1) / G;
+    for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
+        const int np = std::min(ppb, npairs - pair0);
+        dim3 gA(nbx, np), gB(M2 / C, np);
+        KRY_DISPATCH_EG(s.ept_row, G,
+                        (MvLaunch<T>::template a<E_, G_>(gA, thrA, smA, st, vin, ld_in, scale, nvec, pair0, rowptr,
+                                                         colidx, n1, M2, C, slab, tw32, tw64)));
+        KRY_DISPATCH_EG(s.ept_col, C,
+                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64)));
+        if (mode == 0) {
+            KRY_DISPATCH_EG(s.ept_row, G,
+                            (MvLaunch<T>::template c<E_, G_, 0>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
+                                                                ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
+                                                                tau2, dots, nds, tw32, tw64)));
+        } else {
+            KRY_DISPATCH_EG(s.ept_row, G,
+                            (MvLaunch<T>::template c<E_, G_, 1>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
+                                                                ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
+                                                                tau2, dots, nds, tw32, tw64)));
+        }
+    }
+}
+
+int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl) {
+    MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, e->M1, e->M2, dbl);
+    return (e->n1 + s.rows_per_cta - 1) / s.rows_per_cta;
+}
+
+template <typename T>
+void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+               int64_t ld_out, int nvec, double* dots, int nds) {
+    run_matvec<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, e->cov.tau2, dots, nds, 0);
+}
+
+template void matvec_ex<float>(kry_ctx*, const kry_embed*, const float*, int64_t, const double*, float*, int64_t, int,
+                               double*, int);
+template void matvec_ex<double>(kry_ctx*, const kry_embed*, const double*, int64_t, const double*, double*, int64_t,
+                                int, double*, int);
+
+template <typename T>
+void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld, double) {
+    run_matvec<T>(ctx, e, vin, ld, nullptr, vout, ld, nvec, e->cov.tau2, nullptr, 0, 0);
+}
+template void matvec<float>(kry_ctx*, const kry_embed*, const float*, float*, int, int64_t, double);
+template void matvec<double>(kry_ctx*, const kry_embed*, const double*, double*, int, int64_t, double);
+
+void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double* out_grid, int nvec, int64_t ld) {
+    run_matvec<double>(ctx, e, vin, ld, nullptr, out_grid, (int64_t)e->n1 * e->n2, nvec, 0.0, nullptr, 0, 1);
+}
+
+}  // namespace kry

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of the Kryging C ABI (``include/kry.h``).
+
+Argument marshalling only: every step of the hot path runs in ``libkry.so``.
+Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed through);
+host outputs are NumPy arrays.  Importing this module loads the library and
+fails loudly if it has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkry.so")
+
+KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ENOTPSD, KRY_ENOCONV, KRY_ENAN, KRY_ETIMEOUT, KRY_ECUDA, KRY_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["KRY_OK", "KRY_EINVAL", "KRY_ENOMEM", "KRY_ENOTPSD", "KRY_ENOCONV", "KRY_ENAN", "KRY_ETIMEOUT",
+                "KRY_ECUDA", "KRY_EUNSUPPORTED"]
+KRY_F32, KRY_F64 = 0, 1
+
+
+class KryError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class kry_grid(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("dx1", C.c_double), ("dx2", C.c_double)]
+
+
+class kry_cov(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("range", C.c_double), ("nu", C.c_double), ("tau2", C.c_double),
+                ("aniso_angle", C.c_double), ("aniso_ratio", C.c_double)]
+
+
+class kry_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("nprobe", C.c_int32), ("nsteps", C.c_int32), ("seed", C.c_uint64),
+                ("rtol", C.c_double), ("maxit", C.c_int32), ("refine", C.c_int32)]
+
+
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "kry_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "kry_destroy": (None, [_P]),
+    "kry_last_error": (C.c_char_p, [_P]),
+    "kry_set_mask": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.POINTER(C.c_int64)]),
+    "kry_embed_eigs": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.POINTER(_P), _DP]),
+    "kry_embed_free": (None, [_P]),
+    "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
+    "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, _DP, _DP, _DP]),
+    "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32, C.c_int32,
+                            C.POINTER(C.c_int32), _DP]),
+    "kry_profile_loglik": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(kry_cov), C.c_int32, C.POINTER(kry_opts),
+                                     _DP, _DP, _DP, _DP]),
+    "kry_krige": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), _P, _P, C.c_int32, _P, _P, C.c_int64,
+                            _P, _P, C.c_int64, _P, _P, _P, _DP]),
+    "kry_sample": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int32, C.c_int32, _P, _P]),
+    "kry_sample_size": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2012_13133_gb300.build.build_library() "
+                           "(the Kryging path has no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def make_cov(cov) -> kry_cov:
+    """Accepts a kry_cov, or any object with sigma2, range, nu, tau2 (and optional angle, ratio)."""
+    if isinstance(cov, kry_cov):
+        return cov
+    return kry_cov(float(cov.sigma2), float(cov.range), float(cov.nu), float(cov.tau2),
+                   float(getattr(cov, "angle", 0.0)), float(getattr(cov, "ratio", 1.0)))
+
+
+@dataclass
+class Opts:
+    prec: int = KRY_F32
+    nprobe: int = 16
+    nsteps: int = 50
+    seed: int = 0
+    rtol: float = 1e-6
+    maxit: int = 5000
+    refine: int = 4
+
+    def c(self) -> kry_opts:
+        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.refine)
+
+
+class Embed:
+    def __init__(self, ctx, handle, min_over_max, prec):
+        self.ctx, self.handle, self.min_over_max, self.prec = ctx, handle, min_over_max, prec
+
+    def free(self):
+        if self.handle:
+            _lib.kry_embed_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """One library context on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        st = _lib.kry_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if st != KRY_OK:
+            raise KryError(st, "kry_create failed")
+        self.h = h
+        self.p = 0
+        self.n1 = self.n2 = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.kry_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != KRY_OK and st not in allow:
+            raise KryError(st, _lib.kry_last_error(self.h).decode())
+        return st
+
+    # -- observation pattern
+    def set_mask(self, mask, dx1=None, dx2=None) -> int:
+        """mask: torch uint8 CUDA tensor (n1, n2), nonzero = observed."""
+        n1, n2 = mask.shape
+        g = kry_grid(n1, n2, 1.0 / n1 if dx1 is None else dx1, 1.0 / n2 if dx2 is None else dx2)
+        p = C.c_int64()
+        self._check(_lib.kry_set_mask(self.h, C.byref(g), _ptr(mask.contiguous()), C.byref(p)))
+        self.p, self.n1, self.n2 = int(p.value), n1, n2
+        return self.p
+
+    # -- embedding
+    def embed(self, cov, prec=KRY_F32) -> Embed:
+        c = make_cov(cov)
+        e = C.c_void_p()
+        r = C.c_double()
+        self._check(_lib.kry_embed_eigs(self.h, C.byref(c), prec, C.byref(e), C.byref(r)))
+        return Embed(self, e, r.value, prec)
+
+    # -- matvec
+    def matvec(self, emb: Embed, v, out=None):
+        """v: (nvec, p) or (p,) CUDA tensor (float32 for KRY_F32, float64 for KRY_F64)."""
+        squeeze = v.dim() == 1
+        V = v.reshape(1, -1) if squeeze else v
+        assert V.is_contiguous() and V.shape[1] == self.p
+        if out is None:
+            out = self.torch.empty_like(V)
+        self._check(_lib.kry_matvec(self.h, emb.handle, _ptr(V), _ptr(out), V.shape[0], self.p))
+        return out.reshape(-1) if squeeze else out
+
+    def logdet(self, emb: Embed, nprobe: int, nsteps: int, seed: int):
+        ld, se = C.c_double(), C.c_double()
+        per = np.zeros(nprobe)
+        self._check(_lib.kry_logdet(self.h, emb.handle, nprobe, nsteps, C.c_uint64(seed), C.byref(ld), C.byref(se),
+                                    _np_dp(per)))
+        return ld.value, se.value, per
+
+    def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, refine=4, X=None):
+        """B: (nrhs, p) float64 CUDA tensor.  Returns (X, iters, relres, status)."""
+        squeeze = B.dim() == 1
+        Bm = B.reshape(1, -1) if squeeze else B
+        if X is None:
+            X = self.torch.empty_like(Bm)
+        it, rr = C.c_int32(), C.c_double()
+        st = self._check(_lib.kry_solve(self.h, emb.handle, _ptr(Bm), _ptr(X), Bm.shape[0], self.p, rtol, maxit,
+                                        refine, C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
+        return (X.reshape(-1) if squeeze else X), it.value, rr.value, st
+
+    def profile_loglik(self, y, X, thetas, opts: Opts):
+        """y: (p,) float64 CUDA; X: (ncov, p) float64 CUDA (column-major p x ncov)."""
+        ncov = X.shape[0]
+        n = len(thetas)
+        arr = (kry_cov * n)(*[make_cov(t) for t in thetas])
+        ll, beta, ld, se = np.zeros(n), np.zeros(n * ncov), np.zeros(n), np.zeros(n)
+        o = opts.c()
+        st = self._check(_lib.kry_profile_loglik(self.h, _ptr(y), _ptr(X), ncov, arr, n, C.byref(o), _np_dp(ll),
+                                                 _np_dp(beta), _np_dp(ld), _np_dp(se)), allow=(KRY_ENOCONV,))
+        return dict(loglik=ll, beta=beta.reshape(n, ncov), logdet=ld, logdet_se=se, status=st)
+
+    def krige(self, cov, opts: Opts, y, X, cells=None, Xc=None, sites=None, Xs=None, variances=False):
+        """cells: (ncell,) int64 CUDA; Xc: (ncov, ncell) float64; sites: (nsite, 2) float64; Xs: (ncov, nsite)."""
+        torch = self.torch
+        ncov = X.shape[0]
+        ncell = 0 if cells is None else cells.shape[0]
+        nsite = 0 if sites is None else sites.shape[0]
+        dev = y.device
+        mc = torch.empty(ncell, dtype=torch.float64, device=dev) if ncell else None
+        ms = torch.empty(nsite, dtype=torch.float64, device=dev) if nsite else None
+        vc = torch.empty(ncell, dtype=torch.float64, device=dev) if (ncell and variances) else None
+        beta = np.zeros(ncov)
+        c = make_cov(cov)
+        o = opts.c()
+        st = self._check(_lib.kry_krige(self.h, C.byref(c), C.byref(o), _ptr(y), _ptr(X), ncov, _ptr(cells), _ptr(Xc),
+                                        ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms), _ptr(vc),
+                                        _np_dp(beta)), allow=(KRY_ENOCONV,))
+        return dict(mean_cells=mc, mean_sites=ms, var_cells=vc, beta=beta, status=st)
+
+    def sample_size(self, cov):
+        m1, m2 = C.c_int32(), C.c_int32()
+        st = self._check(_lib.kry_sample_size(self.h, C.byref(make_cov(cov)), C.byref(m1), C.byref(m2)),
+                         allow=(KRY_ENOTPSD,))
+        return m1.value, m2.value, st
+
+    def sample(self, cov, M1, M2, xi):
+        """xi: (2, M1, M2) float64 CUDA normals.  Returns the (n1, n2) float64 field."""
+        out = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=xi.device)
+        self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, _ptr(xi.contiguous()), _ptr(out)))
+        return out

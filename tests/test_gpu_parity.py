@@ -1,0 +1,319 @@
+"""GPU parity of the CUDA path against the FP64 oracle, element by element on
+the same seeded inputs.  Tolerances: matvec relative l2 error <= 1e-12 (FP64)
+and <= 1e-5 (FP32); log-det <= 1e-3 relative against the oracle with the same
+probes; kriging mean <= 1e-4 relative l2."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kryoracle as O
+from paper_2012_13133_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2012_13133_gb300 import kry  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = kry.Context(0)
+    yield c
+    c.close()
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def set_mask(ctx, mask):
+    return ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(DEV))
+
+
+MV_CASES = [
+    # n1, n2, cov, frac_missing, mask kind
+    (8, 8, I.Cov(1.0, 0.2, 0.5, 0.1), 0.0, "uniform"),
+    (32, 32, I.Cov(1.0, 0.1, 0.5, 0.1), 0.0, "uniform"),
+    (37, 53, I.Cov(2.0, 0.15, 1.5, 0.05), 0.4, "uniform"),
+    (64, 40, I.Cov(1.0, 0.1, 1.0, 0.2), 0.5, "circles"),
+    (50, 70, I.Cov(1.0, 0.08, 0.5, 0.05, angle=math.radians(30), ratio=3.0), 0.3, "circles"),
+    (128, 128, I.Cov(1.0, 0.05, 2.5, 0.01), 0.5, "uniform"),
+    (300, 260, I.Cov(1.0, 0.05, 1.5, 0.05), 0.5, "uniform"),
+    (4, 4, I.Cov(1.0, 0.5, 0.5, 0.1), 0.25, "uniform"),
+]
+
+
+def make_mask(n1, n2, frac, kind, seed=3):
+    if frac == 0.0:
+        return I.mask_full(n1, n2)
+    if kind == "circles":
+        return I.mask_circles(n1, n2, frac, seed)
+    return I.mask_uniform(n1, n2, frac, seed)
+
+
+@pytest.mark.parametrize("n1,n2,cov,frac,kind", MV_CASES)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_parity(ctx, n1, n2, cov, frac, kind, prec):
+    mask = make_mask(n1, n2, frac, kind)
+    p = set_mask(ctx, mask)
+    assert p == int(mask.sum())
+    P = O.FFTProblem(n1, n2, mask, cov)
+    nvec = 5   # odd: the last complex pair carries one real vector
+    V = I.normals((nvec, p), 11)
+    ref = P.matvec(V)
+    if prec == "f64":
+        emb = ctx.embed(cov, kry.KRY_F64)
+        out = ctx.matvec(emb, torch.tensor(V, device=DEV)).cpu().numpy()
+        tol = 1e-12
+    else:
+        emb = ctx.embed(cov, kry.KRY_F32)
+        out = ctx.matvec(emb, torch.tensor(V, dtype=torch.float32, device=DEV)).double().cpu().numpy()
+        tol = 1e-5
+    for k in range(nvec):
+        assert relerr(out[k], ref[k]) <= tol, (k, relerr(out[k], ref[k]))
+    # min / max eigenvalue report (no clamping)
+    assert emb.min_over_max == pytest.approx(P.lam.min() / P.lam.max(), rel=1e-9, abs=1e-13)
+    emb.free()
+
+
+def test_matvec_matches_dense_brute_force(ctx):
+    n1, n2 = 12, 9
+    cov = I.Cov(1.3, 0.3, 1.0, 0.07)
+    mask = I.mask_uniform(n1, n2, 0.3, 5)
+    p = set_mask(ctx, mask)
+    K = O.dense_K(n1, n2, mask, cov)
+    V = I.normals((2, p), 2)
+    emb = ctx.embed(cov, kry.KRY_F64)
+    out = ctx.matvec(emb, torch.tensor(V, device=DEV)).cpu().numpy()
+    for k in range(2):
+        assert relerr(out[k], K @ V[k]) <= 1e-12
+
+
+def test_matvec_special_cases(ctx):
+    n1, n2 = 16, 16
+    mask = I.mask_uniform(n1, n2, 0.2, 9)
+    p = set_mask(ctx, mask)
+    # sigma2 = 0: K v = tau2 v exactly
+    emb = ctx.embed(I.Cov(0.0, 0.2, 1.5, 0.3), kry.KRY_F64)
+    v = torch.tensor(I.normals(p, 1), device=DEV)
+    out = ctx.matvec(emb, v)
+    assert torch.equal(out, 0.3 * v)
+    # symmetry u^T K v = v^T K u
+    emb = ctx.embed(I.Cov(1.0, 0.2, 1.5, 0.1), kry.KRY_F64)
+    u = torch.tensor(I.normals(p, 2), device=DEV)
+    a = float(u @ ctx.matvec(emb, v))
+    b = float(v @ ctx.matvec(emb, u))
+    assert a == pytest.approx(b, rel=1e-13)
+    # delta vector gives a column of K
+    K = O.dense_K(n1, n2, mask, I.Cov(1.0, 0.2, 1.5, 0.1))
+    e = torch.zeros(p, dtype=torch.float64, device=DEV)
+    e[7] = 1.0
+    assert np.allclose(ctx.matvec(emb, e).cpu().numpy(), K[:, 7], rtol=0, atol=1e-14)
+    # a single observed cell
+    one = np.zeros((n1, n2), bool)
+    one[3, 5] = True
+    assert set_mask(ctx, one) == 1
+    emb = ctx.embed(I.Cov(1.0, 0.2, 1.5, 0.1), kry.KRY_F64)
+    out = ctx.matvec(emb, torch.tensor([2.0], dtype=torch.float64, device=DEV))
+    assert float(out[0]) == pytest.approx(2.0 * 1.1, rel=1e-13)
+    # zero vectors: no-op
+    out0 = ctx.matvec(emb, torch.zeros((0, 1), dtype=torch.float64, device=DEV))
+    assert out0.shape == (0, 1)
+
+
+def test_bessel_general_nu_against_table_and_scipy(ctx):
+    # nu = 1: Matern(r) = x K_1(x), x = sqrt(2) r.  A 1 x 2 lag set comes from a
+    # delta-vector matvec on a row of cells.
+    import scipy.special as sp
+    n1, n2 = 4, 64
+    mask = I.mask_full(n1, n2)
+    p = set_mask(ctx, mask)
+    for nu in [0.3, 1.0, 1.7, 3.2]:
+        cov = I.Cov(1.0, 0.05, nu, 0.0)
+        emb = ctx.embed(cov, kry.KRY_F64)
+        e = torch.zeros(p, dtype=torch.float64, device=DEV)
+        e[0] = 1.0
+        col = ctx.matvec(emb, e).cpu().numpy()[:n2]           # lags (0, j) for j < n2
+        r = np.arange(n2) / n2 / 0.05
+        x = math.sqrt(2 * nu) * r[1:]
+        ref = 2 ** (1 - nu) / math.gamma(nu) * x ** nu * sp.kv(nu, x)
+        assert np.allclose(col[1:], ref, rtol=1e-12, atol=1e-14)
+        assert col[0] == pytest.approx(1.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("n1,n2,cov", [
+    (32, 32, I.Cov(1.0, 0.1, 0.5, 0.1)),
+    (40, 24, I.Cov(1.0, 0.15, 1.5, 0.0)),
+    (30, 30, I.Cov(1.0, 0.1, 0.5, 0.0, angle=math.radians(30), ratio=3.0)),
+])
+def test_sampler_parity(ctx, n1, n2, cov):
+    set_mask(ctx, I.mask_full(n1, n2))
+    M1, M2, st = ctx.sample_size(cov)
+    assert (M1, M2) == O.sample_embed_size(n1, n2, cov)
+    xi = I.field_noise(M1, M2, 4)
+    out = ctx.sample(cov, M1, M2, torch.tensor(xi, device=DEV)).cpu().numpy()
+    ref = O.sample_field(n1, n2, M1, M2, cov, xi)
+    assert relerr(out, ref) <= 1e-12
+
+
+def tiny_data(w=I.WORKLOADS["tiny32"]):
+    mask = I.make_mask(w)
+    M1, M2 = O.sample_embed_size(w.n1, w.n2, w.cov)
+    xi, eps = I.data_noise(M1, M2, int(mask.sum()), w.data_seed)
+    y, X, x = O.make_data(w.n1, w.n2, mask, w.cov, w.beta, xi, eps)
+    return w, mask, y, X
+
+
+def test_logdet_tiny_fp64_same_probes(ctx):
+    w, mask, y, X = tiny_data()
+    set_mask(ctx, mask)
+    emb = ctx.embed(w.cov, kry.KRY_F64)
+    ld, se, per = ctx.logdet(emb, w.nprobe, w.nsteps, w.probe_seed)
+    P = O.FFTProblem(w.n1, w.n2, mask, w.cov)
+    ld_o, se_o, per_o = P.logdet(w.nprobe, w.nsteps, w.probe_seed)
+    assert abs(ld - ld_o) <= 1e-3 * abs(ld_o)
+    assert np.allclose(per, per_o, rtol=1e-9)
+    # within 3 standard errors of the exact log det
+    exact = 2 * np.sum(np.log(np.diag(np.linalg.cholesky(O.dense_K(w.n1, w.n2, mask, w.cov)))))
+    assert abs(ld - exact) <= 3 * se
+
+
+@pytest.mark.parametrize("n1,n2,cov,frac", [
+    (64, 64, I.Cov(1.0, 0.1, 1.5, 0.05), 0.5),
+    (96, 80, I.Cov(1.0, 0.08, 1.0, 0.1), 0.3),
+])
+def test_logdet_fp32_same_probes(ctx, n1, n2, cov, frac):
+    mask = I.mask_uniform(n1, n2, frac, 2)
+    set_mask(ctx, mask)
+    emb = ctx.embed(cov, kry.KRY_F32)
+    ld, se, per = ctx.logdet(emb, 6, 40, 9)
+    P = O.FFTProblem(n1, n2, mask, cov)
+    ld_o, _, per_o = P.logdet(6, 40, 9)
+    assert abs(ld - ld_o) <= 1e-3 * abs(ld_o), (ld, ld_o)
+    assert np.allclose(per, per_o, rtol=1e-3)
+
+
+def test_logdet_nugget_only_is_exact(ctx):
+    n1, n2 = 20, 20
+    mask = I.mask_uniform(n1, n2, 0.5, 1)
+    p = set_mask(ctx, mask)
+    emb = ctx.embed(I.Cov(0.0, 0.1, 0.5, 0.4), kry.KRY_F64)
+    ld, se, per = ctx.logdet(emb, 4, 10, 3)
+    assert ld == pytest.approx(p * math.log(0.4), rel=1e-13)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_solve_parity(ctx, prec):
+    n1, n2 = 48, 40
+    cov = I.Cov(1.0, 0.1, 1.5, 0.05)
+    mask = I.mask_uniform(n1, n2, 0.4, 8)
+    p = set_mask(ctx, mask)
+    B = I.normals((3, p), 6)
+    K = O.dense_K(n1, n2, mask, cov)
+    ref = np.linalg.solve(K, B.T).T
+    emb = ctx.embed(cov, kry.KRY_F64 if prec == "f64" else kry.KRY_F32)
+    X, iters, relres, st = ctx.solve(emb, torch.tensor(B, device=DEV), rtol=1e-9, maxit=4000, refine=6)
+    assert st == kry.KRY_OK and relres <= 1e-9
+    Xn = X.cpu().numpy()
+    for k in range(3):
+        assert relerr(K @ Xn[k], B[k]) <= 2e-9
+        assert relerr(Xn[k], ref[k]) <= 1e-6
+
+
+def test_profile_loglik_tiny_parity(ctx):
+    w, mask, y, X = tiny_data()
+    set_mask(ctx, mask)
+    opts = kry.Opts(prec=kry.KRY_F64, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol, maxit=5000)
+    res = ctx.profile_loglik(torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV), [w.cov], opts)
+    P = O.FFTProblem(w.n1, w.n2, mask, w.cov)
+    ref = P.profile_loglik(y, X, w.nprobe, w.nsteps, w.probe_seed, tol=1e-12)
+    assert res["loglik"][0] == pytest.approx(ref["loglik"], rel=1e-3)
+    assert res["logdet"][0] == pytest.approx(ref["logdet"], rel=1e-9)
+    assert np.allclose(res["beta"][0], ref["beta"], rtol=1e-5, atol=1e-7)
+    dense = O.loglik_dense(O.dense_K(w.n1, w.n2, mask, w.cov), y, X)
+    assert np.allclose(res["beta"][0], dense["beta"], rtol=1e-5, atol=1e-7)
+
+
+def test_profile_loglik_batch_of_thetas_fp32(ctx):
+    n1, n2 = 64, 64
+    mask = I.mask_uniform(n1, n2, 0.3, 3)
+    p = set_mask(ctx, mask)
+    dcov = I.Cov(1.0, 0.08, 1.0, 0.1)
+    M1, M2 = O.sample_embed_size(n1, n2, dcov)
+    xi, eps = I.data_noise(M1, M2, p, 30)
+    y, X, _ = O.make_data(n1, n2, mask, dcov, (1.0, 0.5, -0.5), xi, eps)
+    thetas = [I.Cov(1.0, r, nu, 0.1) for r in (0.04, 0.08) for nu in (0.5, 1.0, 2.5)]
+    opts = kry.Opts(prec=kry.KRY_F32, nprobe=6, nsteps=40, seed=3, rtol=1e-8, maxit=4000, refine=6)
+    res = ctx.profile_loglik(torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV), thetas, opts)
+    for t, th in enumerate(thetas):
+        P = O.FFTProblem(n1, n2, mask, th)
+        ref = P.profile_loglik(y, X, 6, 40, 3, tol=1e-11)
+        assert res["loglik"][t] == pytest.approx(ref["loglik"], rel=1e-3), th
+        assert res["logdet"][t] == pytest.approx(ref["logdet"], rel=1e-3), th
+
+
+def test_krige_tiny_sites_and_cells(ctx):
+    w, mask, y, X = tiny_data()
+    set_mask(ctx, mask)
+    sites = I.uniform_sites(w.extra["n_sites"], w.extra["site_seed"])
+    Xs = I.covariates(sites[:, 0], sites[:, 1])
+    cells = np.array([0, 5, 100, 517, 1023], dtype=np.int64)
+    S1, S2 = I.cell_centres(w.n1, w.n2)
+    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+    opts = kry.Opts(prec=kry.KRY_F64, nprobe=4, nsteps=10, seed=0, rtol=1e-10, maxit=5000)
+    res = ctx.krige(w.cov, opts, torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV),
+                    cells=torch.tensor(cells, device=DEV), Xc=torch.tensor(Xc.T.copy(), device=DEV),
+                    sites=torch.tensor(sites, device=DEV), Xs=torch.tensor(Xs.T.copy(), device=DEV), variances=True)
+    ms, _ = O.krige_dense(w.n1, w.n2, mask, w.cov, y, X, sites, Xs)
+    cs = np.stack([S1.ravel()[cells], S2.ravel()[cells]], axis=1)
+    mc, vc = O.krige_dense(w.n1, w.n2, mask, w.cov, y, X, cs, Xc)
+    assert relerr(res["mean_sites"].cpu().numpy(), ms) <= 1e-4
+    assert relerr(res["mean_cells"].cpu().numpy(), mc) <= 1e-4
+    assert np.allclose(res["var_cells"].cpu().numpy(), vc, rtol=1e-6, atol=1e-8)
+
+
+def test_krige_masked_fp32_cells(ctx):
+    n1, n2 = 48, 56
+    cov = I.Cov(1.0, 0.1, 1.5, 0.05)
+    mask = I.mask_circles(n1, n2, 0.3, 4)
+    p = set_mask(ctx, mask)
+    M1, M2 = O.sample_embed_size(n1, n2, cov)
+    xi, eps = I.data_noise(M1, M2, p, 12)
+    y, X, _ = O.make_data(n1, n2, mask, cov, (1.0, 0.5, -0.5), xi, eps)
+    cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+    S1, S2 = I.cell_centres(n1, n2)
+    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+    opts = kry.Opts(prec=kry.KRY_F32, rtol=1e-8, maxit=4000, refine=6)
+    res = ctx.krige(cov, opts, torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV),
+                    cells=torch.tensor(cells, device=DEV), Xc=torch.tensor(Xc.T.copy(), device=DEV))
+    cs = np.stack([S1.ravel()[cells], S2.ravel()[cells]], axis=1)
+    mc, _ = O.krige_dense(n1, n2, mask, cov, y, X, cs, Xc)
+    assert relerr(res["mean_cells"].cpu().numpy(), mc) <= 1e-4
+
+
+def test_argument_errors(ctx):
+    set_mask(ctx, I.mask_full(8, 8))
+    with pytest.raises(kry.KryError) as ei:
+        ctx.embed(I.Cov(1.0, -0.1, 0.5, 0.1))
+    assert ei.value.status == kry.KRY_EINVAL
+    with pytest.raises(kry.KryError) as ei:
+        ctx.embed(I.Cov(1.0, 0.1, 0.0, 0.1))
+    assert ei.value.status == kry.KRY_EINVAL
+    with pytest.raises(kry.KryError) as ei:
+        ctx.set_mask(torch.zeros((8, 8), dtype=torch.uint8, device=DEV))
+    assert ei.value.status == kry.KRY_EINVAL
+    with pytest.raises(kry.KryError) as ei:
+        ctx.set_mask(torch.ones((5000, 4), dtype=torch.uint8, device=DEV))
+    assert ei.value.status == kry.KRY_EUNSUPPORTED
+    # CG that cannot converge in one iteration reports KRY_ENOCONV with X filled
+    mask = I.mask_uniform(32, 32, 0.3, 1)
+    p = set_mask(ctx, mask)
+    emb = ctx.embed(I.Cov(1.0, 0.1, 1.5, 0.01), kry.KRY_F64)
+    X, iters, relres, st = ctx.solve(emb, torch.ones((1, p), dtype=torch.float64, device=DEV), rtol=1e-12, maxit=1)
+    assert st == kry.KRY_ENOCONV and relres > 1e-12 and torch.isfinite(X).all()
