@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the Kryging hot path on one GB300 (or N replicas).
+
+One step = one profile log-likelihood evaluation of the grid1024 workload plus
+its kriging means: embedding eigenvalues, SLQ log-determinant (64 Rademacher
+probes x 60 Lanczos steps, one batched launch sequence), CG solves of
+K [y, X] with FP64 refinement, GLS beta and loglik, and the kriging mean at
+every unobserved cell.  Inputs are resident on the device before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload, scaled to the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2012_13133_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = "grid1024"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "matvec_grid1024.md")
+KERNEL_SOURCES = ["paper_2012_13133_gb300/csrc/matvec.cu", "paper_2012_13133_gb300/csrc/fft.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def workload_desc(w):
+    return (f"{w.name}: {w.n1}x{w.n2} grid, {int(round((1 - w.frac_missing) * 100))}% observed "
+            f"({w.mask} mask), Matern nu={w.cov.nu}, range={w.cov.range}, sigma2={w.cov.sigma2}, "
+            f"tau2={w.cov.tau2}; SLQ {w.nprobe} probes x {w.nsteps} Lanczos steps; CG on K[y,X] to "
+            f"rel. res. {w.cg_tol:g} (FP32 CG, FP64 refinement); GLS beta; kriging mean at all unobserved cells")
+
+
+def model_bytes_per_vector(n1, n2, M1, M2, p):
+    """Algorithmic bytes of the 3-pass FP32 matvec per real vector: the
+    n1 x M2 complex slab written and read twice (16 n1 M2), the vector read,
+    re-read for the nugget and written plus the index lists (16 p)."""
+    return 16.0 * n1 * M2 + 16.0 * p
+
+
+def read_traffic():
+    """Measured DRAM bytes per real vector of the matvec from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_real_vector:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+class Problem:
+    def __init__(self, ctx, w, dev):
+        import torch
+        from paper_2012_13133_gb300 import kry
+        self.w = w
+        self.mask = I.make_mask(w)
+        self.mask_dev = torch.from_numpy(self.mask.astype(np.uint8)).to(dev)
+        self.p = ctx.set_mask(self.mask_dev)
+        S1, S2 = I.cell_centres(w.n1, w.n2)
+        X = I.covariates(S1[self.mask], S2[self.mask])
+        self.Xt = torch.tensor(X.T.copy(), device=dev)
+        cov = w.cov
+        M1, M2, _ = ctx.sample_size(cov)
+        xi, eps = I.data_noise(M1, M2, self.p, w.data_seed)
+        field = ctx.sample(cov, M1, M2, torch.tensor(xi, device=dev))
+        beta = torch.tensor(w.beta, device=dev, dtype=torch.float64)
+        self.y = (self.Xt.T @ beta + field[self.mask_dev.bool()] +
+                  math.sqrt(cov.tau2) * torch.tensor(eps, device=dev)).contiguous()
+        cells = np.flatnonzero(~self.mask.ravel()).astype(np.int64)
+        self.cells = torch.tensor(cells, device=dev)
+        self.Xc = torch.tensor(I.covariates(S1.ravel()[cells], S2.ravel()[cells]).T.copy(), device=dev)
+        self.opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed,
+                             rtol=w.cg_tol, maxit=10000, refine=6)
+        self.M1, self.M2 = I_embed(w.n1), I_embed(w.n2)
+        # host copies for the end-to-end leg (pinned)
+        self.y_h = self.y.cpu().pin_memory()
+        self.Xt_h = self.Xt.cpu().pin_memory()
+        self.mask_h = self.mask_dev.cpu().pin_memory()
+        self.cells_h = self.cells.cpu().pin_memory()
+        self.Xc_h = self.Xc.cpu().pin_memory()
+
+    def step(self, ctx):
+        res = ctx.profile_loglik(self.y, self.Xt, [self.w.cov], self.opts)
+        kr = ctx.krige(self.w.cov, self.opts, self.y, self.Xt, cells=self.cells, Xc=self.Xc)
+        return res, kr
+
+
+def I_embed(n):
+    M = 1
+    while M < 2 * n:
+        M *= 2
+    return M
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2012_13133_gb300 import kry
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = I.WORKLOADS[args.workload]
+    ctx = kry.Context(local_rank)
+    stream = torch.cuda.current_stream(local_rank)
+    prob = Problem(ctx, w, dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    for _ in range(args.warmup):
+        flush_l2(flush)
+        prob.step(ctx)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    ctx.profile_enable(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = kry.launch_count()
+    dev_ms = 0.0
+    statuses = []
+    ll_vals = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, kr = prob.step(ctx)
+        e1.record(stream)
+        e1.synchronize()
+        dev_ms += e0.elapsed_time(e1)
+        statuses.append((int(res["status"]), int(kr["status"])))
+        ll_vals.append(float(res["loglik"][0]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = kry.launch_count() - launches0
+    clk = clocks.stop()
+    prof32 = ctx.profile_read(kry.KRY_F32)
+    prof64 = ctx.profile_read(kry.KRY_F64)
+    ctx.profile_enable(False)
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+
+    # ---- end to end: host buffers, H2D + D2H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        y_d = torch.empty_like(prob.y)
+        X_d = torch.empty_like(prob.Xt)
+        m_d = torch.empty_like(prob.mask_dev)
+        c_d = torch.empty_like(prob.cells)
+        xc_d = torch.empty_like(prob.Xc)
+        h2d = (prob.y_h.numel() * 8 + prob.Xt_h.numel() * 8 + prob.mask_h.numel() + prob.cells_h.numel() * 8 +
+               prob.Xc_h.numel() * 8)
+        d2h = 0
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush_l2(flush)
+            y_d.copy_(prob.y_h, non_blocking=True)
+            X_d.copy_(prob.Xt_h, non_blocking=True)
+            m_d.copy_(prob.mask_h, non_blocking=True)
+            c_d.copy_(prob.cells_h, non_blocking=True)
+            xc_d.copy_(prob.Xc_h, non_blocking=True)
+            ctx.set_mask(m_d)
+            res = ctx.profile_loglik(y_d, X_d, [w.cov], prob.opts)
+            kr = ctx.krige(w.cov, prob.opts, y_d, X_d, cells=c_d, Xc=xc_d)
+            mean_h = kr["mean_cells"].cpu()
+            d2h = mean_h.numel() * 8 + 8 * (2 + X_d.shape[0])
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        return None
+
+    value = world * args.steps / (dev_ms / 1000.0)
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs") if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    n1, n2, M1, M2, p = w.n1, w.n2, prob.M1, prob.M2, prob.p
+    bytes_vec = model_bytes_per_vector(n1, n2, M1, M2, p)
+    roof = None
+    if prof32["calls"] > 0 and prof32["ms"] > 0:
+        alg = bytes_vec * prof32["vectors"] + 4.0 * M1 * M2 * prof32["calls"]
+        achieved = alg / (prof32["ms"] / 1000.0) / 1e9
+        traffic_vec = read_traffic()
+        per_launch_vectors = prof32["vectors"] / prof32["calls"]
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": (None if traffic_vec is None else round(traffic_vec * per_launch_vectors)),
+                "kernel": "FP32 3-pass FFT matvec (passes A+B+C of one call)",
+                "launches": prof32["calls"], "mean_vectors_per_launch": round(per_launch_vectors, 2),
+                "mean_launch_ms": round(prof32["ms"] / prof32["calls"], 4),
+                "algorithmic_bytes_per_launch": round(alg / prof32["calls"]),
+                "share_of_step": round(prof32["ms"] / dev_ms, 3),
+                "fp64_matvec_share_of_step": round(prof64["ms"] / dev_ms, 3)}
+
+    out = {
+        "metric": "profile-loglik evals/s",
+        "value": round(value, 4),
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dev_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w), "grid": [n1, n2], "embedding": [M1, M2], "p": p,
+                   "probes": w.nprobe, "lanczos_steps": w.nsteps, "kriging_cells": int(prob.cells.numel()),
+                   "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+        "wall_s": round(wall, 3),
+        "loglik": ll_vals[-1],
+        "status": statuses[-1],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, prob.p, mask=prob.mask, cg_mv=None, budget_s=args.cpu_budget)
+    return out
+
+
+# ---------------------------------------------------------------------------- CPU oracle arm
+
+def matvecs_per_eval(w, cg_iters_per_rhs=None):
+    """Real-vector matvecs of one evaluation: SLQ probes x steps plus CG on the
+    (1 + 3) right-hand sides and one kriging matvec.  The CG count defaults to
+    an estimate of 300 iterations per right-hand side."""
+    cg = 300 if cg_iters_per_rhs is None else cg_iters_per_rhs
+    return w.nprobe * w.nsteps + 4 * cg + 1
+
+
+def cpu_baseline(w, p=None, mask=None, cg_mv=None, budget_s=20.0):
+    """Time the oracle's FP64 FFT matvec inside its Lanczos loop on the full
+    workload (one probe, up to nsteps steps or ~budget_s seconds), and scale
+    to evaluations/s by the matvecs of one evaluation."""
+    from oracle import kryoracle as O
+    if mask is None:
+        mask = I.make_mask(w)
+    P = O.FFTProblem(w.n1, w.n2, mask, w.cov)
+    z = O.rademacher_probe(w.probe_seed, 0, P.p)
+    n = 0
+    t0 = time.perf_counter()
+    q = z / np.linalg.norm(z)
+    while n < w.nsteps and (time.perf_counter() - t0) < budget_s:
+        q = P.matvec(q)
+        q /= np.linalg.norm(q)
+        n += 1
+    t = time.perf_counter() - t0
+    per_mv = t / n
+    evals = 1.0 / (per_mv * matvecs_per_eval(w))
+    return {"value": evals, "unit": "evals/s", "cores": O._WORKERS, "kind": "oracle",
+            "sample": f"{n} FP64 FFT matvecs of the oracle at full size ({per_mv * 1e3:.1f} ms each), scaled by "
+                      f"{matvecs_per_eval(w)} real-vector matvecs per evaluation ({w.nprobe}x{w.nsteps} SLQ + "
+                      f"4 RHS x 300 CG iterations + 1 kriging matvec)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    w = I.WORKLOADS[args.workload]
+    mask = I.make_mask(w)
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, mask=mask, budget_s=budget)
+        if k >= args.warmup:
+            vals.append(cb["value"])
+    value = statistics.mean(vals)
+    return {"metric": "profile-loglik evals/s", "value": value, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(w)},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(I.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_gpu(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,18 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
  * size tried if none qualifies.  Synchronises the stream. */
 kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2);
 
+/* Diagnostics (no counterpart in the paper).  kry_profile_enable(ctx, 1)
+ * starts timing every covariance matvec issued on ctx (the three FFT passes
+ * of one call, CUDA events on the context stream) and clears earlier records;
+ * 0 stops.  kry_profile_read sums the records of one precision (KRY_F32 or
+ * KRY_F64): number of matvec calls, real vectors transformed, and device
+ * milliseconds.  Both synchronise the stream. */
+kry_status kry_profile_enable(kry_ctx* ctx, int on);
+kry_status kry_profile_read(kry_ctx* ctx, int32_t prec, int64_t* calls, int64_t* vectors, double* total_ms);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t kry_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

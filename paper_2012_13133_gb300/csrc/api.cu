@@ -29,6 +29,15 @@ bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int
                      double rtol, int maxit, int refine);
 }  // namespace kry
 
+std::atomic<unsigned long long> g_kry_launches{0};
+
+static void prof_clear(kry_ctx* ctx) {
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
+    ctx->prof_nvec.clear();
+    ctx->prof_dbl.clear();
+}
+
 void DevBuf::ensure(size_t bytes) {
     if (bytes <= cap && p) return;
     release();
@@ -168,6 +177,7 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     KRY_REQUIRE(prec == KRY_F32 || prec == KRY_F64, KRY_EINVAL, "prec must be KRY_F32 or KRY_F64");
     kry_embed* e = new kry_embed();
     e->ctx = ctx;
+    e->device = ctx->device;
     e->n1 = ctx->n1;
     e->n2 = ctx->n2;
     e->M1 = pow2_at_least(2 * (int64_t)ctx->n1);
@@ -236,6 +246,7 @@ void kry_destroy(kry_ctx* ctx) {
                       &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
+    prof_clear(ctx);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     delete ctx;
 }
@@ -291,17 +302,18 @@ kry_status kry_embed_eigs(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, kry_e
 
 void kry_embed_free(kry_embed* e) {
     if (!e) return;
-    cudaSetDevice(e->ctx->device);
-    cudaStreamSynchronize(e->ctx->stream);
+    // cudaFree synchronises the device, so work still queued on the embedding
+    // finishes first; the owning context is not touched (it may be gone).
+    cudaSetDevice(e->device);
     free_embed(e);
 }
 
 kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev, int32_t nvec, int64_t ld) {
     return guarded(ctx, [&]() -> kry_status {
         check_embed(ctx, e);
-        KRY_REQUIRE(v_dev && out_dev, KRY_EINVAL, "v_dev and out_dev must not be NULL");
         KRY_REQUIRE(nvec >= 0 && ld >= ctx->p, KRY_EINVAL, "need nvec >= 0 and ld >= p");
         if (nvec == 0) return KRY_OK;
+        KRY_REQUIRE(v_dev && out_dev, KRY_EINVAL, "v_dev and out_dev must not be NULL");
         if (e->prec == KRY_F64)
             kry::matvec_ex<double>(ctx, e, static_cast<const double*>(v_dev), ld, nullptr, static_cast<double*>(out_dev),
                                    ld, nvec, nullptr, 0);
@@ -476,6 +488,38 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
         return st;
     });
 }
+
+kry_status kry_profile_enable(kry_ctx* ctx, int on) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        prof_clear(ctx);
+        ctx->prof_on = on != 0;
+        return KRY_OK;
+    });
+}
+
+kry_status kry_profile_read(kry_ctx* ctx, int32_t prec, int64_t* calls, int64_t* vectors, double* total_ms) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_REQUIRE(calls && vectors && total_ms, KRY_EINVAL, "output pointers must not be NULL");
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        int64_t c = 0, v = 0;
+        double ms = 0.0;
+        for (size_t i = 0; i < ctx->prof_nvec.size(); ++i) {
+            if (ctx->prof_dbl[i] != (prec == KRY_F64 ? 1 : 0)) continue;
+            float t = 0.f;
+            KRY_CUDA(cudaEventElapsedTime(&t, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+            ms += t;
+            ++c;
+            v += ctx->prof_nvec[i];
+        }
+        *calls = c;
+        *vectors = v;
+        *total_ms = ms;
+        return KRY_OK;
+    });
+}
+
+uint64_t kry_launch_count(void) { return g_kry_launches.load(); }
 
 kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2) {
     return guarded(ctx, [&]() -> kry_status {

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/kry.h"
 
@@ -31,7 +33,14 @@ struct KryError {
             throw KryError{KRY_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
     } while (0)
 
-#define KRY_CHECK_LAUNCH() KRY_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through this check, which also
+// counts launches (process-wide, for diagnostics).
+extern std::atomic<unsigned long long> g_kry_launches;
+#define KRY_CHECK_LAUNCH()                                       \
+    do {                                                         \
+        g_kry_launches.fetch_add(1, std::memory_order_relaxed);  \
+        KRY_CUDA(cudaGetLastError());                            \
+    } while (0)
 
 #define KRY_REQUIRE(cond, status, text)        \
     do {                                       \
@@ -91,10 +100,17 @@ struct kry_ctx {
     int max_smem_optin = 0;
 
     MvSched sched32, sched64;
+
+    // optional timing of every matvec (CUDA events on the context stream)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;     // start/stop pairs
+    std::vector<int> prof_nvec;
+    std::vector<int> prof_dbl;
 };
 
 struct kry_embed {
     kry_ctx* ctx = nullptr;
+    int device = 0;
     int n1 = 0, n2 = 0, M1 = 0, M2 = 0;
     kry_cov cov{};
     kry_prec prec = KRY_F32;

@@ -111,7 +111,9 @@ __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ 
     const int64_t off = (int64_t)k * p;
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
-        const T w = U[off + i] - ca * Wc[off + i] - cb * Wp[off + i];
+        // at j = 0 there is no previous vector (its buffer is not initialised)
+        const T wp = (j > 0) ? Wp[off + i] : (T)0;
+        const T w = U[off + i] - ca * Wc[off + i] - cb * wp;
         Wn[off + i] = w;
         acc[0] += (double)w * (double)w;
     }

@@ -204,20 +204,26 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
         }
     }
     if (MODE == 0 && dots != nullptr) {
-        // block reduction of (da, db) in a fixed order
-        for (int o = 16; o > 0; o >>= 1) {
-            da += __shfl_down_sync(0xffffffffu, da, o);
-            db += __shfl_down_sync(0xffffffffu, db, o);
-        }
+        // block reduction of (da, db) in a fixed order; blocks narrower than a
+        // warp (short rows) reduce serially through shared memory
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
-            red[0][w] = da;
-            red[1][w] = db;
+        if (blockDim.x >= 32) {
+            for (int o = 16; o > 0; o >>= 1) {
+                da += __shfl_down_sync(0xffffffffu, da, o);
+                db += __shfl_down_sync(0xffffffffu, db, o);
+            }
+            if (lane == 0) {
+                red[0][w] = da;
+                red[1][w] = db;
+            }
+        } else {
+            red[0][threadIdx.x] = da;
+            red[1][threadIdx.x] = db;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double sa = 0.0, sb = 0.0;
-            const int nw = blockDim.x >> 5;
+            const int nw = (blockDim.x >= 32) ? (blockDim.x >> 5) : blockDim.x;
             for (int k = 0; k < nw; ++k) {
                 sa += red[0][k];
                 sb += red[1][k];
@@ -329,6 +335,12 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
     const int thrB = C * (M1 / s.ept_col);
     const size_t smB = (size_t)C * (M1 + 1) * cx_size(dbl);
     const int nbx = (n1 + G - 1) / G;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (ctx->prof_on) {
+        KRY_CUDA(cudaEventCreate(&ev0));
+        KRY_CUDA(cudaEventCreate(&ev1));
+        KRY_CUDA(cudaEventRecord(ev0, st));
+    }
     for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
         const int np = std::min(ppb, npairs - pair0);
         dim3 gA(nbx, np), gB(M2 / C, np);
@@ -348,6 +360,13 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
                                                                 ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
                                                                 tau2, dots, nds, tw32, tw64)));
         }
+    }
+    if (ctx->prof_on) {
+        KRY_CUDA(cudaEventRecord(ev1, st));
+        ctx->prof_ev.push_back(ev0);
+        ctx->prof_ev.push_back(ev1);
+        ctx->prof_nvec.push_back(nvec);
+        ctx->prof_dbl.push_back(dbl ? 1 : 0);
     }
 }
 

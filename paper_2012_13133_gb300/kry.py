@@ -8,8 +8,8 @@ fails loudly if it has not been built: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -63,6 +63,9 @@ SIGNATURES = {
                             _P, _P, C.c_int64, _P, _P, _P, _DP]),
     "kry_sample": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int32, C.c_int32, _P, _P]),
     "kry_sample_size": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "kry_profile_enable": (C.c_int, [_P, C.c_int]),
+    "kry_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _DP]),
+    "kry_launch_count": (C.c_uint64, []),
 }
 
 
@@ -83,6 +86,11 @@ _lib = load_library()
 
 def lib():
     return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libkry.so in this process so far."""
+    return int(_lib.kry_launch_count())
 
 
 def _ptr(t):
@@ -120,6 +128,7 @@ class Opts:
 class Embed:
     def __init__(self, ctx, handle, min_over_max, prec):
         self.ctx, self.handle, self.min_over_max, self.prec = ctx, handle, min_over_max, prec
+        ctx._embeds.add(self)
 
     def free(self):
         if self.handle:
@@ -150,9 +159,12 @@ class Context:
         self.h = h
         self.p = 0
         self.n1 = self.n2 = 0
+        self._embeds = weakref.WeakSet()
 
     def close(self):
         if getattr(self, "h", None):
+            for e in list(self._embeds):
+                e.free()
             _lib.kry_destroy(self.h)
             self.h = None
 
@@ -242,6 +254,14 @@ class Context:
                                         ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms), _ptr(vc),
                                         _np_dp(beta)), allow=(KRY_ENOCONV,))
         return dict(mean_cells=mc, mean_sites=ms, var_cells=vc, beta=beta, status=st)
+
+    def profile_enable(self, on=True):
+        self._check(_lib.kry_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, prec=KRY_F32):
+        c, v, ms = C.c_int64(), C.c_int64(), C.c_double()
+        self._check(_lib.kry_profile_read(self.h, prec, C.byref(c), C.byref(v), C.byref(ms)))
+        return dict(calls=c.value, vectors=v.value, ms=ms.value)
 
     def sample_size(self, cov):
         m1, m2 = C.c_int32(), C.c_int32()
