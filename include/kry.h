@@ -125,6 +125,22 @@ void kry_embed_free(kry_embed* e);
 kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev,
                       int32_t nvec, int64_t ld);
 
+/* Allocation-free form of kry_matvec (the paper has no counterpart; this is a
+ * deployment aid).  Same arguments and result as kry_matvec, for callers that
+ * cannot allocate device memory at call time: work recorded under a
+ * global-mode CUDA stream capture (where cudaMalloc is not allowed), hosts
+ * whose device memory is owned by their own pool, and latency-critical loops
+ * that cannot absorb the device synchronisation of cudaMalloc/cudaFree.
+ * The FFT intermediate lives in a 16 MiB static device array of the library
+ * (held by every GPU that loads it, until exit), so n1 * M2 * sizeof(complex)
+ * must not exceed 16 MiB (e.g. grids up to 1024 x 1024 in FP32); larger grids
+ * return KRY_EUNSUPPORTED.  The call performs no allocation itself; ctx, its
+ * mask and e must be set up beforehand.  The first call on a device looks up
+ * the array's address: make it before any stream capture.  All calls on a
+ * device share the array: calls that overlap on the GPU race.  Asynchronous. */
+kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev,
+                              int32_t nvec, int64_t ld);
+
 /* Stochastic Lanczos quadrature estimate of log det K (Sec. 3.3, stochastic
  * trace alternative): probe k has entries z_k[i] = +1 if bit 63 of
  * splitmix64(seed XOR (k * 2^32 + i)) is 0, else -1; nsteps Lanczos steps

@@ -22,6 +22,8 @@
 // c < C, so that pass B reads and writes one contiguous block per CTA and
 // passes A and C touch G*C contiguous elements per tile for G rows per CTA.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "fft.cuh"
 #include "kry_internal.cuh"
@@ -397,4 +399,122 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
     run_matvec<double>(ctx, e, vin, ld, nullptr, out_grid, (int64_t)e->n1 * e->n2, nvec, 0.0, nullptr, 0, 1);
 }
 
+// ------------------------------------------------------------------ allocation-free matvec
+//
+// kry_matvec_noalloc serves callers that cannot allocate device memory when
+// they call: code recorded into a CUDA graph under global-mode stream capture
+// (where cudaMalloc is not permitted), applications whose device memory is all
+// owned by their own pool, and latency-critical loops that cannot afford the
+// device-wide synchronisation of cudaMalloc / cudaFree.  It launches the same
+// three FFT passes as kry_matvec, but its slab lives in a fixed file-scope
+// device array instead of context scratch.  The array is part of the module,
+// so every GPU that loads this library holds it until the process exits.
+//
+// Set-up: the first call on a device looks up the array's device address
+// (cudaGetSymbolAddress, with that device current) and caches it; make that
+// first call before any stream capture.  The context, its mask and the
+// embedding must already exist (creating them does allocate).
+//
+// Sharing: every call on a device uses the same array and it keeps the last
+// call's contents.  Nothing needs clearing, because pass A writes every slab
+// element that passes B and C read.  Calls whose work overlaps on the GPU
+// (other streams, other host threads) race on the array and must be
+// serialised by the caller.
+
+#define KRY_NOALLOC_SCRATCH_BYTES (16u << 20)   // 16 MiB: one 1024 x 1024 FP32 complex pair
+#define KRY_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KRY_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[KRY_NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+static void* noalloc_scratch(int device) {
+    KRY_REQUIRE(device >= 0 && device < KRY_NOALLOC_MAX_DEVICES, KRY_EUNSUPPORTED,
+                "device index too large for the allocation-free matvec");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[device] == nullptr) {
+        void* ptr = nullptr;
+        cudaError_t err = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (err != cudaSuccess)
+            throw KryError{KRY_ECUDA, std::string("cudaGetSymbolAddress of the static matvec scratch failed: ") +
+                                          cudaGetErrorString(err)};
+        g_noalloc_addr[device] = ptr;
+    }
+    return g_noalloc_addr[device];
+}
+
+template <typename T>
+static void run_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld,
+                               void* scratch) {
+    using Cx = typename cx_of<T>::type;
+    const bool dbl = sizeof(T) == 8;
+    const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
+    MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, M1, M2, dbl);
+    const size_t slab_pair = (size_t)n1 * M2 * cx_size(dbl);
+    KRY_REQUIRE(slab_pair <= KRY_NOALLOC_SCRATCH_BYTES, KRY_EUNSUPPORTED,
+                "grid too large for the allocation-free matvec: n1 * M2 * sizeof(complex) = " +
+                    std::to_string(slab_pair) + " bytes exceeds its 16 MiB static scratch");
+    const int npairs = (nvec + 1) / 2;
+    const int ppb = std::max(1, std::min(npairs, (int)(KRY_NOALLOC_SCRATCH_BYTES / slab_pair)));
+    Cx* slab = static_cast<Cx*>(scratch);
+    const T* lamT = dbl ? reinterpret_cast<const T*>(e->lam64T) : reinterpret_cast<const T*>(e->lam32T);
+    const int C = s.cols_per_cta;
+    const int G = s.rows_per_cta;
+    const int* rowptr = ctx->rowptr.as<int>();
+    const int* colidx = ctx->colidx.as<int>();
+    const void* tw32 = ctx->tw32.p;
+    const void* tw64 = ctx->tw64.p;
+    cudaStream_t st = ctx->stream;
+    const int thrA = G * (M2 / s.ept_row);
+    const size_t smA = (size_t)G * (M2 + 1) * cx_size(dbl);
+    const int thrB = C * (M1 / s.ept_col);
+    const size_t smB = (size_t)C * (M1 + 1) * cx_size(dbl);
+    const int nbx = (n1 + G - 1) / G;
+    const double tau2 = e->cov.tau2;
+    for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
+        const int np = std::min(ppb, npairs - pair0);
+        dim3 gA(nbx, np), gB(M2 / C, np);
+        KRY_DISPATCH_EG(s.ept_row, G,
+                        (MvLaunch<T>::template a<E_, G_>(gA, thrA, smA, st, vin, ld, nullptr, nvec, pair0, rowptr,
+                                                         colidx, n1, M2, C, slab, tw32, tw64)));
+        KRY_DISPATCH_EG(s.ept_col, C,
+                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64)));
+        KRY_DISPATCH_EG(s.ept_row, G,
+                        (MvLaunch<T>::template c<E_, G_, 0>(gA, thrA, smA, st, slab, vin, ld, nullptr, vout, ld,
+                                                            nvec, pair0, rowptr, colidx, n1, n2, M2, C, tau2,
+                                                            nullptr, 0, tw32, tw64)));
+    }
+}
+
 }  // namespace kry
+
+extern "C" kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev,
+                                         int32_t nvec, int64_t ld) {
+    if (!ctx) return KRY_EINVAL;
+    try {
+        KRY_CUDA(cudaSetDevice(ctx->device));
+        ctx->err.clear();
+        KRY_REQUIRE(e != nullptr && e->ctx == ctx, KRY_EINVAL, "embedding is NULL or belongs to another context");
+        KRY_REQUIRE(ctx->p > 0 && e->n1 == ctx->n1 && e->n2 == ctx->n2, KRY_EINVAL,
+                    "no mask set, or the embedding grid differs from the mask grid");
+        KRY_REQUIRE(nvec >= 0 && ld >= ctx->p, KRY_EINVAL, "need nvec >= 0 and ld >= p");
+        if (nvec == 0) return KRY_OK;
+        KRY_REQUIRE(v_dev && out_dev, KRY_EINVAL, "v_dev and out_dev must not be NULL");
+        void* scratch = kry::noalloc_scratch(ctx->device);
+        if (e->prec == KRY_F64)
+            kry::run_matvec_noalloc<double>(ctx, e, static_cast<const double*>(v_dev), static_cast<double*>(out_dev),
+                                            nvec, ld, scratch);
+        else
+            kry::run_matvec_noalloc<float>(ctx, e, static_cast<const float*>(v_dev), static_cast<float*>(out_dev),
+                                           nvec, ld, scratch);
+        return KRY_OK;
+    } catch (const KryError& err) {
+        ctx->err = err.msg;
+        return err.st;
+    } catch (const std::exception& err) {
+        ctx->err = err.what();
+        return KRY_ECUDA;
+    }
+}

@@ -54,6 +54,7 @@ SIGNATURES = {
     "kry_embed_eigs": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.POINTER(_P), _DP]),
     "kry_embed_free": (None, [_P]),
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
+    "kry_matvec_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
     "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, _DP, _DP, _DP]),
     "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32, C.c_int32,
                             C.POINTER(C.c_int32), _DP]),
