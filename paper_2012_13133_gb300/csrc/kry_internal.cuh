@@ -68,6 +68,8 @@ struct MvSched {
     int ept_col = 8;
     int cols_per_cta = 4;
     int pairs_per_batch = 0;   // 0 = all pairs at once
+    int g16 = 0;               // radix-16 path: rows per block (0 = default)
+    int c16 = 0;               // radix-16 path: columns per block / slab tile width (0 = default)
 };
 
 struct kry_ctx {

@@ -26,6 +26,7 @@
 #include <string>
 
 #include "fft.cuh"
+#include "fft16.cuh"
 #include "kry_internal.cuh"
 
 namespace kry {
@@ -236,6 +237,221 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
     }
 }
 
+// ------------------------------------------------------------------ radix-16 passes (64 <= L <= 8192)
+//
+// Same three passes as above, built from the radix-16 register stages of
+// fft16.cuh: G rows (pass A/C) or CC columns (pass B) per block, interleaved
+// in padded shared memory; the first and last stages read and write global
+// memory (or registers) directly, and pass B multiplies by Lambda between its
+// forward and inverse column transforms without leaving registers.
+
+template <typename T, int G>
+__global__ void __launch_bounds__(512) k16_pass_a(const T* __restrict__ vin, int64_t ld, const double* __restrict__ scale,
+                                                  int nvec, int pair0, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ colidx, int n1, int n2, int M2, int C,
+                                                  int logC, int PS, typename cx_of<T>::type* __restrict__ slab,
+                                                  const void* tw32, const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    const int L = M2, b = 31 - __clz(L), LT = L >> 4;
+    const int g = threadIdx.x % G, t = threadIdx.x / G;
+    const int row = blockIdx.x * G + g;
+    const int pair = pair0 + blockIdx.y;
+    const int va = 2 * pair, vb = 2 * pair + 1;
+    const bool has_b = vb < nvec;
+    const Cx* tw = twiddles<T>(tw32, tw64);
+    const Cx zero = cmk<Cx>((T)0, (T)0);
+
+    for (int pos = t; pos < n2; pos += LT) buf[kry16::spos(pos, PS, G, g)] = zero;
+    __syncthreads();
+    if (row < n1) {
+        const T sa = scale ? (T)scale[va] : (T)1;
+        const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
+        const T* pa = vin + (int64_t)va * ld;
+        const T* pb = vin + (int64_t)vb * ld;
+        const int q1 = rowptr[row + 1];
+        for (int q = rowptr[row] + t; q < q1; q += LT)
+            buf[kry16::spos(colidx[q], PS, G, g)] = cmk<Cx>(pa[q] * sa, has_b ? pb[q] * sb : (T)0);
+    }
+    __syncthreads();
+
+    Cx* out = slab + (int64_t)blockIdx.y * n1 * M2 + (int64_t)row * C;
+    const int64_t tstride = (int64_t)n1 * C;
+    auto ld_s = [&](int pos) { return buf[kry16::spos(pos, PS, G, g)]; };
+    auto ld_0 = [&](int pos) { return pos < n2 ? buf[kry16::spos(pos, PS, G, g)] : zero; };
+    auto st_s = [&](int pos, Cx z) { buf[kry16::spos(pos, PS, G, g)] = z; };
+    auto st_g = [&](int pos, Cx z) {
+        if (row < n1) out[(int64_t)(pos >> logC) * tstride + (pos & (C - 1))] = z;
+    };
+    Cx v[16];
+    kry16::transform<Cx, false>(b, v, t, tw, ld_0, ld_s, st_s, st_g, true, false);
+}
+
+template <typename T, int CC>
+__global__ void __launch_bounds__(512) k16_pass_b(typename cx_of<T>::type* __restrict__ slab,
+                                                  const T* __restrict__ lamT, int n1, int M1, int M2, int PS,
+                                                  const void* tw32, const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    const int L = M1, b = 31 - __clz(L), LT = L >> 4;
+    const int c = threadIdx.x % CC, t = threadIdx.x / CC;
+    const int tile = blockIdx.x;
+    Cx* blk = slab + (int64_t)blockIdx.y * n1 * M2 + (int64_t)tile * n1 * CC;
+    const Cx* tw = twiddles<T>(tw32, tw64);
+    const Cx zero = cmk<Cx>((T)0, (T)0);
+
+    auto ld_g = [&](int pos) { return pos < n1 ? blk[pos * CC + c] : zero; };
+    auto ld_s = [&](int pos) { return buf[kry16::spos(pos, PS, CC, c)]; };
+    auto st_s = [&](int pos, Cx z) { buf[kry16::spos(pos, PS, CC, c)] = z; };
+    auto st_g = [&](int pos, Cx z) {
+        if (pos < n1) blk[pos * CC + c] = z;
+    };
+    const int nst = kry16::num_stages(b);
+    Cx v[16];
+    // forward column transform, ending in registers (slot m = row t + m L/16)
+    {
+        const int r0 = kry16::stage_radix(b, 0);
+        switch (r0) {
+            case 2: kry16::stage<Cx, 2, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            case 4: kry16::stage<Cx, 4, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            case 8: kry16::stage<Cx, 8, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            default: kry16::stage<Cx, 16, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
+        }
+        __syncthreads();
+        int Ns = r0;
+#pragma unroll 1
+        for (int s = 1; s < nst - 1; ++s) {
+            kry16::stage<Cx, 16, false>(v, t, L, Ns, tw, ld_s, st_s, true);
+            __syncthreads();
+            Ns *= 16;
+        }
+        kry16::last_stage_regs<Cx, false>(v, t, L, Ns, tw, ld_s, true);
+    }
+    // eigenvalue multiply (scaled by 1/(M1 M2))
+    const T* lam = lamT + (int64_t)(tile * CC + c) * L;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const T l = lam[t + m * LT];
+        v[m] = cmk<Cx>(v[m].x * l, v[m].y * l);
+    }
+    // inverse column transform, starting from registers, keeping rows < n1
+    {
+        const int r0 = kry16::stage_radix(b, 0);
+        kry16::first_stage_regs<Cx, true>(r0, v, t, L, tw, st_s);
+        __syncthreads();
+        int Ns = r0;
+#pragma unroll 1
+        for (int s = 1; s < nst - 1; ++s) {
+            kry16::stage<Cx, 16, true>(v, t, L, Ns, tw, ld_s, st_s, true);
+            __syncthreads();
+            Ns *= 16;
+        }
+        kry16::stage<Cx, 16, true>(v, t, L, Ns, tw, ld_s, st_g, false);
+    }
+}
+
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(512) k16_pass_c(const typename cx_of<T>::type* __restrict__ slab,
+                                                  const T* __restrict__ vin, int64_t ld_in,
+                                                  const double* __restrict__ scale, T* __restrict__ vout,
+                                                  int64_t ld_out, int nvec, int pair0, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ colidx, int n1, int n2, int M2, int C,
+                                                  int logC, int PS, double tau2, double* __restrict__ dots,
+                                                  int ndot_stride, const void* tw32, const void* tw64) {
+    using Cx = typename cx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    __shared__ double red[2][32];
+    const int L = M2, b = 31 - __clz(L), LT = L >> 4;
+    const int g = threadIdx.x % G, t = threadIdx.x / G;
+    const int row = blockIdx.x * G + g;
+    const int pair = pair0 + blockIdx.y;
+    const int va = 2 * pair, vb = 2 * pair + 1;
+    const bool has_b = vb < nvec;
+    const Cx* tw = twiddles<T>(tw32, tw64);
+    const Cx zero = cmk<Cx>((T)0, (T)0);
+
+    const Cx* in = slab + (int64_t)blockIdx.y * n1 * M2 + (int64_t)row * C;
+    const int64_t tstride = (int64_t)n1 * C;
+    auto ld_g = [&](int pos) {
+        return row < n1 ? in[(int64_t)(pos >> logC) * tstride + (pos & (C - 1))] : zero;
+    };
+    auto ld_s = [&](int pos) { return buf[kry16::spos(pos, PS, G, g)]; };
+    auto st_s = [&](int pos, Cx z) { buf[kry16::spos(pos, PS, G, g)] = z; };
+    auto st_n = [&](int pos, Cx z) {
+        if (pos < n2) buf[kry16::spos(pos, PS, G, g)] = z;
+    };
+    Cx v[16];
+    kry16::transform<Cx, true>(b, v, t, tw, ld_g, ld_s, st_s, st_n, false, true);
+    __syncthreads();
+
+    double da = 0.0, db = 0.0;
+    if (row < n1) {
+        if (MODE == 0) {
+            const T sa = scale ? (T)scale[va] : (T)1;
+            const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
+            const T t2 = (T)tau2;
+            const T* pa = vin + (int64_t)va * ld_in;
+            const T* pb = vin + (int64_t)vb * ld_in;
+            T* oa = vout + (int64_t)va * ld_out;
+            T* ob = vout + (int64_t)vb * ld_out;
+            const int q1 = rowptr[row + 1];
+            for (int q = rowptr[row] + t; q < q1; q += LT) {
+                const Cx z = buf[kry16::spos(colidx[q], PS, G, g)];
+                const T xa = pa[q] * sa;
+                const T ya = z.x + t2 * xa;
+                oa[q] = ya;
+                da += (double)xa * (double)ya;
+                if (has_b) {
+                    const T xb = pb[q] * sb;
+                    const T yb = z.y + t2 * xb;
+                    ob[q] = yb;
+                    db += (double)xb * (double)yb;
+                }
+            }
+        } else {
+            T* oa = vout + (int64_t)va * ld_out + (int64_t)row * n2;
+            T* ob = vout + (int64_t)vb * ld_out + (int64_t)row * n2;
+            for (int j = t; j < n2; j += LT) {
+                const Cx z = buf[kry16::spos(j, PS, G, g)];
+                oa[j] = z.x;
+                if (has_b) ob[j] = z.y;
+            }
+        }
+    }
+    if (MODE == 0 && dots != nullptr) {
+        // rows are interleaved across lanes (g fastest); the block reduction
+        // sums every row's products of the block in a fixed order
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (blockDim.x >= 32) {
+            for (int o = 16; o > 0; o >>= 1) {
+                da += __shfl_down_sync(0xffffffffu, da, o);
+                db += __shfl_down_sync(0xffffffffu, db, o);
+            }
+            if (lane == 0) {
+                red[0][w] = da;
+                red[1][w] = db;
+            }
+        } else {
+            red[0][threadIdx.x] = da;
+            red[1][threadIdx.x] = db;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sa = 0.0, sb = 0.0;
+            const int nw = (blockDim.x >= 32) ? (blockDim.x >> 5) : blockDim.x;
+            for (int k = 0; k < nw; ++k) {
+                sa += red[0][k];
+                sb += red[1][k];
+            }
+            dots[(int64_t)va * ndot_stride + blockIdx.x] = sa;
+            if (has_b) dots[(int64_t)vb * ndot_stride + blockIdx.x] = sb;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 
 static size_t cx_size(bool dbl) { return dbl ? sizeof(double2) : sizeof(float2); }
@@ -311,12 +527,137 @@ static MvSched pick_sched(kry_ctx* ctx, const MvSched& want, int M1, int M2, boo
     return s;
 }
 
+// ---- radix-16 path: schedule, shared-memory pad shift and launches
+
+static bool use16(int M1, int M2) { return M1 >= 64 && M2 >= 64 && M1 <= KRY_MAX_M && M2 <= KRY_MAX_M; }
+
+// Pad shift of the interleaved shared-memory layout for NT transforms of
+// length L (chosen from a bank-conflict model of the stage access patterns).
+static int pad_shift(int L, int NT) {
+    if (L >= 4096) return 4;
+    if (L == 2048) return NT == 1 ? 4 : 3;
+    if (NT >= 4) return 2;
+    if (NT == 2) return 3;
+    return 4;
+}
+
+static size_t smem16(int L, int NT, bool dbl) {
+    return (size_t)(L + (L >> pad_shift(L, NT))) * NT * cx_size(dbl);
+}
+
+static int ilog2(int x) { return 31 - __builtin_clz((unsigned)x); }
+
+// Rows per block (pass A/C) and columns per block (pass B, = slab tile width).
+static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int* G, int* C) {
+    const MvSched& want = dbl ? ctx->sched64 : ctx->sched32;
+    const size_t lim = (size_t)ctx->max_smem_optin;
+    auto fit = [&](int L, int nt) {
+        nt = std::max(1, std::min(nt, 16));
+        while (nt > 1 && (nt * (L >> 4) > 512 || smem16(L, nt, dbl) > lim)) nt >>= 1;
+        return nt;
+    };
+    int g = want.g16 > 0 ? want.g16 : std::max(1, 256 / (M2 >> 4));
+    int c = want.c16 > 0 ? want.c16 : std::max(1, 512 / (M1 >> 4));
+    *G = fit(M2, g);
+    *C = std::min(fit(M1, c), M2);
+}
+
+#define KRY_DISPATCH_NT(NTV, ...)                                  \
+    do {                                                            \
+        switch (NTV) {                                              \
+            case 1: { constexpr int N_ = 1; __VA_ARGS__; } break;          \
+            case 2: { constexpr int N_ = 2; __VA_ARGS__; } break;          \
+            case 4: { constexpr int N_ = 4; __VA_ARGS__; } break;          \
+            case 8: { constexpr int N_ = 8; __VA_ARGS__; } break;          \
+            case 16: { constexpr int N_ = 16; __VA_ARGS__; } break;        \
+            default: throw KryError{KRY_EUNSUPPORTED, "bad transforms per block"}; \
+        }                                                           \
+    } while (0)
+
+template <typename T>
+static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+                         int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode,
+                         typename cx_of<T>::type* slab, int ppb) {
+    const bool dbl = sizeof(T) == 8;
+    const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
+    int G, C;
+    sched16(ctx, M1, M2, dbl, &G, &C);
+    const int npairs = (nvec + 1) / 2;
+    const T* lamT = dbl ? reinterpret_cast<const T*>(e->lam64T) : reinterpret_cast<const T*>(e->lam32T);
+    const int* rowptr = ctx->rowptr.as<int>();
+    const int* colidx = ctx->colidx.as<int>();
+    const void* tw32 = ctx->tw32.p;
+    const void* tw64 = ctx->tw64.p;
+    cudaStream_t st = ctx->stream;
+    const int psA = pad_shift(M2, G), psB = pad_shift(M1, C);
+    const int thrA = G * (M2 >> 4), thrB = C * (M1 >> 4);
+    const size_t smA = smem16(M2, G, dbl), smB = smem16(M1, C, dbl);
+    const int nbx = (n1 + G - 1) / G;
+    const int logC = ilog2(C);
+    for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
+        const int np = std::min(ppb, npairs - pair0);
+        dim3 gA(nbx, np), gB(M2 / C, np);
+        KRY_DISPATCH_NT(G, {
+            auto k = k16_pass_a<T, N_>;
+            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+            k<<<gA, thrA, smA, st>>>(vin, ld_in, scale, nvec, pair0, rowptr, colidx, n1, n2, M2, C, logC, psA, slab,
+                                    tw32, tw64);
+            KRY_CHECK_LAUNCH();
+        });
+        KRY_DISPATCH_NT(C, {
+            auto k = k16_pass_b<T, N_>;
+            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
+            k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64);
+            KRY_CHECK_LAUNCH();
+        });
+        if (mode == 0) {
+            KRY_DISPATCH_NT(G, {
+                auto k = k16_pass_c<T, N_, 0>;
+                KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+                k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64);
+                KRY_CHECK_LAUNCH();
+            });
+        } else {
+            KRY_DISPATCH_NT(G, {
+                auto k = k16_pass_c<T, N_, 1>;
+                KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+                k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64);
+                KRY_CHECK_LAUNCH();
+            });
+        }
+    }
+}
+
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                        int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode) {
     using Cx = typename cx_of<T>::type;
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
+    if (use16(M1, M2)) {
+        const int npairs = (nvec + 1) / 2;
+        const MvSched& want = dbl ? ctx->sched64 : ctx->sched32;
+        const int ppb = want.pairs_per_batch > 0 ? std::min(want.pairs_per_batch, npairs) : npairs;
+        DevBuf& sb = dbl ? ctx->slab64 : ctx->slab32;
+        sb.ensure((size_t)n1 * M2 * cx_size(dbl) * ppb);
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (ctx->prof_on) {
+            KRY_CUDA(cudaEventCreate(&ev0));
+            KRY_CUDA(cudaEventCreate(&ev1));
+            KRY_CUDA(cudaEventRecord(ev0, ctx->stream));
+        }
+        run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb);
+        if (ctx->prof_on) {
+            KRY_CUDA(cudaEventRecord(ev1, ctx->stream));
+            ctx->prof_ev.push_back(ev0);
+            ctx->prof_ev.push_back(ev1);
+            ctx->prof_nvec.push_back(nvec);
+            ctx->prof_dbl.push_back(dbl ? 1 : 0);
+        }
+        return;
+    }
     MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, M1, M2, dbl);
     const int npairs = (nvec + 1) / 2;
     int ppb = s.pairs_per_batch > 0 ? std::min(s.pairs_per_batch, npairs) : npairs;
@@ -373,6 +714,11 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
 }
 
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl) {
+    if (use16(e->M1, e->M2)) {
+        int G, C;
+        sched16(ctx, e->M1, e->M2, dbl, &G, &C);
+        return (e->n1 + G - 1) / G;
+    }
     MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, e->M1, e->M2, dbl);
     return (e->n1 + s.rows_per_cta - 1) / s.rows_per_cta;
 }

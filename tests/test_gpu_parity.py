@@ -82,6 +82,34 @@ def test_matvec_parity(ctx, n1, n2, cov, frac, kind, prec):
     emb.free()
 
 
+@pytest.mark.parametrize("n1,n2,cov,frac,kind,nvec", [
+    # the grid1024 workload at full size, in the batch width the Lanczos loop uses
+    (1024, 1024, I.WORKLOADS["grid1024"].cov, 0.5, "uniform", 64),
+    (1500, 700, I.Cov(1.0, 0.03, 1.5, 0.05), 0.3, "circles", 3),     # M = 4096 x 2048
+    (2100, 200, I.Cov(1.0, 0.02, 0.5, 0.05), 0.5, "uniform", 2),     # M1 = 8192
+    (96, 4096, I.Cov(1.0, 0.02, 0.5, 0.05, angle=0.4, ratio=2.0), 0.3, "uniform", 2),   # M2 = 8192
+])
+def test_matvec_parity_large(ctx, n1, n2, cov, frac, kind, nvec):
+    mask = make_mask(n1, n2, frac, kind)
+    p = set_mask(ctx, mask)
+    P = O.FFTProblem(n1, n2, mask, cov)
+    V = I.normals((nvec, p), 5)
+    emb = ctx.embed(cov, kry.KRY_F32)
+    out = ctx.matvec(emb, torch.tensor(V, dtype=torch.float32, device=DEV)).double().cpu().numpy()
+    check = [0, nvec - 1] if nvec > 2 else list(range(nvec))
+    ref = P.matvec(V[check])
+    for a, k in enumerate(check):
+        assert relerr(out[k], ref[a]) <= 1e-5, (k, relerr(out[k], ref[a]))
+    emb.free()
+    if n1 * n2 <= 1024 * 1024:
+        emb = ctx.embed(cov, kry.KRY_F64)
+        out = ctx.matvec(emb, torch.tensor(V[:2], device=DEV)).cpu().numpy()
+        ref = P.matvec(V[:2])
+        for k in range(2):
+            assert relerr(out[k], ref[k]) <= 1e-12
+        emb.free()
+
+
 def test_matvec_matches_dense_brute_force(ctx):
     n1, n2 = 12, 9
     cov = I.Cov(1.3, 0.3, 1.0, 0.07)
