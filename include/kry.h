@@ -209,6 +209,22 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
  * size tried if none qualifies.  Synchronises the stream. */
 kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2);
 
+/* Schedule autotuner (no counterpart in the paper; the paper names no GPU
+ * schedule).  Times every feasible launch schedule of the covariance matvec on
+ * embedding e for batches of nvec vectors -- rows per block of the row passes,
+ * columns per block (= slab tile width) of the column pass, and complex pairs
+ * per batch (all, or chunks whose FFT intermediate fits ~32/64 MB of L2) --
+ * and keeps the fastest for (M1, M2, precision, batch-size bucket) in ctx;
+ * every later matvec, log-det, solve and likelihood on ctx with that shape
+ * uses it.  Reports the best time per call (ms) and the chosen schedule
+ * (host pointers, each may be NULL).  Allocates and frees two test buffers
+ * of nvec * p values.  Synchronises the stream. */
+kry_status kry_autotune(kry_ctx* ctx, const kry_embed* e, int32_t nvec, double* best_ms,
+                        int32_t* rows_per_block, int32_t* cols_per_block, int32_t* pairs_per_batch);
+/* Set that schedule explicitly (0 = library default for each field). */
+kry_status kry_set_schedule(kry_ctx* ctx, const kry_embed* e, int32_t nvec, int32_t rows_per_block,
+                            int32_t cols_per_block, int32_t pairs_per_batch);
+
 /* Diagnostics (no counterpart in the paper).  kry_profile_enable(ctx, 1)
  * starts timing every covariance matvec issued on ctx (the three FFT passes
  * of one call, CUDA events on the context stream) and clears earlier records;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -102,6 +103,8 @@ struct kry_ctx {
     int max_smem_optin = 0;
 
     MvSched sched32, sched64;
+    // autotuned / user-set schedules keyed by (M1, M2, precision, batch bucket)
+    std::map<uint64_t, MvSched> tuned;
 
     // optional timing of every matvec (CUDA events on the context stream)
     bool prof_on = false;
@@ -148,6 +151,10 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
 void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out);
 
 int smem_limit(kry_ctx* ctx);
+
+// Schedule key and lookup (falls back to the per-precision default).
+uint64_t sched_key(int M1, int M2, bool dbl, int nvec);
+const MvSched& sched_for(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec);
 
 struct SolveInfo {
     int iters = 0;

@@ -24,7 +24,7 @@ namespace kry {
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                int64_t ld_out, int nvec, double* dots, int nds);
-int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl);
+int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
 
 static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
 
@@ -204,7 +204,7 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nst
     const bool dbl = sizeof(T) == 8;
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
-    const int nblkC = matvec_num_partials(ctx, e, dbl);
+    const int nblkC = matvec_num_partials(ctx, e, dbl, nprobe);
     const size_t vbytes = (size_t)nprobe * p * sizeof(T);
     for (int b = 0; b < 4; ++b) ctx->work[b].ensure(vbytes);
     T* U = ctx->work[0].as<T>();
@@ -384,7 +384,7 @@ static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t l
     T* R = ctx->work[7].as<T>();
     T* P = ctx->work[8].as<T>();
     T* Q = ctx->work[9].as<T>();
-    const int nblkC = matvec_num_partials(ctx, e, dbl);
+    const int nblkC = matvec_num_partials(ctx, e, dbl, nrhs);
     ctx->work[10].ensure((size_t)nrhs * std::max(nblkC, RED_BLOCKS) * sizeof(double));
     double* part = ctx->work[10].as<double>();
     ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);

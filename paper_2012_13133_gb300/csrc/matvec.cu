@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(512) k16_pass_a(const T* __restrict__ vin, int
         if (row < n1) out[(int64_t)(pos >> logC) * tstride + (pos & (C - 1))] = z;
     };
     Cx v[16];
-    kry16::transform<Cx, false>(b, v, t, tw, ld_0, ld_s, st_s, st_g, true, false);
+    kry16::transform<Cx, false, true>(b, v, t, tw, ld_0, ld_s, st_s, st_g, true, false);
 }
 
 template <typename T, int CC>
@@ -313,11 +313,14 @@ __global__ void __launch_bounds__(512) k16_pass_b(typename cx_of<T>::type* __res
     // forward column transform, ending in registers (slot m = row t + m L/16)
     {
         const int r0 = kry16::stage_radix(b, 0);
+        // rows >= n1 (>= M1/2) are zero: half-input first stage
+        using LDG = decltype(ld_g)&;
+        using STS = decltype(st_s)&;
         switch (r0) {
-            case 2: kry16::stage<Cx, 2, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
-            case 4: kry16::stage<Cx, 4, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
-            case 8: kry16::stage<Cx, 8, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
-            default: kry16::stage<Cx, 16, false>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            case 2: kry16::stage<Cx, 2, false, LDG, STS, true>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            case 4: kry16::stage<Cx, 4, false, LDG, STS, true>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            case 8: kry16::stage<Cx, 8, false, LDG, STS, true>(v, t, L, 1, tw, ld_g, st_s, false); break;
+            default: kry16::stage<Cx, 16, false, LDG, STS, true>(v, t, L, 1, tw, ld_g, st_s, false); break;
         }
         __syncthreads();
         int Ns = r0;
@@ -529,6 +532,10 @@ static MvSched pick_sched(kry_ctx* ctx, const MvSched& want, int M1, int M2, boo
 
 // ---- radix-16 path: schedule, shared-memory pad shift and launches
 
+#ifndef KRY_SMEM_CARVEOUT
+#define KRY_SMEM_CARVEOUT -1   // L1 / shared-memory split: driver default (measured fastest)
+#endif
+
 static bool use16(int M1, int M2) { return M1 >= 64 && M2 >= 64 && M1 <= KRY_MAX_M && M2 <= KRY_MAX_M; }
 
 // Pad shift of the interleaved shared-memory layout for NT transforms of
@@ -547,9 +554,25 @@ static size_t smem16(int L, int NT, bool dbl) {
 
 static int ilog2(int x) { return 31 - __builtin_clz((unsigned)x); }
 
+static int batch_bucket(int nvec) {
+    int b = 1;
+    while (b < nvec && b < 64) b <<= 1;
+    return b;
+}
+
+uint64_t sched_key(int M1, int M2, bool dbl, int nvec) {
+    return (uint64_t)M1 | ((uint64_t)M2 << 16) | ((uint64_t)(dbl ? 1 : 0) << 32) | ((uint64_t)batch_bucket(nvec) << 40);
+}
+
+const MvSched& sched_for(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec) {
+    auto it = ctx->tuned.find(sched_key(M1, M2, dbl, nvec));
+    if (it != ctx->tuned.end()) return it->second;
+    return dbl ? ctx->sched64 : ctx->sched32;
+}
+
 // Rows per block (pass A/C) and columns per block (pass B, = slab tile width).
-static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int* G, int* C) {
-    const MvSched& want = dbl ? ctx->sched64 : ctx->sched32;
+static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, int* C) {
+    const MvSched& want = sched_for(ctx, M1, M2, dbl, nvec);
     const size_t lim = (size_t)ctx->max_smem_optin;
     auto fit = [&](int L, int nt) {
         nt = std::max(1, std::min(nt, 16));
@@ -581,7 +604,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
     int G, C;
-    sched16(ctx, M1, M2, dbl, &G, &C);
+    sched16(ctx, M1, M2, dbl, nvec, &G, &C);
     const int npairs = (nvec + 1) / 2;
     const T* lamT = dbl ? reinterpret_cast<const T*>(e->lam64T) : reinterpret_cast<const T*>(e->lam32T);
     const int* rowptr = ctx->rowptr.as<int>();
@@ -600,6 +623,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
         KRY_DISPATCH_NT(G, {
             auto k = k16_pass_a<T, N_>;
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
             k<<<gA, thrA, smA, st>>>(vin, ld_in, scale, nvec, pair0, rowptr, colidx, n1, n2, M2, C, logC, psA, slab,
                                     tw32, tw64);
             KRY_CHECK_LAUNCH();
@@ -607,6 +631,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
         KRY_DISPATCH_NT(C, {
             auto k = k16_pass_b<T, N_>;
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
+            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
             k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64);
             KRY_CHECK_LAUNCH();
         });
@@ -614,6 +639,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
             KRY_DISPATCH_NT(G, {
                 auto k = k16_pass_c<T, N_, 0>;
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+                KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
                                         M2, C, logC, psA, tau2, dots, nds, tw32, tw64);
                 KRY_CHECK_LAUNCH();
@@ -638,7 +664,7 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
     if (use16(M1, M2)) {
         const int npairs = (nvec + 1) / 2;
-        const MvSched& want = dbl ? ctx->sched64 : ctx->sched32;
+        const MvSched& want = sched_for(ctx, M1, M2, dbl, nvec);
         const int ppb = want.pairs_per_batch > 0 ? std::min(want.pairs_per_batch, npairs) : npairs;
         DevBuf& sb = dbl ? ctx->slab64 : ctx->slab32;
         sb.ensure((size_t)n1 * M2 * cx_size(dbl) * ppb);
@@ -713,10 +739,12 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
     }
 }
 
-int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl) {
+// Number of per-block dot partials pass C writes per vector for a batch of
+// nvec vectors (the Krylov finalisers sum exactly this many).
+int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec) {
     if (use16(e->M1, e->M2)) {
         int G, C;
-        sched16(ctx, e->M1, e->M2, dbl, &G, &C);
+        sched16(ctx, e->M1, e->M2, dbl, nvec, &G, &C);
         return (e->n1 + G - 1) / G;
     }
     MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, e->M1, e->M2, dbl);
@@ -862,5 +890,149 @@ extern "C" kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const
     } catch (const std::exception& err) {
         ctx->err = err.what();
         return KRY_ECUDA;
+    }
+}
+
+// ------------------------------------------------------------------ schedule autotuner
+//
+// Times every feasible radix-16 schedule (rows per block for the row passes,
+// columns per block = slab tile width for the column pass, complex pairs per
+// batch: all at once, or chunks whose slab stays within ~32 or ~64 MB of L2)
+// on the caller's embedding and batch width, and caches the fastest for
+// (M1, M2, precision, batch bucket).
+
+namespace kry {
+
+template <typename T>
+__global__ void k_fill_test(T* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (T)(((i * 2654435761ll) & 1023) - 511) * (T)(1.0 / 512.0);
+}
+
+template <typename T>
+static double time_sched(kry_ctx* ctx, const kry_embed* e, const T* v, T* out, int nvec, int reps) {
+    cudaEvent_t a, b;
+    KRY_CUDA(cudaEventCreate(&a));
+    KRY_CUDA(cudaEventCreate(&b));
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false;
+    run_matvec<T>(ctx, e, v, ctx->p, nullptr, out, ctx->p, nvec, e->cov.tau2, nullptr, 0, 0);   // warm-up
+    KRY_CUDA(cudaEventRecord(a, ctx->stream));
+    for (int r = 0; r < reps; ++r)
+        run_matvec<T>(ctx, e, v, ctx->p, nullptr, out, ctx->p, nvec, e->cov.tau2, nullptr, 0, 0);
+    KRY_CUDA(cudaEventRecord(b, ctx->stream));
+    KRY_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    KRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->prof_on = prof;
+    return ms / reps;
+}
+
+template <typename T>
+static double autotune_t(kry_ctx* ctx, const kry_embed* e, int nvec, MvSched* best_out) {
+    const bool dbl = sizeof(T) == 8;
+    const int M1 = e->M1, M2 = e->M2;
+    const uint64_t key = sched_key(M1, M2, dbl, nvec);
+    const size_t n = (size_t)nvec * ctx->p;
+    DevBuf tv, to;
+    tv.ensure(n * sizeof(T));
+    to.ensure(n * sizeof(T));
+    k_fill_test<T><<<1024, 256, 0, ctx->stream>>>(tv.as<T>(), (int64_t)n);
+    KRY_CHECK_LAUNCH();
+    const int npairs = (nvec + 1) / 2;
+    const size_t slab_pair = (size_t)e->n1 * M2 * cx_size(dbl);
+    std::vector<int> ppbs = {0};
+    for (size_t budget : {(size_t)32 << 20, (size_t)64 << 20}) {
+        const int c = (int)std::max<size_t>(1, budget / slab_pair);
+        if (c < npairs && std::find(ppbs.begin(), ppbs.end(), c) == ppbs.end()) ppbs.push_back(c);
+    }
+    const size_t lim = (size_t)ctx->max_smem_optin;
+    double best = 1e30;
+    MvSched bs = dbl ? ctx->sched64 : ctx->sched32;
+    const bool had = ctx->tuned.count(key) > 0;
+    const MvSched prev = had ? ctx->tuned[key] : bs;
+    if (use16(M1, M2)) {
+        for (int g : {1, 2, 4, 8, 16}) {
+            if (g * (M2 >> 4) > 512 || smem16(M2, g, dbl) > lim) continue;
+            for (int c : {1, 2, 4, 8, 16}) {
+                if (c * (M1 >> 4) > 512 || smem16(M1, c, dbl) > lim || c > M2) continue;
+                for (int ppb : ppbs) {
+                    MvSched cand = bs;
+                    cand.g16 = g;
+                    cand.c16 = c;
+                    cand.pairs_per_batch = ppb;
+                    ctx->tuned[key] = cand;
+                    const double ms = time_sched<T>(ctx, e, tv.as<T>(), to.as<T>(), nvec, 3);
+                    if (ms < best) {
+                        best = ms;
+                        bs = cand;
+                    }
+                }
+            }
+        }
+        ctx->tuned[key] = bs;
+    } else {
+        if (had) ctx->tuned[key] = prev;
+        best = time_sched<T>(ctx, e, tv.as<T>(), to.as<T>(), nvec, 3);
+    }
+    tv.release();
+    to.release();
+    if (best_out) *best_out = bs;
+    return best;
+}
+
+double autotune(kry_ctx* ctx, const kry_embed* e, int nvec, MvSched* best) {
+    return e->prec == KRY_F64 ? autotune_t<double>(ctx, e, nvec, best) : autotune_t<float>(ctx, e, nvec, best);
+}
+
+}  // namespace kry
+
+extern "C" kry_status kry_autotune(kry_ctx* ctx, const kry_embed* e, int32_t nvec, double* best_ms,
+                                   int32_t* rows_per_block, int32_t* cols_per_block, int32_t* pairs_per_batch) {
+    if (!ctx) return KRY_EINVAL;
+    try {
+        KRY_CUDA(cudaSetDevice(ctx->device));
+        ctx->err.clear();
+        KRY_REQUIRE(e != nullptr && e->ctx == ctx, KRY_EINVAL, "embedding is NULL or belongs to another context");
+        KRY_REQUIRE(ctx->p > 0 && e->n1 == ctx->n1 && e->n2 == ctx->n2, KRY_EINVAL,
+                    "no mask set, or the embedding grid differs from the mask grid");
+        KRY_REQUIRE(nvec >= 1, KRY_EINVAL, "nvec must be >= 1");
+        MvSched b;
+        const double ms = kry::autotune(ctx, e, nvec, &b);
+        if (best_ms) *best_ms = ms;
+        if (rows_per_block) *rows_per_block = b.g16;
+        if (cols_per_block) *cols_per_block = b.c16;
+        if (pairs_per_batch) *pairs_per_batch = b.pairs_per_batch;
+        return KRY_OK;
+    } catch (const KryError& err) {
+        ctx->err = err.msg;
+        return err.st;
+    } catch (const std::exception& err) {
+        ctx->err = err.what();
+        return KRY_ECUDA;
+    }
+}
+
+extern "C" kry_status kry_set_schedule(kry_ctx* ctx, const kry_embed* e, int32_t nvec, int32_t rows_per_block,
+                                       int32_t cols_per_block, int32_t pairs_per_batch) {
+    if (!ctx) return KRY_EINVAL;
+    try {
+        KRY_REQUIRE(e != nullptr && e->ctx == ctx, KRY_EINVAL, "embedding is NULL or belongs to another context");
+        auto pow2 = [](int x) { return x >= 0 && (x & (x - 1)) == 0; };
+        KRY_REQUIRE(nvec >= 1 && pow2(rows_per_block) && pow2(cols_per_block) && rows_per_block <= 16 &&
+                        cols_per_block <= 16 && pairs_per_batch >= 0,
+                    KRY_EINVAL, "rows/cols per block must be 0 (default) or a power of two <= 16; pairs >= 0");
+        const bool dbl = e->prec == KRY_F64;
+        MvSched s = dbl ? ctx->sched64 : ctx->sched32;
+        s.g16 = rows_per_block;
+        s.c16 = cols_per_block;
+        s.pairs_per_batch = pairs_per_batch;
+        ctx->tuned[kry::sched_key(e->M1, e->M2, dbl, nvec)] = s;
+        return KRY_OK;
+    } catch (const KryError& err) {
+        ctx->err = err.msg;
+        return err.st;
     }
 }

@@ -64,6 +64,9 @@ SIGNATURES = {
                             _P, _P, C.c_int64, _P, _P, _P, _DP]),
     "kry_sample": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int32, C.c_int32, _P, _P]),
     "kry_sample_size": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "kry_autotune": (C.c_int, [_P, _P, C.c_int32, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32)]),
+    "kry_set_schedule": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "kry_profile_enable": (C.c_int, [_P, C.c_int]),
     "kry_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _DP]),
     "kry_launch_count": (C.c_uint64, []),
@@ -255,6 +258,17 @@ class Context:
                                         ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms), _ptr(vc),
                                         _np_dp(beta)), allow=(KRY_ENOCONV,))
         return dict(mean_cells=mc, mean_sites=ms, var_cells=vc, beta=beta, status=st)
+
+    def autotune(self, emb: Embed, nvec: int):
+        """Time the feasible matvec schedules for batches of nvec; keep the fastest."""
+        ms = C.c_double()
+        g, c, ppb = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(_lib.kry_autotune(self.h, emb.handle, nvec, C.byref(ms), C.byref(g), C.byref(c), C.byref(ppb)))
+        return dict(ms=ms.value, rows_per_block=g.value, cols_per_block=c.value, pairs_per_batch=ppb.value)
+
+    def set_schedule(self, emb: Embed, nvec: int, rows_per_block=0, cols_per_block=0, pairs_per_batch=0):
+        self._check(_lib.kry_set_schedule(self.h, emb.handle, nvec, rows_per_block, cols_per_block,
+                                          pairs_per_batch))
 
     def profile_enable(self, on=True):
         self._check(_lib.kry_profile_enable(self.h, 1 if on else 0))

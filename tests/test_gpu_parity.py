@@ -110,6 +110,33 @@ def test_matvec_parity_large(ctx, n1, n2, cov, frac, kind, nvec):
         emb.free()
 
 
+def test_schedules_and_autotune_keep_parity(ctx):
+    n1, n2 = 300, 260
+    cov = I.Cov(1.0, 0.05, 1.5, 0.05)
+    mask = make_mask(n1, n2, 0.5, "uniform")
+    p = set_mask(ctx, mask)
+    P = O.FFTProblem(n1, n2, mask, cov)
+    V = I.normals((5, p), 8)
+    ref = P.matvec(V)
+    emb = ctx.embed(cov, kry.KRY_F32)
+    Vt = torch.tensor(V, dtype=torch.float32, device=DEV)
+    for g, c, ppb in [(1, 1, 1), (4, 2, 0), (16, 16, 0), (2, 8, 1), (8, 4, 2)]:
+        ctx.set_schedule(emb, 5, g, c, ppb)
+        out = ctx.matvec(emb, Vt).double().cpu().numpy()
+        for k in range(5):
+            assert relerr(out[k], ref[k]) <= 1e-5, (g, c, ppb, k)
+    best = ctx.autotune(emb, 5)
+    assert best["ms"] > 0 and best["rows_per_block"] >= 1 and best["cols_per_block"] >= 1
+    out = ctx.matvec(emb, Vt).double().cpu().numpy()
+    for k in range(5):
+        assert relerr(out[k], ref[k]) <= 1e-5
+    # the Krylov loops pick up the tuned schedule (their dot partials follow it)
+    ld, _, per = ctx.logdet(emb, 5, 20, 1)
+    ld_o, _, per_o = P.logdet(5, 20, 1)
+    assert abs(ld - ld_o) <= 1e-3 * abs(ld_o)
+    emb.free()
+
+
 def test_matvec_matches_dense_brute_force(ctx):
     n1, n2 = 12, 9
     cov = I.Cov(1.3, 0.3, 1.0, 0.07)
