@@ -39,7 +39,8 @@
  *   Precision  KRY_F32: FP32 vectors and FFTs, FP64 Krylov scalars (alpha,
  *              beta, dot products, quadrature).  KRY_F64: FP64 throughout.
  *              Solves always take and return FP64 vectors; with KRY_F32 they
- *              run FP32 CG inside FP64 iterative refinement.
+ *              run FP32 CG whose solution accumulates in FP64 and whose
+ *              residual is periodically replaced by the true FP64 residual.
  */
 #ifndef KRY_H
 #define KRY_H
@@ -80,15 +81,14 @@ typedef struct {
 } kry_cov;
 
 /* Krylov settings.  nprobe Rademacher probes x nsteps Lanczos steps for the
- * log-determinant; CG to relative residual rtol (maxit iterations at most) with
- * up to `refine` FP64 refinement rounds when prec = KRY_F32. */
+ * log-determinant; CG to true relative residual rtol (maxit iterations at most
+ * per right-hand side). */
 typedef struct {
     kry_prec prec;
     int32_t nprobe, nsteps;
     uint64_t seed;
     double rtol;
     int32_t maxit;
-    int32_t refine;
 } kry_opts;
 
 typedef struct kry_ctx kry_ctx;       /* opaque, library-owned */
@@ -153,14 +153,18 @@ kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t 
                       uint64_t seed, double* logdet, double* stderr_out, double* per_probe);
 
 /* Solve K X = B for nrhs FP64 right-hand sides (column-major, leading
- * dimension ld) by CG from X = 0 to ||B - K X|| <= rtol ||B|| per column.
- * With KRY_F32 embeddings the CG runs in FP32 with FP64 scalars inside at
- * most `refine` FP64 refinement rounds (true residual by the FP64 matvec).
- * iters (host, may be NULL) receives the total CG iterations, relres (host,
- * may be NULL) the largest final relative residual.  Returns KRY_ENOCONV,
- * with X filled, when rtol was not reached.  Synchronises the stream. */
+ * dimension ld) by CG from X = 0 until the true residual satisfies
+ * ||B - K X|| <= rtol ||B|| per column.  FP64 embeddings run FP64 CG.  FP32
+ * embeddings run FP32 CG (FP32 matvec, FP64 scalars) with the solution
+ * accumulated in FP64 and the recursive residual replaced by the true
+ * residual from the FP64 matvec whenever it has fallen 10x or reached rtol
+ * (reliable updates; convergence is judged on true residuals only).
+ * iters (host, may be NULL) receives the largest per-column iteration count,
+ * relres (host, may be NULL) the largest final true relative residual.
+ * Returns KRY_ENOCONV, with X filled, when rtol was not reached within maxit
+ * iterations.  Synchronises the stream. */
 kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev,
-                     int32_t nrhs, int64_t ld, double rtol, int32_t maxit, int32_t refine,
+                     int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
                      int32_t* iters, double* relres);
 
 /* Marginal log-likelihood of the observed cells with beta profiled by GLS,
@@ -168,7 +172,7 @@ kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, doub
  *   beta = (X^T K^-1 X)^-1 X^T K^-1 y,  r = y - X beta,
  *   loglik = -1/2 [log det K + r^T K^-1 r + p log 2 pi],
  * log det K by kry_logdet's estimator (opts->nprobe, nsteps, seed), the solves
- * by kry_solve (opts->rtol, maxit, refine).  It equals the paper's exact
+ * by kry_solve (opts->rtol, maxit).  It equals the paper's exact
  * profile likelihood (Eq. exact_plik) minus 1/2 log det Gamma^-1 and a
  * constant.  y_dev: p FP64; X_dev: p x ncov FP64 column-major (1 <= ncov <= 8).
  * Host outputs: loglik[ntheta], beta[ntheta * ncov], logdet[ntheta],
@@ -193,6 +197,20 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts,
                      const double* sites_dev, const double* Xs_dev, int64_t nsite,
                      double* mean_cells_dev, double* mean_sites_dev, double* var_cells_dev,
                      double* beta_out);
+
+/* One evaluation for one covariance setting: the profile log-likelihood of
+ * kry_profile_loglik (log det K by SLQ, GLS beta, loglik) together with the
+ * kriging means (and optional variances) of kry_krige, sharing one embedding
+ * and one solve of K^-1 [y, X] (the kriging weights K^-1 (y - X beta) follow
+ * from it without another solve).  Arguments as in those two calls; loglik,
+ * beta[ncov], logdet and logdet_se are host outputs (all but loglik may be
+ * NULL).  Synchronises the stream. */
+kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts,
+                            const double* y_dev, const double* X_dev, int32_t ncov,
+                            const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,
+                            const double* sites_dev, const double* Xs_dev, int64_t nsite,
+                            double* mean_cells_dev, double* mean_sites_dev, double* var_cells_dev,
+                            double* loglik, double* beta, double* logdet, double* logdet_se);
 
 /* Circulant-embedding sample of the latent process on the n1 x n2 grid of the
  * last kry_set_mask (Sec. 3.5 bootstrap): out = Re FFT2( sqrt(max(Lambda, 0) /

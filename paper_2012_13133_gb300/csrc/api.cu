@@ -18,7 +18,7 @@ void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, co
                int64_t ld_out, int nvec, double* dots, int nds);
 void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe);
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit, int refine);
+                double rtol, int maxit);
 GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet);
 void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_dev, double* w);
 void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, int64_t ncell, const double* Xc,
@@ -26,7 +26,7 @@ void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, 
 void krige_launch_sites(kry_ctx* ctx, const kry_cov& cov, const double* sites, int64_t nsite, const double* Xs,
                         int ncov, const double* beta_dev, const double* w, double* mean);
 bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
-                     double rtol, int maxit, int refine);
+                     double rtol, int maxit);
 }  // namespace kry
 
 std::atomic<unsigned long long> g_kry_launches{0};
@@ -354,13 +354,13 @@ kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t 
 }
 
 kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev, int32_t nrhs, int64_t ld,
-                     double rtol, int32_t maxit, int32_t refine, int32_t* iters, double* relres) {
+                     double rtol, int32_t maxit, int32_t* iters, double* relres) {
     return guarded(ctx, [&]() -> kry_status {
         check_embed(ctx, e);
         KRY_REQUIRE(B_dev && X_dev, KRY_EINVAL, "B_dev and X_dev must not be NULL");
         KRY_REQUIRE(nrhs >= 1 && nrhs <= 1024 && ld >= ctx->p, KRY_EINVAL, "need 1 <= nrhs <= 1024 and ld >= p");
-        KRY_REQUIRE(rtol > 0 && maxit >= 1 && refine >= 0, KRY_EINVAL, "need rtol > 0, maxit >= 1, refine >= 0");
-        kry::SolveInfo si = kry::solve(ctx, e, B_dev, ld, X_dev, ld, nrhs, rtol, maxit, refine);
+        KRY_REQUIRE(rtol > 0 && maxit >= 1, KRY_EINVAL, "need rtol > 0 and maxit >= 1");
+        kry::SolveInfo si = kry::solve(ctx, e, B_dev, ld, X_dev, ld, nrhs, rtol, maxit);
         if (iters) *iters = si.iters;
         if (relres) *relres = si.relres;
         if (!isfinite(si.relres)) return fail(ctx, KRY_ENAN, "CG residual is NaN/Inf");
@@ -373,7 +373,7 @@ static void check_opts(const kry_opts* o) {
     KRY_REQUIRE(o != nullptr, KRY_EINVAL, "opts is NULL");
     KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64, KRY_EINVAL, "opts->prec invalid");
     KRY_REQUIRE(o->nprobe >= 1 && o->nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
-    KRY_REQUIRE(o->rtol > 0 && o->maxit >= 1 && o->refine >= 0, KRY_EINVAL, "need rtol > 0, maxit >= 1, refine >= 0");
+    KRY_REQUIRE(o->rtol > 0 && o->maxit >= 1, KRY_EINVAL, "need rtol > 0 and maxit >= 1");
 }
 
 // [y, X] packed into one (p x (ncov+1)) FP64 block and its solve Z = K^-1 [y, X].
@@ -388,7 +388,7 @@ static kry::SolveInfo solve_yx(kry_ctx* ctx, const kry_embed* e, const double* y
     KRY_CUDA(cudaMemcpyAsync(V + p, X, (size_t)ncov * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     *V_out = V;
     *Z_out = Z;
-    return kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit, o->refine);
+    return kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit);
 }
 
 kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
@@ -431,6 +431,58 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
     });
 }
 
+}  // extern "C"
+
+// Kriging means (and optional variances) from an embedding, the solve
+// Z = K^-1 [y, X] and its GLS beta; shared by kry_krige and kry_loglik_krige.
+static kry_status krige_from_solution(kry_ctx* ctx, kry_embed* e, const kry_cov& cov, const kry_opts* opts,
+                                      const double* Z, int ncov, const kry::GlsResult& g, const kry::SolveInfo& si,
+                                      const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,
+                                      const double* sites_dev, const double* Xs_dev, int64_t nsite,
+                                      double* mean_cells_dev, double* mean_sites_dev, double* var_cells_dev) {
+    const int64_t p = ctx->p;
+    const int64_t N = (int64_t)ctx->n1 * ctx->n2;
+    ctx->gbuf.ensure((size_t)(N + p + KRY_MAX_COV + 1) * sizeof(double));
+    double* grid = ctx->gbuf.as<double>();
+    double* w = grid + N;
+    double* bdev = w + p;
+    int* bad = reinterpret_cast<int*>(bdev + KRY_MAX_COV);
+    KRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    KRY_CUDA(cudaMemcpyAsync(bdev, g.beta, ncov * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    kry::resid_weights(ctx, Z, ncov, bdev, w);
+    if (ncell > 0) {
+        // sigma2 Sigma A^T w on every grid cell (FP64 FFT path, no nugget)
+        kry::sigma_to_grid64(ctx, e, w, grid, 1, p);
+        kry::krige_launch_cells(ctx, grid, cells_dev, ncell, Xc_dev, ncov, bdev, mean_cells_dev, bad);
+    }
+    kry::krige_launch_sites(ctx, cov, sites_dev, nsite, Xs_dev, ncov, bdev, w, mean_sites_dev);
+    bool vok = true;
+    if (var_cells_dev && ncell > 0)
+        vok = kry::krige_variances(ctx, e, cells_dev, ncell, var_cells_dev, opts->rtol, opts->maxit);
+    int* hbad = reinterpret_cast<int*>(ctx->host_pinned);
+    KRY_CUDA(cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (*hbad) return fail(ctx, KRY_EINVAL, "a target cell index lies outside the grid (its mean is NaN)");
+    if (!g.ok) return fail(ctx, KRY_ENAN, "X^T K^-1 X is singular");
+    if (!si.converged || !vok) return fail(ctx, KRY_ENOCONV, "CG did not reach rtol");
+    return KRY_OK;
+}
+
+static void check_krige_args(const kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
+                             const int64_t* cells_dev, const double* Xc_dev, int64_t ncell, const double* sites_dev,
+                             const double* Xs_dev, int64_t nsite, double* mean_cells_dev, double* mean_sites_dev) {
+    (void)ctx;
+    KRY_REQUIRE(y_dev && X_dev, KRY_EINVAL, "y_dev and X_dev must not be NULL");
+    KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
+    KRY_REQUIRE(ncell >= 0 && nsite >= 0, KRY_EINVAL, "ncell and nsite must be >= 0");
+    KRY_REQUIRE(ncell == 0 || (cells_dev && Xc_dev && mean_cells_dev), KRY_EINVAL,
+                "cells_dev, Xc_dev and mean_cells_dev are required when ncell > 0");
+    KRY_REQUIRE(nsite == 0 || (sites_dev && Xs_dev && mean_sites_dev), KRY_EINVAL,
+                "sites_dev, Xs_dev and mean_sites_dev are required when nsite > 0");
+}
+
+extern "C" {
+
 kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, const double* y_dev, const double* X_dev,
                      int32_t ncov, const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,
                      const double* sites_dev, const double* Xs_dev, int64_t nsite, double* mean_cells_dev,
@@ -439,13 +491,8 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
         require_mask(ctx);
         check_opts(opts);
         check_cov(cov);
-        KRY_REQUIRE(y_dev && X_dev, KRY_EINVAL, "y_dev and X_dev must not be NULL");
-        KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
-        KRY_REQUIRE(ncell >= 0 && nsite >= 0, KRY_EINVAL, "ncell and nsite must be >= 0");
-        KRY_REQUIRE(ncell == 0 || (cells_dev && Xc_dev && mean_cells_dev), KRY_EINVAL,
-                    "cells_dev, Xc_dev and mean_cells_dev are required when ncell > 0");
-        KRY_REQUIRE(nsite == 0 || (sites_dev && Xs_dev && mean_sites_dev), KRY_EINVAL,
-                    "sites_dev, Xs_dev and mean_sites_dev are required when nsite > 0");
+        check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
+                         mean_cells_dev, mean_sites_dev);
         kry_embed* e = make_embed(ctx, cov, opts->prec);
         kry_status st = KRY_OK;
         try {
@@ -454,32 +501,47 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
             kry::GlsResult g = kry::gls(ctx, V, Z, ncov, 0.0);
             if (beta_out)
                 for (int c = 0; c < ncov; ++c) beta_out[c] = g.beta[c];
-            const int64_t p = ctx->p;
-            const int64_t N = (int64_t)ctx->n1 * ctx->n2;
-            ctx->gbuf.ensure((size_t)(N + p + KRY_MAX_COV + 1) * sizeof(double));
-            double* grid = ctx->gbuf.as<double>();
-            double* w = grid + N;
-            double* bdev = w + p;
-            int* bad = reinterpret_cast<int*>(bdev + KRY_MAX_COV);
-            KRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
-            KRY_CUDA(cudaMemcpyAsync(bdev, g.beta, ncov * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-            kry::resid_weights(ctx, Z, ncov, bdev, w);
-            if (ncell > 0) {
-                // sigma2 Sigma A^T w on every grid cell (FP64 FFT path, no nugget)
-                kry::sigma_to_grid64(ctx, e, w, grid, 1, p);
-                kry::krige_launch_cells(ctx, grid, cells_dev, ncell, Xc_dev, ncov, bdev, mean_cells_dev, bad);
-            }
-            kry::krige_launch_sites(ctx, *cov, sites_dev, nsite, Xs_dev, ncov, bdev, w, mean_sites_dev);
-            bool vok = true;
-            if (var_cells_dev && ncell > 0)
-                vok = kry::krige_variances(ctx, e, cells_dev, ncell, var_cells_dev, opts->rtol, opts->maxit,
-                                           opts->refine);
-            int* hbad = reinterpret_cast<int*>(ctx->host_pinned);
-            KRY_CUDA(cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-            KRY_CUDA(cudaStreamSynchronize(ctx->stream));
-            if (*hbad) st = fail(ctx, KRY_EINVAL, "a target cell index lies outside the grid (its mean is NaN)");
-            else if (!g.ok) st = fail(ctx, KRY_ENAN, "X^T K^-1 X is singular");
-            else if (!si.converged || !vok) st = fail(ctx, KRY_ENOCONV, "CG did not reach rtol");
+            st = krige_from_solution(ctx, e, *cov, opts, Z, ncov, g, si, cells_dev, Xc_dev, ncell, sites_dev,
+                                     Xs_dev, nsite, mean_cells_dev, mean_sites_dev, var_cells_dev);
+        } catch (...) {
+            free_embed(e);
+            throw;
+        }
+        free_embed(e);
+        return st;
+    });
+}
+
+kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, const double* y_dev,
+                            const double* X_dev, int32_t ncov, const int64_t* cells_dev, const double* Xc_dev,
+                            int64_t ncell, const double* sites_dev, const double* Xs_dev, int64_t nsite,
+                            double* mean_cells_dev, double* mean_sites_dev, double* var_cells_dev, double* loglik,
+                            double* beta, double* logdet, double* logdet_se) {
+    return guarded(ctx, [&]() -> kry_status {
+        require_mask(ctx);
+        check_opts(opts);
+        check_cov(cov);
+        KRY_REQUIRE(loglik != nullptr, KRY_EINVAL, "loglik must not be NULL");
+        check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
+                         mean_cells_dev, mean_sites_dev);
+        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry_status st = KRY_OK;
+        try {
+            std::vector<double> vals(opts->nprobe);
+            kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+            double ld = 0, se = 0;
+            mean_se(vals, &ld, &se);
+            double *V, *Z;
+            kry::SolveInfo si = solve_yx(ctx, e, y_dev, X_dev, ncov, opts, &V, &Z);
+            kry::GlsResult g = kry::gls(ctx, V, Z, ncov, ld);
+            *loglik = g.loglik;
+            if (beta)
+                for (int c = 0; c < ncov; ++c) beta[c] = g.beta[c];
+            if (logdet) *logdet = ld;
+            if (logdet_se) *logdet_se = se;
+            st = krige_from_solution(ctx, e, *cov, opts, Z, ncov, g, si, cells_dev, Xc_dev, ncell, sites_dev,
+                                     Xs_dev, nsite, mean_cells_dev, mean_sites_dev, var_cells_dev);
+            if (st == KRY_OK && !isfinite(g.loglik)) st = fail(ctx, KRY_ENAN, "log-likelihood is NaN/Inf");
         } catch (...) {
             free_embed(e);
             throw;

@@ -1,7 +1,7 @@
 // Krylov loops on the covariance matvec:
 //   * stochastic Lanczos quadrature for log det K (Sec. 3.3 names stochastic
 //     trace estimation as the alternative to the circulant log-det);
-//   * conjugate gradients for K X = B with FP64 iterative refinement (the
+//   * conjugate gradients for K X = B with FP64 residual replacement (the
 //     matvec-only solves that replace the O(n^3) inversions of Sec. 3);
 //   * GLS beta and the profile log-likelihood; kriging means (the paper's
 //     x-hat, Eq. act_xhat, by Woodbury) and simple-kriging variances (the
@@ -435,14 +435,6 @@ static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t l
     return mx;
 }
 
-// X64 += (double) D; R64 = B - K X64 (FP64 matvec) and per-column norms.
-template <typename T>
-__global__ void k_accum(double* __restrict__ X, int64_t ldx, const T* __restrict__ D, int64_t p) {
-    const int k = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
-        X[(int64_t)k * ldx + i] += (double)D[(int64_t)k * p + i];
-}
-
 __global__ void k_residual(const double* __restrict__ B, int64_t ldb, const double* __restrict__ KX,
                            double* __restrict__ R, int64_t p, double* __restrict__ part) {
     const int k = blockIdx.y;
@@ -474,12 +466,6 @@ __global__ void k_set(double* x, int64_t n, double v) {
         x[i] = v;
 }
 
-__global__ void k_zero_cols(double* __restrict__ X, int64_t ldx, int64_t p) {
-    const int k = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
-        X[(int64_t)k * ldx + i] = 0.0;
-}
-
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                int64_t ld_out, int nvec, double* dots, int nds);
@@ -504,60 +490,257 @@ static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int
     KRY_CUDA(cudaStreamSynchronize(st));
 }
 
+// ------------------------------------------------------------------ reliable-update mixed-precision CG
+//
+// FP32 CG (FP32 matvec, FP64 scalars) whose solution accumulates in FP64 and
+// whose recursive FP32 residual is replaced by the true residual b - K x,
+// computed with the FP64 matvec, whenever it has fallen 10x since the last
+// replacement or reached the target (the "reliable updates" of van der Vorst
+// & Ye, "Residual replacement strategies for Krylov subspace iterative
+// methods", SIAM J. Sci. Comput. 2000).  The search direction is kept across
+// replacements, so the Krylov progress of FP64 CG is retained while every
+// matvec of the iteration runs in FP32.  Convergence is declared only on a
+// true FP64 residual.
+
+struct RcgState {
+    double* rr;       // [nrhs] current r^T r
+    double* rr_ref;   // [nrhs] r^T r at the last replacement
+    double* thr2;     // [nrhs] (rtol ||b||)^2
+    double* alpha;    // [nrhs]
+    double* beta;     // [nrhs]
+    int* done;        // [nrhs]
+    int* iters;       // [nrhs]
+    int* nwant;       // [1] columns asking for a replacement (or done)
+};
+
+// X = 0 (FP64), R = (float) B, P = R; partials of ||B||^2 (exact) per column.
+__global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, double* __restrict__ X, int64_t ldx,
+                            float* __restrict__ R, float* __restrict__ P, int64_t p, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        const double b = B[(int64_t)k * ldb + i];
+        X[(int64_t)k * ldx + i] = 0.0;
+        const float r = (float)b;
+        R[(int64_t)k * p + i] = r;
+        P[(int64_t)k * p + i] = r;
+        acc[0] += b * b;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+__global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part, int nblk, int nrhs,
+                                   const double* __restrict__ tol) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrhs) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+        S.rr[k] = s;
+        S.rr_ref[k] = s;
+        S.thr2[k] = tol[k] * tol[k] * s;
+        S.done[k] = (s == 0.0) ? 1 : 0;
+        S.iters[k] = 0;
+        S.alpha[k] = 0.0;
+        S.beta[k] = 0.0;
+    }
+    if (k == 0) *S.nwant = 0;
+}
+
+__global__ void k_rcg_alpha(RcgState S, const double* __restrict__ part, int nblk, int nrhs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrhs) return;
+    double pq = 0.0;
+    for (int b = 0; b < nblk; ++b) pq += part[(int64_t)k * nblk + b];
+    S.alpha[k] = (S.done[k] || !(pq > 0.0)) ? 0.0 : S.rr[k] / pq;
+}
+
+// X += alpha P (FP64), R -= alpha Q (FP32); partial ||R||^2.
+__global__ void k_rcg_update(double* __restrict__ X, int64_t ldx, float* __restrict__ R, const float* __restrict__ P,
+                             const float* __restrict__ Q, int64_t p, RcgState S, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    const double a = S.alpha[k];
+    const float af = (float)a;
+    const bool act = !S.done[k];
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+        float r = R[(int64_t)k * p + i];
+        if (act) {
+            X[(int64_t)k * ldx + i] += a * (double)P[(int64_t)k * p + i];
+            r -= af * Q[(int64_t)k * p + i];
+            R[(int64_t)k * p + i] = r;
+        }
+        acc[0] += (double)r * (double)r;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+// beta = rr_new / rr; ask for a residual replacement when r^T r fell 100x
+// (||r|| 10x) since the last one or reached the target.
+__global__ void k_rcg_beta(RcgState S, const double* __restrict__ part, int nblk, int nrhs, int maxit) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int want = 0;
+    if (k < nrhs) {
+        if (!S.done[k]) {
+            double s = 0.0;
+            for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+            S.iters[k] += 1;
+            S.beta[k] = (S.rr[k] > 0.0) ? s / S.rr[k] : 0.0;
+            S.rr[k] = s;
+            want = (s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit) ? 1 : 0;
+        } else {
+            S.beta[k] = 0.0;
+        }
+    }
+    const int n = __syncthreads_count(want);
+    if (threadIdx.x == 0) *S.nwant = n;
+}
+
+__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S) {
+    const int k = blockIdx.y;
+    if (S.done[k]) return;
+    const float b = (float)S.beta[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        P[(int64_t)k * p + i] = R[(int64_t)k * p + i] + b * P[(int64_t)k * p + i];
+}
+
+// Residual replacement: R = (float) R64, rr = rr_ref = ||R64||^2; done when
+// ||R64|| <= rtol ||B|| or the iteration budget is spent.
+__global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
+                              const double* __restrict__ norms, RcgState S, int maxit) {
+    const int k = blockIdx.y;
+    if (S.done[k]) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double rn = norms[2 * k];
+        S.rr[k] = rn * rn;
+        S.rr_ref[k] = rn * rn;
+        if (rn * rn <= S.thr2[k] || S.iters[k] >= maxit || !(rn == rn)) S.done[k] = 1;
+    }
+}
+
+__global__ void k_cg_zero_nwant(int* n) { *n = 0; }
+
+__global__ void k_count_done(RcgState S, int nrhs) {
+    int d = 0;
+    for (int k = 0; k < nrhs; ++k) d += S.done[k];
+    *S.nwant = d;
+}
+
+static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm);
+
+// Returns the largest per-column iteration count.
+static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx,
+                       int nrhs, double rtol, int maxit, std::vector<double>& nrm, bool* fresh) {
+    const int64_t p = ctx->p;
+    cudaStream_t st = ctx->stream;
+    const size_t vb = (size_t)nrhs * p * sizeof(float);
+    ctx->work[7].ensure(vb);
+    ctx->work[8].ensure(vb);
+    ctx->work[9].ensure(vb);
+    float* R = ctx->work[7].as<float>();
+    float* P = ctx->work[8].as<float>();
+    float* Q = ctx->work[9].as<float>();
+    const int nblkC = matvec_num_partials(ctx, e, false, nrhs);
+    ctx->work[10].ensure((size_t)nrhs * std::max(nblkC, RED_BLOCKS) * sizeof(double));
+    double* part = ctx->work[10].as<double>();
+    ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);
+    char* sb = ctx->work[11].as<char>();
+    RcgState S;
+    S.rr = reinterpret_cast<double*>(sb);
+    S.rr_ref = S.rr + nrhs;
+    S.thr2 = S.rr_ref + nrhs;
+    S.alpha = S.thr2 + nrhs;
+    S.beta = S.alpha + nrhs;
+    S.done = reinterpret_cast<int*>(S.beta + nrhs);
+    S.iters = S.done + nrhs;
+    S.nwant = S.iters + nrhs;
+    ctx->tolbuf.ensure(nrhs * sizeof(double));
+    std::vector<double> tol_h(nrhs, rtol);
+    KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    ctx->work[4].ensure((size_t)nrhs * p * sizeof(double));
+    double* R64 = ctx->work[4].as<double>();
+    ctx->kxbuf.ensure((size_t)nrhs * p * sizeof(double));
+
+    dim3 gv(RED_BLOCKS, nrhs);
+    const int tb = 128;
+    const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
+    k_rcg_start<<<gv, 256, 0, st>>>(B, ldb, X, ldx, R, P, p, part);
+    KRY_CHECK_LAUNCH();
+    k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, ctx->tolbuf.as<double>());
+    KRY_CHECK_LAUNCH();
+    int* hflag = reinterpret_cast<int*>(ctx->host_pinned);
+    const int poll = 8;
+    nrm.assign(2 * nrhs, 0.0);
+    *fresh = false;
+    for (int it = 0; it < maxit + poll; ++it) {
+        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC);
+        k_rcg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
+        KRY_CHECK_LAUNCH();
+        k_rcg_update<<<gv, 256, 0, st>>>(X, ldx, R, P, Q, p, S, part);
+        KRY_CHECK_LAUNCH();
+        k_rcg_beta<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
+        KRY_CHECK_LAUNCH();
+        k_rcg_pupdate<<<gv, 256, 0, st>>>(P, R, p, S);
+        KRY_CHECK_LAUNCH();
+        if ((it + 1) % poll == 0) {
+            KRY_CUDA(cudaMemcpyAsync(hflag, S.nwant, sizeof(int), cudaMemcpyDeviceToHost, st));
+            KRY_CUDA(cudaStreamSynchronize(st));
+            if (*hflag > 0) {
+                // residual replacement for every column still running
+                true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm);
+                double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
+                k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit);
+                KRY_CHECK_LAUNCH();
+                k_count_done<<<1, 1, 0, st>>>(S, nrhs);
+                KRY_CHECK_LAUNCH();
+                KRY_CUDA(cudaMemcpyAsync(hflag, S.nwant, sizeof(int), cudaMemcpyDeviceToHost, st));
+                KRY_CUDA(cudaStreamSynchronize(st));
+                if (*hflag >= nrhs) {
+                    *fresh = true;
+                    break;
+                }
+                k_cg_zero_nwant<<<1, 1, 0, st>>>(S.nwant);
+                KRY_CHECK_LAUNCH();
+            }
+        }
+    }
+    std::vector<int> its(nrhs);
+    KRY_CUDA(cudaMemcpyAsync(its.data(), S.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    KRY_CUDA(cudaStreamSynchronize(st));
+    int mx = 0;
+    for (int k = 0; k < nrhs; ++k) mx = std::max(mx, its[k]);
+    return mx;
+}
+
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit, int refine) {
+                double rtol, int maxit) {
     SolveInfo info;
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     KRY_REQUIRE(nrhs >= 1, KRY_EINVAL, "nrhs must be >= 1");
     KRY_REQUIRE(rtol > 0 && maxit >= 1, KRY_EINVAL, "rtol must be > 0 and maxit >= 1");
-    dim3 gv(RED_BLOCKS, nrhs);
-    // host-side per-column inner tolerances
-    DevBuf& tolbuf = ctx->tolbuf;
-    tolbuf.ensure(nrhs * sizeof(double));
-    std::vector<double> tol_h(nrhs);
+    ctx->kxbuf.ensure((size_t)nrhs * p * sizeof(double));
+    ctx->work[4].ensure((size_t)nrhs * p * sizeof(double));
+    double* R = ctx->work[4].as<double>();
+    std::vector<double> nrm;
+    bool fresh = false;
     if (e->prec == KRY_F64) {
-        for (int k = 0; k < nrhs; ++k) tol_h[k] = rtol;
-        KRY_CUDA(cudaMemcpyAsync(tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+        // plain FP64 CG
+        ctx->tolbuf.ensure(nrhs * sizeof(double));
+        std::vector<double> tol_h(nrhs, rtol);
+        KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
         double* Xd;
-        info.iters = cg_inner<double>(ctx, e, B, ldb, nrhs, tolbuf.as<double>(), maxit, &Xd);
+        info.iters = cg_inner<double>(ctx, e, B, ldb, nrhs, ctx->tolbuf.as<double>(), maxit, &Xd);
         KRY_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, p * sizeof(double), p * sizeof(double), nrhs,
                                    cudaMemcpyDeviceToDevice, st));
     } else {
-        k_zero_cols<<<gv, 256, 0, st>>>(X, ldx, p);
-        KRY_CHECK_LAUNCH();
+        // FP32 CG with FP64 solution and residual replacement
+        info.iters = cg_reliable(ctx, e, B, ldb, X, ldx, nrhs, rtol, maxit, nrm, &fresh);
     }
-    // FP64 refinement rounds (FP32 embeddings) / final residual (FP64)
-    DevBuf& Rb = ctx->work[4];
-    DevBuf& kxbuf = ctx->kxbuf;
-    kxbuf.ensure((size_t)nrhs * p * sizeof(double));
-    std::vector<double> nrm;
-    const int rounds = (e->prec == KRY_F64) ? 0 : std::max(1, refine + 1);
-    Rb.ensure((size_t)nrhs * p * sizeof(double));
-    double* R = Rb.as<double>();
-    if (e->prec == KRY_F64) {
-        true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
-    } else {
-        // start: R = B, norms
-        true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
-        for (int round = 0; round < rounds; ++round) {
-            bool all = true;
-            for (int k = 0; k < nrhs; ++k) {
-                const double rn = nrm[2 * k], bn = nrm[2 * k + 1];
-                const double rel = bn > 0 ? rn / bn : 0.0;
-                if (rel > rtol) all = false;
-                // inner tolerance relative to the current residual
-                tol_h[k] = (rn > 0) ? std::max(0.5 * rtol * bn / rn, 2e-6) : 1.0;
-            }
-            if (all) break;
-            KRY_CUDA(cudaMemcpyAsync(tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-            float* D;
-            info.iters += cg_inner<float>(ctx, e, R, p, nrhs, tolbuf.as<double>(), maxit, &D);
-            k_accum<float><<<gv, 256, 0, st>>>(X, ldx, D, p);
-            KRY_CHECK_LAUNCH();
-            true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, kxbuf.as<double>(), nrm);
-        }
-    }
+    // the reported residual is always the true FP64 residual of the returned X
+    if (!fresh) true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, ctx->kxbuf.as<double>(), nrm);
     info.relres = 0.0;
     for (int k = 0; k < nrhs; ++k) {
         const double bn = nrm[2 * k + 1];
@@ -781,7 +964,7 @@ void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_d
 
 // Simple-kriging variances at target cells, nb targets per batch of solves.
 bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
-                     double rtol, int maxit, int refine) {
+                     double rtol, int maxit) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     const int nb = 32;
@@ -797,7 +980,7 @@ bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int
         k_cross_cols<<<g, 256, 0, st>>>(cells, t0, ctx->cellidx.as<int>(), p, ctx->n2, (int64_t)ctx->n1 * ctx->n2, cp,
                                          cbuf.as<double>());
         KRY_CHECK_LAUNCH();
-        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit, refine);
+        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit);
         ok = ok && si.converged;
         k_var_final<<<k, 256, 0, st>>>(cbuf.as<double>(), sbuf.as<double>(), p, e->cov.sigma2, var, t0);
         KRY_CHECK_LAUNCH();

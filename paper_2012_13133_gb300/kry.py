@@ -40,7 +40,7 @@ class kry_cov(C.Structure):
 
 class kry_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("nprobe", C.c_int32), ("nsteps", C.c_int32), ("seed", C.c_uint64),
-                ("rtol", C.c_double), ("maxit", C.c_int32), ("refine", C.c_int32)]
+                ("rtol", C.c_double), ("maxit", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -56,12 +56,14 @@ SIGNATURES = {
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
     "kry_matvec_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
     "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, _DP, _DP, _DP]),
-    "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32, C.c_int32,
+    "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32,
                             C.POINTER(C.c_int32), _DP]),
     "kry_profile_loglik": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(kry_cov), C.c_int32, C.POINTER(kry_opts),
                                      _DP, _DP, _DP, _DP]),
     "kry_krige": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), _P, _P, C.c_int32, _P, _P, C.c_int64,
                             _P, _P, C.c_int64, _P, _P, _P, _DP]),
+    "kry_loglik_krige": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), _P, _P, C.c_int32, _P, _P,
+                                   C.c_int64, _P, _P, C.c_int64, _P, _P, _P, _DP, _DP, _DP, _DP]),
     "kry_sample": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int32, C.c_int32, _P, _P]),
     "kry_sample_size": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "kry_autotune": (C.c_int, [_P, _P, C.c_int32, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -123,10 +125,9 @@ class Opts:
     seed: int = 0
     rtol: float = 1e-6
     maxit: int = 5000
-    refine: int = 4
 
     def c(self) -> kry_opts:
-        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.refine)
+        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit)
 
 
 class Embed:
@@ -219,7 +220,7 @@ class Context:
                                     _np_dp(per)))
         return ld.value, se.value, per
 
-    def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, refine=4, X=None):
+    def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, X=None):
         """B: (nrhs, p) float64 CUDA tensor.  Returns (X, iters, relres, status)."""
         squeeze = B.dim() == 1
         Bm = B.reshape(1, -1) if squeeze else B
@@ -227,7 +228,7 @@ class Context:
             X = self.torch.empty_like(Bm)
         it, rr = C.c_int32(), C.c_double()
         st = self._check(_lib.kry_solve(self.h, emb.handle, _ptr(Bm), _ptr(X), Bm.shape[0], self.p, rtol, maxit,
-                                        refine, C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
+                                        C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
         return (X.reshape(-1) if squeeze else X), it.value, rr.value, st
 
     def profile_loglik(self, y, X, thetas, opts: Opts):
@@ -277,6 +278,28 @@ class Context:
         c, v, ms = C.c_int64(), C.c_int64(), C.c_double()
         self._check(_lib.kry_profile_read(self.h, prec, C.byref(c), C.byref(v), C.byref(ms)))
         return dict(calls=c.value, vectors=v.value, ms=ms.value)
+
+    def loglik_krige(self, cov, opts: Opts, y, X, cells=None, Xc=None, sites=None, Xs=None, variances=False,
+                     mean_cells=None):
+        """Profile log-likelihood and kriging means for one covariance setting (one shared solve)."""
+        torch = self.torch
+        ncov = X.shape[0]
+        ncell = 0 if cells is None else cells.shape[0]
+        nsite = 0 if sites is None else sites.shape[0]
+        dev = y.device
+        mc = mean_cells if mean_cells is not None else (
+            torch.empty(ncell, dtype=torch.float64, device=dev) if ncell else None)
+        ms = torch.empty(nsite, dtype=torch.float64, device=dev) if nsite else None
+        vc = torch.empty(ncell, dtype=torch.float64, device=dev) if (ncell and variances) else None
+        ll, beta, ld, se = C.c_double(), np.zeros(ncov), C.c_double(), C.c_double()
+        c = make_cov(cov)
+        o = opts.c()
+        st = self._check(_lib.kry_loglik_krige(self.h, C.byref(c), C.byref(o), _ptr(y), _ptr(X), ncov, _ptr(cells),
+                                               _ptr(Xc), ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms),
+                                               _ptr(vc), C.byref(ll), _np_dp(beta), C.byref(ld), C.byref(se)),
+                         allow=(KRY_ENOCONV,))
+        return dict(loglik=ll.value, beta=beta, logdet=ld.value, logdet_se=se.value, mean_cells=mc, mean_sites=ms,
+                    var_cells=vc, status=st)
 
     def sample_size(self, cov):
         m1, m2 = C.c_int32(), C.c_int32()

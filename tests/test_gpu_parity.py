@@ -273,7 +273,7 @@ def test_solve_parity(ctx, prec):
     K = O.dense_K(n1, n2, mask, cov)
     ref = np.linalg.solve(K, B.T).T
     emb = ctx.embed(cov, kry.KRY_F64 if prec == "f64" else kry.KRY_F32)
-    X, iters, relres, st = ctx.solve(emb, torch.tensor(B, device=DEV), rtol=1e-9, maxit=4000, refine=6)
+    X, iters, relres, st = ctx.solve(emb, torch.tensor(B, device=DEV), rtol=1e-9, maxit=4000)
     assert st == kry.KRY_OK and relres <= 1e-9
     Xn = X.cpu().numpy()
     for k in range(3):
@@ -304,7 +304,7 @@ def test_profile_loglik_batch_of_thetas_fp32(ctx):
     xi, eps = I.data_noise(M1, M2, p, 30)
     y, X, _ = O.make_data(n1, n2, mask, dcov, (1.0, 0.5, -0.5), xi, eps)
     thetas = [I.Cov(1.0, r, nu, 0.1) for r in (0.04, 0.08) for nu in (0.5, 1.0, 2.5)]
-    opts = kry.Opts(prec=kry.KRY_F32, nprobe=6, nsteps=40, seed=3, rtol=1e-8, maxit=4000, refine=6)
+    opts = kry.Opts(prec=kry.KRY_F32, nprobe=6, nsteps=40, seed=3, rtol=1e-8, maxit=4000)
     res = ctx.profile_loglik(torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV), thetas, opts)
     for t, th in enumerate(thetas):
         P = O.FFTProblem(n1, n2, mask, th)
@@ -344,12 +344,38 @@ def test_krige_masked_fp32_cells(ctx):
     cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
     S1, S2 = I.cell_centres(n1, n2)
     Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
-    opts = kry.Opts(prec=kry.KRY_F32, rtol=1e-8, maxit=4000, refine=6)
+    opts = kry.Opts(prec=kry.KRY_F32, rtol=1e-8, maxit=4000)
     res = ctx.krige(cov, opts, torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV),
                     cells=torch.tensor(cells, device=DEV), Xc=torch.tensor(Xc.T.copy(), device=DEV))
     cs = np.stack([S1.ravel()[cells], S2.ravel()[cells]], axis=1)
     mc, _ = O.krige_dense(n1, n2, mask, cov, y, X, cs, Xc)
     assert relerr(res["mean_cells"].cpu().numpy(), mc) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_loglik_krige_matches_oracle(ctx, prec):
+    n1, n2 = 40, 44
+    cov = I.Cov(1.0, 0.12, 1.5, 0.08)
+    mask = I.mask_circles(n1, n2, 0.3, 6)
+    p = set_mask(ctx, mask)
+    M1, M2 = O.sample_embed_size(n1, n2, cov)
+    xi, eps = I.data_noise(M1, M2, p, 14)
+    y, X, _ = O.make_data(n1, n2, mask, cov, (1.0, 0.5, -0.5), xi, eps)
+    cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+    S1, S2 = I.cell_centres(n1, n2)
+    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+    opts = kry.Opts(prec=kry.KRY_F64 if prec == "f64" else kry.KRY_F32, nprobe=6, nsteps=30, seed=2, rtol=1e-9,
+                    maxit=4000)
+    res = ctx.loglik_krige(cov, opts, torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV),
+                           cells=torch.tensor(cells, device=DEV), Xc=torch.tensor(Xc.T.copy(), device=DEV))
+    assert res["status"] == kry.KRY_OK
+    P = O.FFTProblem(n1, n2, mask, cov)
+    ref = P.profile_loglik(y, X, 6, 30, 2, tol=1e-12)
+    assert res["loglik"] == pytest.approx(ref["loglik"], rel=1e-3)
+    assert res["logdet"] == pytest.approx(ref["logdet"], rel=1e-3)
+    assert np.allclose(res["beta"], ref["beta"], rtol=1e-6, atol=1e-8)
+    mu = P.krige_cells(y, X, ref["beta"], cells, Xc, tol=1e-12)
+    assert relerr(res["mean_cells"].cpu().numpy(), mu) <= 1e-4
 
 
 def test_argument_errors(ctx):
