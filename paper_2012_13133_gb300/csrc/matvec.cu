@@ -238,6 +238,10 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
 }
 
 // ------------------------------------------------------------------ radix-16 passes (64 <= L <= 8192)
+
+#ifndef KRY_K16_MINB
+#define KRY_K16_MINB 2   // register budget for 2 resident 512-thread blocks per SM (<= 64 registers; measured fastest)
+#endif
 //
 // Same three passes as above, built from the radix-16 register stages of
 // fft16.cuh: G rows (pass A/C) or CC columns (pass B) per block, interleaved
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
 // forward and inverse column transforms without leaving registers.
 
 template <typename T, int G>
-__global__ void __launch_bounds__(512) k16_pass_a(const T* __restrict__ vin, int64_t ld, const double* __restrict__ scale,
+__global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_a(const T* __restrict__ vin, int64_t ld, const double* __restrict__ scale,
                                                   int nvec, int pair0, const int* __restrict__ rowptr,
                                                   const int* __restrict__ colidx, int n1, int n2, int M2, int C,
                                                   int logC, int PS, typename cx_of<T>::type* __restrict__ slab,
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(512) k16_pass_a(const T* __restrict__ vin, int
 }
 
 template <typename T, int CC>
-__global__ void __launch_bounds__(512) k16_pass_b(typename cx_of<T>::type* __restrict__ slab,
+__global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_b(typename cx_of<T>::type* __restrict__ slab,
                                                   const T* __restrict__ lamT, int n1, int M1, int M2, int PS,
                                                   const void* tw32, const void* tw64) {
     using Cx = typename cx_of<T>::type;
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(512) k16_pass_b(typename cx_of<T>::type* __res
 }
 
 template <typename T, int G, int MODE>
-__global__ void __launch_bounds__(512) k16_pass_c(const typename cx_of<T>::type* __restrict__ slab,
+__global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename cx_of<T>::type* __restrict__ slab,
                                                   const T* __restrict__ vin, int64_t ld_in,
                                                   const double* __restrict__ scale, T* __restrict__ vout,
                                                   int64_t ld_out, int nvec, int pair0, const int* __restrict__ rowptr,

@@ -33,6 +33,7 @@ def main():
     ap.add_argument("--nvec", type=int, default=8)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--autotune", action="store_true", help="autotune the schedule for this batch first")
     args = ap.parse_args()
 
     w = I.WORKLOADS[args.workload]
@@ -43,6 +44,7 @@ def main():
     prec = kry.KRY_F32 if args.prec == "f32" else kry.KRY_F64
     dt = torch.float32 if args.prec == "f32" else torch.float64
     emb = ctx.embed(w.cov, prec)
+    tuned = ctx.autotune(emb, args.nvec) if args.autotune else None
     V = torch.tensor(I.normals((args.nvec, p), 1), dtype=dt, device=dev)
     out = torch.empty_like(V)
     ctx.matvec(emb, V, out)                      # warm-up (allocates the slab)
@@ -63,7 +65,7 @@ def main():
         M2 *= 2
     bpv = 16.0 * w.n1 * M2 + 16.0 * p
     ms = float(np.mean(times))
-    print(json.dumps({"workload": w.name, "nvec": args.nvec, "prec": args.prec, "ms_per_call": ms,
+    print(json.dumps({"workload": w.name, "nvec": args.nvec, "prec": args.prec, "schedule": tuned, "ms_per_call": ms,
                       "model_bytes_per_call": bpv * args.nvec + 4.0 * M1 * M2,
                       "model_GBps": (bpv * args.nvec + 4.0 * M1 * M2) / ms / 1e6}))
     ctx.close()
