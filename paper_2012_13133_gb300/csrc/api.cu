@@ -12,13 +12,14 @@
 #include "kry_internal.cuh"
 
 namespace kry {
-void store_embedding(kry_ctx* ctx, kry_embed* e);
+void store_embedding(kry_ctx* ctx, kry_embed* e, int slot);
+void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_vec);
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0);
 void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe);
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit);
+                double rtol, int maxit, int vpt = 0);
 GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet);
 void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_dev, double* w);
 void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, int64_t ncell, const double* Xc,
@@ -189,7 +190,7 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
         const size_t MM = (size_t)e->M1 * e->M2;
         KRY_CUDA(cudaMalloc(&e->lam64T, MM * sizeof(double)));
         if (prec == KRY_F32) KRY_CUDA(cudaMalloc(&e->lam32T, MM * sizeof(float)));
-        kry::store_embedding(ctx, e);
+        kry::store_embedding(ctx, e, 0);
     } catch (...) {
         if (e->lam64T) cudaFree(e->lam64T);
         if (e->lam32T) cudaFree(e->lam32T);
@@ -203,7 +204,50 @@ static void free_embed(kry_embed* e) {
     if (!e) return;
     if (e->lam64T) cudaFree(e->lam64T);
     if (e->lam32T) cudaFree(e->lam32T);
+    if (e->tau2_dev) cudaFree(e->tau2_dev);
     delete e;
+}
+
+// Several covariance settings on the grid of the mask in one embedding:
+// eigenvalue blocks back to back, per-setting nuggets on the device.
+static kry_embed* make_embed_batch(kry_ctx* ctx, const kry_cov* thetas, int ntheta, kry_prec prec) {
+    require_mask(ctx);
+    for (int t = 0; t < ntheta; ++t) check_cov(&thetas[t]);
+    kry_embed* e = new kry_embed();
+    e->ctx = ctx;
+    e->device = ctx->device;
+    e->n1 = ctx->n1;
+    e->n2 = ctx->n2;
+    e->M1 = pow2_at_least(2 * (int64_t)ctx->n1);
+    e->M2 = pow2_at_least(2 * (int64_t)ctx->n2);
+    e->cov = thetas[0];
+    e->prec = prec;
+    e->ntheta = ntheta;
+    const size_t MM = (size_t)e->M1 * e->M2;
+    e->lam_stride = (int64_t)MM;
+    try {
+        KRY_CUDA(cudaMalloc(&e->lam64T, ntheta * MM * sizeof(double)));
+        if (prec == KRY_F32) KRY_CUDA(cudaMalloc(&e->lam32T, ntheta * MM * sizeof(float)));
+        KRY_CUDA(cudaMalloc(&e->tau2_dev, ntheta * sizeof(double)));
+        std::vector<double> t2(ntheta);
+        for (int t = 0; t < ntheta; ++t) {
+            double lo, hi;
+            kry::compute_eigs(ctx, thetas[t], ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, e->M1, e->M2, &lo, &hi);
+            kry::store_embedding(ctx, e, t);
+            t2[t] = thetas[t].tau2;
+            if (t == 0 || lo / hi < e->lam_min / e->lam_max) {
+                e->lam_min = lo;
+                e->lam_max = hi;
+            }
+        }
+        KRY_CUDA(cudaMemcpyAsync(e->tau2_dev, t2.data(), ntheta * sizeof(double), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        free_embed(e);
+        throw;
+    }
+    return e;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -247,6 +291,7 @@ void kry_destroy(kry_ctx* ctx) {
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
     prof_clear(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
     delete ctx;
 }
@@ -401,24 +446,56 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
         KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
         KRY_REQUIRE(ntheta >= 1, KRY_EINVAL, "ntheta must be >= 1");
         for (int t = 0; t < ntheta; ++t) check_cov(&thetas[t]);
+        const int64_t p = ctx->p;
+        const int nc = ncov + 1;
+        const int ncp = nc + (nc & 1);   // right-hand sides per setting, padded to pair up
+        const bool batched = ntheta > 1 && opts->nprobe % 2 == 0;
+        // settings per group: keep the batched vectors within ~2048 (log-det) per launch sequence
+        const int group = batched ? std::max(1, std::min<int>(ntheta, 2048 / opts->nprobe)) : 1;
         kry_status worst = KRY_OK;
-        for (int t = 0; t < ntheta; ++t) {
-            kry_embed* e = make_embed(ctx, &thetas[t], opts->prec);
+        for (int t0 = 0; t0 < ntheta; t0 += group) {
+            const int ng = std::min(group, ntheta - t0);
+            kry_embed* e = (ng > 1) ? make_embed_batch(ctx, thetas + t0, ng, opts->prec)
+                                    : make_embed(ctx, &thetas[t0], opts->prec);
             try {
-                std::vector<double> vals(opts->nprobe);
-                kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
-                double ld = 0, se = 0;
-                mean_se(vals, &ld, &se);
-                double *V, *Z;
-                kry::SolveInfo si = solve_yx(ctx, e, y_dev, X_dev, ncov, opts, &V, &Z);
-                kry::GlsResult g = kry::gls(ctx, V, Z, ncov, ld);
-                loglik[t] = g.loglik;
-                if (beta)
-                    for (int c = 0; c < ncov; ++c) beta[(size_t)t * ncov + c] = g.beta[c];
-                if (logdet) logdet[t] = ld;
-                if (logdet_se) logdet_se[t] = se;
-                if (!isfinite(g.loglik) || !g.ok) worst = KRY_ENAN;
-                else if (!si.converged && worst == KRY_OK) worst = KRY_ENOCONV;
+                // log-determinants: ng settings x nprobe probes in one batched Lanczos
+                std::vector<double> vals((size_t)ng * opts->nprobe);
+                if (ng > 1)
+                    kry::logdet_batched(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+                else
+                    kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+                // right-hand sides [y, X] (zero-padded to ncp columns) repeated for each setting
+                ctx->zbuf.ensure((size_t)(nc + 2 * (size_t)ng * ncp) * p * sizeof(double));
+                double* V = ctx->zbuf.as<double>();
+                double* Vrep = V + (size_t)nc * p;
+                double* Z = Vrep + (size_t)ng * ncp * p;
+                KRY_CUDA(cudaMemcpyAsync(V, y_dev, p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+                KRY_CUDA(cudaMemcpyAsync(V + p, X_dev, (size_t)ncov * p * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+                for (int t = 0; t < ng; ++t) {
+                    double* blk = Vrep + (size_t)t * ncp * p;
+                    KRY_CUDA(cudaMemcpyAsync(blk, V, (size_t)nc * p * sizeof(double), cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+                    if (ncp > nc)
+                        KRY_CUDA(cudaMemsetAsync(blk + (size_t)nc * p, 0, p * sizeof(double), ctx->stream));
+                }
+                kry::SolveInfo si = kry::solve(ctx, e, Vrep, p, Z, p, ng * ncp, opts->rtol, opts->maxit,
+                                               ng > 1 ? ncp : 0);
+                for (int t = 0; t < ng; ++t) {
+                    std::vector<double> pv(vals.begin() + (size_t)t * opts->nprobe,
+                                           vals.begin() + (size_t)(t + 1) * opts->nprobe);
+                    double ld = 0, se = 0;
+                    mean_se(pv, &ld, &se);
+                    kry::GlsResult g = kry::gls(ctx, V, Z + (size_t)t * ncp * p, ncov, ld);
+                    const int ti = t0 + t;
+                    loglik[ti] = g.loglik;
+                    if (beta)
+                        for (int c = 0; c < ncov; ++c) beta[(size_t)ti * ncov + c] = g.beta[c];
+                    if (logdet) logdet[ti] = ld;
+                    if (logdet_se) logdet_se[ti] = se;
+                    if (!isfinite(g.loglik) || !g.ok) worst = KRY_ENAN;
+                }
+                if (!si.converged && worst == KRY_OK) worst = KRY_ENOCONV;
             } catch (...) {
                 free_embed(e);
                 throw;

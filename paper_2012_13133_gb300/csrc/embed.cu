@@ -288,10 +288,13 @@ __global__ void k_transpose_scale(const double* __restrict__ lam, int M1, int M2
     }
 }
 
-void store_embedding(kry_ctx* ctx, kry_embed* e) {
+// Store the eigenvalues in ctx->eig_c as setting `slot` of embedding e.
+void store_embedding(kry_ctx* ctx, kry_embed* e, int slot) {
     dim3 grid((e->M2 + 31) / 32, (e->M1 + 31) / 32), blk(32, 8);
+    const int64_t off = (int64_t)slot * e->M1 * e->M2;
     k_transpose_scale<<<grid, blk, 0, ctx->stream>>>(ctx->eig_c.as<double>(), e->M1, e->M2,
-                                                     1.0 / ((double)e->M1 * (double)e->M2), e->lam64T, e->lam32T);
+                                                     1.0 / ((double)e->M1 * (double)e->M2), e->lam64T + off,
+                                                     e->lam32T ? e->lam32T + off : nullptr);
     KRY_CHECK_LAUNCH();
 }
 

@@ -106,6 +106,11 @@ struct kry_ctx {
     // autotuned / user-set schedules keyed by (M1, M2, precision, batch bucket)
     std::map<uint64_t, MvSched> tuned;
 
+    // CUDA-graph capture of the Lanczos loop (a library-owned capture stream
+    // joined to the context stream with events)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+
     // optional timing of every matvec (CUDA events on the context stream)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;     // start/stop pairs
@@ -124,6 +129,13 @@ struct kry_embed {
     double* lam64T = nullptr;
     float* lam32T = nullptr;
     double lam_min = 0, lam_max = 0;
+    // several covariance settings in one embedding (batched likelihood
+    // search): ntheta eigenvalue blocks lam_stride elements apart, per-theta
+    // nuggets on the device; a matvec call names how many consecutive real
+    // vectors belong to each theta (vectors per theta, even)
+    int ntheta = 1;
+    int64_t lam_stride = 0;
+    double* tau2_dev = nullptr;
 };
 
 // ------------------------------------------------------------------ internal entry points
@@ -146,11 +158,15 @@ void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, i
 // Sigma (no nugget) applied to observed values, evaluated at every grid cell:
 // out_grid[n1*n2] per vector (FP64 only; used for kriging).
 void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double* out_grid, int nvec,
-                     int64_t ld);
+                     int64_t ld, int vpt = 0);
 
 void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out);
 
 int smem_limit(kry_ctx* ctx);
+
+// Record a profiling event on the context stream; inside a stream capture it
+// becomes an external event-record node, so it still times the graph replay.
+void prof_record(kry_ctx* ctx, cudaEvent_t ev);
 
 // Schedule key and lookup (falls back to the per-precision default).
 uint64_t sched_key(int M1, int M2, bool dbl, int nvec);

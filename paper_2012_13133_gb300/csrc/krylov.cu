@@ -23,7 +23,7 @@ namespace kry {
 
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0);
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
 
 static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
@@ -38,13 +38,58 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
+// Vector v holds Rademacher probe (v mod nprobe): every covariance setting of a
+// batched search sees the same probes.
 template <typename T>
-__global__ void k_probes(T* __restrict__ W, int64_t p, int nprobe, int probe0, uint64_t seed) {
-    const int k = blockIdx.y;
+__global__ void k_probes(T* __restrict__ W, int64_t p, int nprobe, uint64_t seed) {
+    const int v = blockIdx.y;
+    const uint64_t k = (uint64_t)(v % nprobe);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = seed ^ (((uint64_t)(probe0 + k) << 32) | (uint64_t)i);
-        W[(int64_t)k * p + i] = (splitmix64(key) >> 63) ? (T)-1 : (T)1;
+        const uint64_t key = seed ^ ((k << 32) | (uint64_t)i);
+        W[(int64_t)v * p + i] = (splitmix64(key) >> 63) ? (T)-1 : (T)1;
     }
+}
+
+// Run fn() under stream capture on the library's capture stream and replay the
+// captured graph once, ordered after earlier work on ctx->stream and before
+// later work on it.  Without graphs (ctx->use_graphs false) fn() runs directly.
+template <class F>
+static void run_captured(kry_ctx* ctx, F&& fn) {
+    if (!ctx->use_graphs) {
+        fn();
+        return;
+    }
+    if (!ctx->cap_stream) KRY_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->stream, cap = ctx->cap_stream;
+    cudaEvent_t fork, join;
+    KRY_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    KRY_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    KRY_CUDA(cudaEventRecord(fork, user));
+    KRY_CUDA(cudaStreamWaitEvent(cap, fork, 0));
+    cudaGraph_t graph = nullptr;
+    ctx->stream = cap;
+    KRY_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    try {
+        fn();
+    } catch (...) {
+        cudaStreamEndCapture(cap, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        ctx->stream = user;
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
+        throw;
+    }
+    ctx->stream = user;
+    KRY_CUDA(cudaStreamEndCapture(cap, &graph));
+    cudaGraphExec_t exec = nullptr;
+    KRY_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    KRY_CUDA(cudaGraphLaunch(exec, cap));
+    KRY_CUDA(cudaEventRecord(join, cap));
+    KRY_CUDA(cudaStreamWaitEvent(user, join, 0));
+    KRY_CUDA(cudaGraphExecDestroy(exec));
+    KRY_CUDA(cudaGraphDestroy(graph));
+    KRY_CUDA(cudaEventDestroy(fork));
+    KRY_CUDA(cudaEventDestroy(join));
 }
 
 // ------------------------------------------------------------------ block reduction helper
@@ -198,66 +243,87 @@ __global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, doubl
     out[k] = znorm2 * acc;
 }
 
+// Lanczos over nvec vectors (vector v holds probe v mod nprobe; vpt consecutive
+// vectors share one covariance setting of a batched embedding, 0 = one
+// setting).  Step 0 runs directly (it sizes every buffer); steps 1.. are
+// captured into one CUDA graph and replayed as one launch.
 template <typename T>
-static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed,
-                           double* per_probe) {
+static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprobe, int nsteps, uint64_t seed,
+                           double* per_vec, int vpt) {
     const bool dbl = sizeof(T) == 8;
     const int64_t p = ctx->p;
-    cudaStream_t st = ctx->stream;
-    const int nblkC = matvec_num_partials(ctx, e, dbl, nprobe);
-    const size_t vbytes = (size_t)nprobe * p * sizeof(T);
+    const int nblkC = matvec_num_partials(ctx, e, dbl, nvec);
+    const size_t vbytes = (size_t)nvec * p * sizeof(T);
     for (int b = 0; b < 4; ++b) ctx->work[b].ensure(vbytes);
     T* U = ctx->work[0].as<T>();
     T* W[3] = {ctx->work[1].as<T>(), ctx->work[2].as<T>(), ctx->work[3].as<T>()};
     const int nred = std::max(nblkC, RED_BLOCKS);
-    ctx->work[4].ensure((size_t)nprobe * nred * sizeof(double));
+    ctx->work[4].ensure((size_t)nvec * nred * sizeof(double));
     double* part = ctx->work[4].as<double>();
-    ctx->scal.ensure((size_t)nprobe * (2 * nsteps + 4) * sizeof(double) + nprobe * sizeof(double));
+    ctx->scal.ensure((size_t)nvec * (2 * nsteps + 4) * sizeof(double) + nvec * sizeof(double));
     double* sc = ctx->scal.as<double>();
     LanczosState S;
     S.s_cur = sc;
-    S.s_prev = sc + nprobe;
-    S.alpha = sc + 2 * nprobe;
-    S.beta = S.alpha + (size_t)nprobe * nsteps;
-    double* res = S.beta + (size_t)nprobe * nsteps;
-    ctx->work[5].ensure((size_t)nprobe * sizeof(int));
+    S.s_prev = sc + nvec;
+    S.alpha = sc + 2 * nvec;
+    S.beta = S.alpha + (size_t)nvec * nsteps;
+    double* res = S.beta + (size_t)nvec * nsteps;
+    ctx->work[5].ensure((size_t)nvec * sizeof(int));
     S.m_eff = ctx->work[5].as<int>();
 
     const int tb = 256;
-    k_lanczos_init<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, nprobe, nsteps, 1.0 / sqrt((double)p));
+    k_lanczos_init<<<(nvec + tb - 1) / tb, tb, 0, ctx->stream>>>(S, nvec, nsteps, 1.0 / sqrt((double)p));
     KRY_CHECK_LAUNCH();
-    dim3 gp((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nprobe);
-    k_probes<T><<<gp, 256, 0, st>>>(W[0], p, nprobe, 0, seed);
+    dim3 gp((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nvec);
+    k_probes<T><<<gp, 256, 0, ctx->stream>>>(W[0], p, nprobe, seed);
     KRY_CHECK_LAUNCH();
     int ip = 2, ic = 0, in = 1;   // W indices: previous, current, next
-    for (int j = 0; j < nsteps; ++j) {
-        matvec_ex<T>(ctx, e, W[ic], p, S.s_cur, U, p, nprobe, part, nblkC);
-        k_lanczos_alpha<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nprobe, nsteps, j);
+    auto step = [&](int j) {
+        cudaStream_t st = ctx->stream;
+        matvec_ex<T>(ctx, e, W[ic], p, S.s_cur, U, p, nvec, part, nblkC, vpt);
+        k_lanczos_alpha<<<(nvec + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
-        if (j == nsteps - 1) break;
-        dim3 gu(RED_BLOCKS, nprobe);
+        if (j == nsteps - 1) return;
+        dim3 gu(RED_BLOCKS, nvec);
         k_lanczos_update<T><<<gu, 256, 0, st>>>(U, W[ic], W[ip], W[in], p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
-        k_lanczos_beta<<<(nprobe + tb - 1) / tb, tb, 0, st>>>(S, part, RED_BLOCKS, nprobe, nsteps, j);
+        k_lanczos_beta<<<(nvec + tb - 1) / tb, tb, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
         const int t = ip;
         ip = ic;
         ic = in;
         in = t;
-    }
-    k_quadrature<<<(nprobe + 63) / 64, 64, 0, st>>>(S, nprobe, nsteps, (double)p, res);
+    };
+    step(0);
+    if (nsteps > 1)
+        run_captured(ctx, [&]() {
+            for (int j = 1; j < nsteps; ++j) step(j);
+        });
+    k_quadrature<<<(nvec + 63) / 64, 64, 0, ctx->stream>>>(S, nvec, nsteps, (double)p, res);
     KRY_CHECK_LAUNCH();
-    KRY_CUDA(cudaMemcpyAsync(per_probe, res, nprobe * sizeof(double), cudaMemcpyDeviceToHost, st));
-    KRY_CUDA(cudaStreamSynchronize(st));
+    KRY_CUDA(cudaMemcpyAsync(per_vec, res, nvec * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KRY_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
 void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe) {
     KRY_REQUIRE(nsteps >= 1 && nsteps <= KRY_MAX_STEPS, KRY_EINVAL, "nsteps must be in [1, 256]");
     KRY_REQUIRE(nprobe >= 1, KRY_EINVAL, "nprobe must be >= 1");
     if (e->prec == KRY_F64)
-        lanczos_logdet<double>(ctx, e, nprobe, nsteps, seed, per_probe);
+        lanczos_logdet<double>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0);
     else
-        lanczos_logdet<float>(ctx, e, nprobe, nsteps, seed, per_probe);
+        lanczos_logdet<float>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0);
+}
+
+// Batched form: ntheta settings of a batched embedding x nprobe probes each
+// (nprobe even), per_vec[ntheta * nprobe].
+void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_vec) {
+    KRY_REQUIRE(nsteps >= 1 && nsteps <= KRY_MAX_STEPS, KRY_EINVAL, "nsteps must be in [1, 256]");
+    KRY_REQUIRE(nprobe >= 2 && nprobe % 2 == 0, KRY_EINVAL, "batched log-det needs an even probe count");
+    const int nvec = e->ntheta * nprobe;
+    if (e->prec == KRY_F64)
+        lanczos_logdet<double>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, e->ntheta > 1 ? nprobe : 0);
+    else
+        lanczos_logdet<float>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, e->ntheta > 1 ? nprobe : 0);
 }
 
 // ------------------------------------------------------------------ CG
@@ -371,7 +437,7 @@ __global__ void k_cg_pupdate(T* __restrict__ P, const T* __restrict__ R, int64_t
 // ctx->work[6].  Returns the largest iteration count.
 template <typename T>
 static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, int nrhs, const double* tol_dev,
-                    int maxit, T** X_out) {
+                    int maxit, T** X_out, int vpt) {
     const bool dbl = sizeof(T) == 8;
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
@@ -408,7 +474,7 @@ static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t l
     int it = 0;
     const int poll = 8;
     for (; it < maxit; ++it) {
-        matvec_ex<T>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC);
+        matvec_ex<T>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt);
         k_cg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
         KRY_CHECK_LAUNCH();
         k_cg_update<T><<<gv, 256, 0, st>>>(X, R, P, Q, p, S, part);
@@ -466,17 +532,13 @@ __global__ void k_set(double* x, int64_t n, double v) {
         x[i] = v;
 }
 
-template <typename T>
-void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds);
-
 // FP64 true residual R = B - K X; returns per-column (||R||, ||B||) on the host.
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
-                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm) {
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     // KX = K X (FP64 matvec); X has leading dimension ldx
-    matvec_ex<double>(ctx, e, X, ldx, nullptr, KX, p, nrhs, nullptr, 0);
+    matvec_ex<double>(ctx, e, X, ldx, nullptr, KX, p, nrhs, nullptr, 0, vpt);
     ctx->red.ensure((size_t)nrhs * RED_BLOCKS * 2 * sizeof(double) + (size_t)nrhs * 2 * sizeof(double));
     double* part = ctx->red.as<double>();
     double* fin = part + (size_t)nrhs * RED_BLOCKS * 2;
@@ -628,11 +690,11 @@ __global__ void k_count_done(RcgState S, int nrhs) {
 }
 
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
-                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm);
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt);
 
 // Returns the largest per-column iteration count.
 static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx,
-                       int nrhs, double rtol, int maxit, std::vector<double>& nrm, bool* fresh) {
+                       int nrhs, double rtol, int maxit, std::vector<double>& nrm, bool* fresh, int vpt) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     const size_t vb = (size_t)nrhs * p * sizeof(float);
@@ -675,7 +737,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     nrm.assign(2 * nrhs, 0.0);
     *fresh = false;
     for (int it = 0; it < maxit + poll; ++it) {
-        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC);
+        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt);
         k_rcg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
         KRY_CHECK_LAUNCH();
         k_rcg_update<<<gv, 256, 0, st>>>(X, ldx, R, P, Q, p, S, part);
@@ -689,7 +751,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             KRY_CUDA(cudaStreamSynchronize(st));
             if (*hflag > 0) {
                 // residual replacement for every column still running
-                true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm);
+                true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
                 double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
                 k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit);
                 KRY_CHECK_LAUNCH();
@@ -715,7 +777,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
 }
 
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit) {
+                double rtol, int maxit, int vpt) {
     SolveInfo info;
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
@@ -732,15 +794,15 @@ SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, 
         std::vector<double> tol_h(nrhs, rtol);
         KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
         double* Xd;
-        info.iters = cg_inner<double>(ctx, e, B, ldb, nrhs, ctx->tolbuf.as<double>(), maxit, &Xd);
+        info.iters = cg_inner<double>(ctx, e, B, ldb, nrhs, ctx->tolbuf.as<double>(), maxit, &Xd, vpt);
         KRY_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), Xd, p * sizeof(double), p * sizeof(double), nrhs,
                                    cudaMemcpyDeviceToDevice, st));
     } else {
         // FP32 CG with FP64 solution and residual replacement
-        info.iters = cg_reliable(ctx, e, B, ldb, X, ldx, nrhs, rtol, maxit, nrm, &fresh);
+        info.iters = cg_reliable(ctx, e, B, ldb, X, ldx, nrhs, rtol, maxit, nrm, &fresh, vpt);
     }
     // the reported residual is always the true FP64 residual of the returned X
-    if (!fresh) true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, ctx->kxbuf.as<double>(), nrm);
+    if (!fresh) true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, ctx->kxbuf.as<double>(), nrm, vpt);
     info.relres = 0.0;
     for (int k = 0; k < nrhs; ++k) {
         const double bn = nrm[2 * k + 1];
@@ -980,7 +1042,7 @@ bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int
         k_cross_cols<<<g, 256, 0, st>>>(cells, t0, ctx->cellidx.as<int>(), p, ctx->n2, (int64_t)ctx->n1 * ctx->n2, cp,
                                          cbuf.as<double>());
         KRY_CHECK_LAUNCH();
-        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit);
+        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit, 0);
         ok = ok && si.converged;
         k_var_final<<<k, 256, 0, st>>>(cbuf.as<double>(), sbuf.as<double>(), p, e->cov.sigma2, var, t0);
         KRY_CHECK_LAUNCH();

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_a(const T* __re
 
 template <typename T, int EPT, int CC>
 __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_b(typename cx_of<T>::type* __restrict__ slab, const T* __restrict__ lamT,
-                                                 int n1, int M1, int M2, const void* tw32, const void* tw64) {
+                                                 int n1, int M1, int M2, const void* tw32, const void* tw64,
+                                                 int pair0, int64_t lam_stride, int vpt) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_b(typename cx_o
     Cx* cb = buf + g * stride;
     const Cx* tw = twiddles<T>(tw32, tw64);
     fft_smem<Cx, false, EPT>(cb, L, tl, tw);
-    const T* lam = lamT + (int64_t)(tile * CC + g) * L;
+    const int theta = vpt ? (2 * (pair0 + (int)blockIdx.y)) / vpt : 0;
+    const T* lam = lamT + theta * lam_stride + (int64_t)(tile * CC + g) * L;
     for (int k = tl; k < L; k += LT) {
         const T l = lam[k];
         Cx z = cb[k];
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
                                                  int64_t ld_out, int nvec, int pair0, const int* __restrict__ rowptr,
                                                  const int* __restrict__ colidx, int n1, int n2, int M2, int C,
                                                  double tau2, double* __restrict__ dots, int ndot_stride,
-                                                 const void* tw32, const void* tw64) {
+                                                 const void* tw32, const void* tw64, const double* __restrict__ tau2v,
+                                                 int vpt) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
         if (MODE == 0) {
             const T sa = scale ? (T)scale[va] : (T)1;
             const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
-            const T t2 = (T)tau2;
+            const T t2 = (T)(tau2v ? tau2v[vpt ? va / vpt : 0] : tau2);
             const T* pa = vin + (int64_t)va * ld_in;
             const T* pb = vin + (int64_t)vb * ld_in;
             T* oa = vout + (int64_t)va * ld_out;
@@ -295,7 +298,8 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_a(const T* __restr
 template <typename T, int CC>
 __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_b(typename cx_of<T>::type* __restrict__ slab,
                                                   const T* __restrict__ lamT, int n1, int M1, int M2, int PS,
-                                                  const void* tw32, const void* tw64) {
+                                                  const void* tw32, const void* tw64, int pair0, int64_t lam_stride,
+                                                  int vpt) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -337,7 +341,8 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_b(typename cx_of<T
         kry16::last_stage_regs<Cx, false>(v, t, L, Ns, tw, ld_s, true);
     }
     // eigenvalue multiply (scaled by 1/(M1 M2))
-    const T* lam = lamT + (int64_t)(tile * CC + c) * L;
+    const int theta = vpt ? (2 * (pair0 + (int)blockIdx.y)) / vpt : 0;
+    const T* lam = lamT + theta * lam_stride + (int64_t)(tile * CC + c) * L;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
         const T l = lam[t + m * LT];
@@ -366,7 +371,8 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
                                                   int64_t ld_out, int nvec, int pair0, const int* __restrict__ rowptr,
                                                   const int* __restrict__ colidx, int n1, int n2, int M2, int C,
                                                   int logC, int PS, double tau2, double* __restrict__ dots,
-                                                  int ndot_stride, const void* tw32, const void* tw64) {
+                                                  int ndot_stride, const void* tw32, const void* tw64,
+                                                  const double* __restrict__ tau2v, int vpt) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
         if (MODE == 0) {
             const T sa = scale ? (T)scale[va] : (T)1;
             const T sb = (scale && has_b) ? (T)scale[vb] : (T)1;
-            const T t2 = (T)tau2;
+            const T t2 = (T)(tau2v ? tau2v[vpt ? va / vpt : 0] : tau2);
             const T* pa = vin + (int64_t)va * ld_in;
             const T* pb = vin + (int64_t)vb * ld_in;
             T* oa = vout + (int64_t)va * ld_out;
@@ -480,21 +486,21 @@ struct MvLaunch {
     }
     template <int EPT, int CC>
     static void b(dim3 grid, int threads, size_t smem, cudaStream_t s, Cx* slab, const T* lamT, int n1, int M1, int M2,
-                  const void* tw32, const void* tw64) {
+                  const void* tw32, const void* tw64, int pair0 = 0, int64_t lam_stride = 0, int vpt = 0) {
         auto k = k_pass_b<T, EPT, CC>;
         KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, threads, smem, s>>>(slab, lamT, n1, M1, M2, tw32, tw64);
+        k<<<grid, threads, smem, s>>>(slab, lamT, n1, M1, M2, tw32, tw64, pair0, lam_stride, vpt);
         KRY_CHECK_LAUNCH();
     }
     template <int EPT, int G, int MODE>
     static void c(dim3 grid, int threads, size_t smem, cudaStream_t s, const Cx* slab, const T* vin, int64_t ld_in,
                   const double* scale, T* vout, int64_t ld_out, int nvec, int pair0, const int* rowptr,
                   const int* colidx, int n1, int n2, int M2, int C, double tau2, double* dots, int nds,
-                  const void* tw32, const void* tw64) {
+                  const void* tw32, const void* tw64, const double* tau2v = nullptr, int vpt = 0) {
         auto k = k_pass_c<T, EPT, G, MODE>;
         KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, threads, smem, s>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2,
-                                      C, tau2, dots, nds, tw32, tw64);
+                                      C, tau2, dots, nds, tw32, tw64, tau2v, vpt);
         KRY_CHECK_LAUNCH();
     }
 };
@@ -539,6 +545,15 @@ static MvSched pick_sched(kry_ctx* ctx, const MvSched& want, int M1, int M2, boo
 #ifndef KRY_SMEM_CARVEOUT
 #define KRY_SMEM_CARVEOUT -1   // L1 / shared-memory split: driver default (measured fastest)
 #endif
+
+void prof_record(kry_ctx* ctx, cudaEvent_t ev) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KRY_CUDA(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+        KRY_CUDA(cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal));
+    else
+        KRY_CUDA(cudaEventRecord(ev, ctx->stream));
+}
 
 static bool use16(int M1, int M2) { return M1 >= 64 && M2 >= 64 && M1 <= KRY_MAX_M && M2 <= KRY_MAX_M; }
 
@@ -604,7 +619,7 @@ static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, in
 template <typename T>
 static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                          int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode,
-                         typename cx_of<T>::type* slab, int ppb) {
+                         typename cx_of<T>::type* slab, int ppb, int vpt) {
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
     int G, C;
@@ -636,7 +651,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
             auto k = k16_pass_b<T, N_>;
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
-            k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64);
+            k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64, pair0, e->lam_stride, vpt);
             KRY_CHECK_LAUNCH();
         });
         if (mode == 0) {
@@ -645,7 +660,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt);
                 KRY_CHECK_LAUNCH();
             });
         } else {
@@ -653,7 +668,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
                 auto k = k16_pass_c<T, N_, 1>;
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt);
                 KRY_CHECK_LAUNCH();
             });
         }
@@ -662,7 +677,9 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
 
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode) {
+                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt = 0) {
+    KRY_REQUIRE(vpt == 0 || (vpt % 2 == 0 && nvec % vpt == 0 && nvec / vpt <= e->ntheta), KRY_EINVAL,
+                "vectors per theta must be even and divide the batch");
     using Cx = typename cx_of<T>::type;
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
@@ -676,11 +693,11 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
         if (ctx->prof_on) {
             KRY_CUDA(cudaEventCreate(&ev0));
             KRY_CUDA(cudaEventCreate(&ev1));
-            KRY_CUDA(cudaEventRecord(ev0, ctx->stream));
+            prof_record(ctx, ev0);
         }
-        run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb);
+        run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb, vpt);
         if (ctx->prof_on) {
-            KRY_CUDA(cudaEventRecord(ev1, ctx->stream));
+            prof_record(ctx, ev1);
             ctx->prof_ev.push_back(ev0);
             ctx->prof_ev.push_back(ev1);
             ctx->prof_nvec.push_back(nvec);
@@ -712,7 +729,7 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
     if (ctx->prof_on) {
         KRY_CUDA(cudaEventCreate(&ev0));
         KRY_CUDA(cudaEventCreate(&ev1));
-        KRY_CUDA(cudaEventRecord(ev0, st));
+        prof_record(ctx, ev0);
     }
     for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
         const int np = std::min(ppb, npairs - pair0);
@@ -721,21 +738,22 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
                         (MvLaunch<T>::template a<E_, G_>(gA, thrA, smA, st, vin, ld_in, scale, nvec, pair0, rowptr,
                                                          colidx, n1, M2, C, slab, tw32, tw64)));
         KRY_DISPATCH_EG(s.ept_col, C,
-                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64)));
+                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64, pair0,
+                                                         e->lam_stride, vpt)));
         if (mode == 0) {
             KRY_DISPATCH_EG(s.ept_row, G,
                             (MvLaunch<T>::template c<E_, G_, 0>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
                                                                 ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
-                                                                tau2, dots, nds, tw32, tw64)));
+                                                                tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt)));
         } else {
             KRY_DISPATCH_EG(s.ept_row, G,
                             (MvLaunch<T>::template c<E_, G_, 1>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
                                                                 ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
-                                                                tau2, dots, nds, tw32, tw64)));
+                                                                tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt)));
         }
     }
     if (ctx->prof_on) {
-        KRY_CUDA(cudaEventRecord(ev1, st));
+        prof_record(ctx, ev1);
         ctx->prof_ev.push_back(ev0);
         ctx->prof_ev.push_back(ev1);
         ctx->prof_nvec.push_back(nvec);
@@ -757,14 +775,14 @@ int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec) {
 
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds) {
-    run_matvec<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, e->cov.tau2, dots, nds, 0);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt) {
+    run_matvec<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, e->cov.tau2, dots, nds, 0, vpt);
 }
 
 template void matvec_ex<float>(kry_ctx*, const kry_embed*, const float*, int64_t, const double*, float*, int64_t, int,
-                               double*, int);
+                               double*, int, int);
 template void matvec_ex<double>(kry_ctx*, const kry_embed*, const double*, int64_t, const double*, double*, int64_t,
-                                int, double*, int);
+                                int, double*, int, int);
 
 template <typename T>
 void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld, double) {
@@ -773,8 +791,9 @@ void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, i
 template void matvec<float>(kry_ctx*, const kry_embed*, const float*, float*, int, int64_t, double);
 template void matvec<double>(kry_ctx*, const kry_embed*, const double*, double*, int, int64_t, double);
 
-void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double* out_grid, int nvec, int64_t ld) {
-    run_matvec<double>(ctx, e, vin, ld, nullptr, out_grid, (int64_t)e->n1 * e->n2, nvec, 0.0, nullptr, 0, 1);
+void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double* out_grid, int nvec, int64_t ld,
+                     int vpt) {
+    run_matvec<double>(ctx, e, vin, ld, nullptr, out_grid, (int64_t)e->n1 * e->n2, nvec, 0.0, nullptr, 0, 1, vpt);
 }
 
 // ------------------------------------------------------------------ allocation-free matvec

@@ -313,6 +313,30 @@ def test_profile_loglik_batch_of_thetas_fp32(ctx):
         assert res["logdet"][t] == pytest.approx(ref["logdet"], rel=1e-3), th
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batched_thetas_equal_individual_calls(ctx, prec):
+    """The batched search (all settings in shared launches) gives each setting the
+    same log-likelihood as a call for that setting alone."""
+    n1, n2 = 96, 80
+    mask = I.mask_uniform(n1, n2, 0.3, 5)
+    p = set_mask(ctx, mask)
+    dcov = I.Cov(1.0, 0.08, 1.0, 0.1)
+    M1, M2 = O.sample_embed_size(n1, n2, dcov)
+    xi, eps = I.data_noise(M1, M2, p, 31)
+    y, X, _ = O.make_data(n1, n2, mask, dcov, (1.0, 0.5, -0.5), xi, eps)
+    yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
+    thetas = [I.Cov(1.0, r, nu, 0.1 if nu != 2.5 else 0.05) for r in (0.04, 0.1) for nu in (0.5, 1.0, 2.5)]
+    opts = kry.Opts(prec=kry.KRY_F32 if prec == "f32" else kry.KRY_F64, nprobe=8, nsteps=30, seed=7, rtol=1e-8,
+                    maxit=4000)
+    batch = ctx.profile_loglik(yt, Xt, thetas, opts)
+    assert batch["status"] == kry.KRY_OK
+    for t, th in enumerate(thetas):
+        one = ctx.profile_loglik(yt, Xt, [th], opts)
+        assert batch["loglik"][t] == pytest.approx(one["loglik"][0], rel=1e-6)
+        assert batch["logdet"][t] == pytest.approx(one["logdet"][0], rel=1e-6)
+        assert np.allclose(batch["beta"][t], one["beta"][0], rtol=1e-6, atol=1e-8)
+
+
 def test_krige_tiny_sites_and_cells(ctx):
     w, mask, y, X = tiny_data()
     set_mask(ctx, mask)
