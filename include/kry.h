@@ -227,6 +227,57 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
  * size tried if none qualifies.  Synchronises the stream. */
 kry_status kry_sample_size(kry_ctx* ctx, const kry_cov* cov, int32_t* M1, int32_t* M2);
 
+/* ---- Continuous-batching server (no counterpart in the paper; it serves many
+ * independent likelihood or kriging requests on one GPU).
+ *
+ * A server runs nslots worker threads, each with its own CUDA stream and
+ * context, so requests in different slots overlap on the device.  Requests
+ * wait in one queue; a free slot admits the first queued request whose
+ * estimated device footprint fits in what mem_budget_bytes has left (smaller
+ * requests may pass a large one that does not fit yet; an idle slot gives its
+ * cached buffers back when a queued request cannot be admitted).  All request
+ * buffers are host memory owned by the caller and must stay valid until
+ * kry_server_wait returns for the ticket.  A request is computed exactly as a
+ * kry_profile_loglik (kind KRY_REQ_LOGLIK, one setting) or kry_krige (kind
+ * KRY_REQ_KRIGE, means at the given target cells) call in a fresh context
+ * with default launch schedules, so its result does not depend on what else
+ * runs. */
+typedef enum { KRY_REQ_LOGLIK = 0, KRY_REQ_KRIGE = 1 } kry_request_kind;
+
+typedef struct {
+    int32_t kind;                  /* kry_request_kind */
+    int32_t n1, n2;                /* grid, cell sizes 1/n1 x 1/n2 */
+    const uint8_t* mask;           /* n1*n2 bytes, row-major, nonzero = observed */
+    const double* y;               /* p observations (row-major order of observed cells) */
+    const double* X;               /* p x ncov covariates, column-major */
+    int32_t ncov;
+    kry_cov cov;
+    kry_opts opts;
+    double* loglik;                /* out (LOGLIK): profile log-likelihood */
+    double* logdet;                /* out (LOGLIK, may be NULL): log det K estimate */
+    double* beta;                  /* out (may be NULL): ncov GLS coefficients */
+    const int64_t* target_cells;   /* KRIGE: the N - p unobserved cells, row-major indices */
+    const double* target_X;        /* KRIGE: (N - p) x ncov covariates at those cells, column-major */
+    double* mean;                  /* out (KRIGE): N - p kriging means */
+} kry_request;
+
+typedef struct kry_server kry_server;
+
+kry_status kry_server_create(kry_server** server, int device, int32_t nslots, int64_t mem_budget_bytes);
+/* Queue a request (returns at once).  KRY_ENOMEM if it can never fit the budget. */
+kry_status kry_server_submit(kry_server* server, const kry_request* req, uint64_t* ticket);
+/* Wait at most timeout_s seconds for a ticket (KRY_ETIMEOUT if it has not
+ * finished).  On completion reports the request's own status, its latency
+ * from submission to completion in ms, the slot that ran it and (err_buf of
+ * err_len bytes, may be NULL) the request's error message; the ticket is then
+ * retired. */
+kry_status kry_server_wait(kry_server* server, uint64_t ticket, double timeout_s, kry_status* req_status,
+                           double* latency_ms, int32_t* slot, char* err_buf, int32_t err_len);
+/* Requests queued and not yet admitted. */
+int64_t kry_server_queued(kry_server* server);
+/* Stops the workers after their current request; queued requests are dropped. */
+void kry_server_destroy(kry_server* server);
+
 /* Schedule autotuner (no counterpart in the paper; the paper names no GPU
  * schedule).  Times every feasible launch schedule of the covariance matvec on
  * embedding e for batches of nvec vectors -- rows per block of the row passes,

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include "kry_internal.cuh"
@@ -16,7 +18,7 @@ void store_embedding(kry_ctx* ctx, kry_embed* e, int slot);
 void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_vec);
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
 void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe);
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
                 double rtol, int maxit, int vpt = 0);
@@ -32,6 +34,22 @@ bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int
 
 std::atomic<unsigned long long> g_kry_launches{0};
 
+void kry_allow_max_smem(const void* func) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    KRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({func, dev})) return;
+    int optin = 0;
+    KRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes a;
+    KRY_CUDA(cudaFuncGetAttributes(&a, func));
+    KRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)a.sharedSizeBytes));
+    done.insert({func, dev});
+}
+
 static void prof_clear(kry_ctx* ctx) {
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     ctx->prof_ev.clear();
@@ -43,22 +61,43 @@ void DevBuf::ensure(size_t bytes) {
     if (bytes <= cap && p) return;
     release();
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {
         p = nullptr;
         cap = 0;
         (void)cudaGetLastError();
-        throw KryError{KRY_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
-                                       cudaGetErrorString(e)};
+        throw KryError{KRY_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                       " bytes failed: " + cudaGetErrorString(e)};
     }
     cap = bytes;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, stream);
     p = nullptr;
     cap = 0;
 }
+
+static void dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+        throw KryError{KRY_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                       " bytes failed: " + cudaGetErrorString(e)};
+    }
+}
+
+namespace kry {
+void ctx_trim(kry_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& b : ctx->work) b.release();
+}
+}  // namespace kry
 
 // ------------------------------------------------------------------ mask compaction
 
@@ -185,27 +224,33 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     e->M2 = pow2_at_least(2 * (int64_t)ctx->n2);
     e->cov = *cov;
     e->prec = prec;
+    e->stream = ctx->stream;
     try {
         kry::compute_eigs(ctx, *cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, e->M1, e->M2, &e->lam_min, &e->lam_max);
         const size_t MM = (size_t)e->M1 * e->M2;
-        KRY_CUDA(cudaMalloc(&e->lam64T, MM * sizeof(double)));
-        if (prec == KRY_F32) KRY_CUDA(cudaMalloc(&e->lam32T, MM * sizeof(float)));
+        dev_alloc((void**)&e->lam64T, MM * sizeof(double), ctx->stream);
+        if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, MM * sizeof(float), ctx->stream);
         kry::store_embedding(ctx, e, 0);
     } catch (...) {
-        if (e->lam64T) cudaFree(e->lam64T);
-        if (e->lam32T) cudaFree(e->lam32T);
+        if (e->lam64T) cudaFreeAsync(e->lam64T, ctx->stream);
+        if (e->lam32T) cudaFreeAsync(e->lam32T, ctx->stream);
         delete e;
         throw;
     }
     return e;
 }
 
-static void free_embed(kry_embed* e) {
+// Stream-ordered release on stream s (the creating context's stream while it
+// lives; the legacy stream from kry_embed_free, whose context may be gone).
+static void free_embed(kry_embed* e, cudaStream_t s) {
     if (!e) return;
-    if (e->lam64T) cudaFree(e->lam64T);
-    if (e->lam32T) cudaFree(e->lam32T);
-    if (e->tau2_dev) cudaFree(e->tau2_dev);
+    if (e->lam64T) cudaFreeAsync(e->lam64T, s);
+    if (e->lam32T) cudaFreeAsync(e->lam32T, s);
+    if (e->tau2_dev) cudaFreeAsync(e->tau2_dev, s);
     delete e;
+}
+static void free_embed(kry_embed* e) {
+    if (e) free_embed(e, e->stream);
 }
 
 // Several covariance settings on the grid of the mask in one embedding:
@@ -222,13 +267,14 @@ static kry_embed* make_embed_batch(kry_ctx* ctx, const kry_cov* thetas, int nthe
     e->M2 = pow2_at_least(2 * (int64_t)ctx->n2);
     e->cov = thetas[0];
     e->prec = prec;
+    e->stream = ctx->stream;
     e->ntheta = ntheta;
     const size_t MM = (size_t)e->M1 * e->M2;
     e->lam_stride = (int64_t)MM;
     try {
-        KRY_CUDA(cudaMalloc(&e->lam64T, ntheta * MM * sizeof(double)));
-        if (prec == KRY_F32) KRY_CUDA(cudaMalloc(&e->lam32T, ntheta * MM * sizeof(float)));
-        KRY_CUDA(cudaMalloc(&e->tau2_dev, ntheta * sizeof(double)));
+        dev_alloc((void**)&e->lam64T, ntheta * MM * sizeof(double), ctx->stream);
+        if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, ntheta * MM * sizeof(float), ctx->stream);
+        dev_alloc((void**)&e->tau2_dev, ntheta * sizeof(double), ctx->stream);
         std::vector<double> t2(ntheta);
         for (int t = 0; t < ntheta; ++t) {
             double lo, hi;
@@ -266,6 +312,17 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         KRY_REQUIRE(device >= 0 && device < ndev, KRY_EINVAL, "no such CUDA device");
         KRY_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
         KRY_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+        // every scratch buffer is stream-ordered on the context stream; keep freed
+        // pool memory cached in this process instead of returning it at each sync
+        DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->slab32,
+                          &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+        for (DevBuf* b : bufs) b->stream = ctx->stream;
+        for (auto& b : ctx->work) b.stream = ctx->stream;
+        cudaMemPool_t pool;
+        KRY_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t keep = UINT64_MAX;
+        KRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
         KRY_CUDA(cudaMallocHost(&ctx->host_pinned, 4096 * sizeof(double)));
         kry::init_twiddles(ctx);
         KRY_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -347,10 +404,11 @@ kry_status kry_embed_eigs(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, kry_e
 
 void kry_embed_free(kry_embed* e) {
     if (!e) return;
-    // cudaFree synchronises the device, so work still queued on the embedding
-    // finishes first; the owning context is not touched (it may be gone).
+    // the owning context (and its stream) may be gone: free in order on the
+    // legacy stream after the device has finished the embedding's work
     cudaSetDevice(e->device);
-    free_embed(e);
+    cudaDeviceSynchronize();
+    free_embed(e, (cudaStream_t)0);
 }
 
 kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev, int32_t nvec, int64_t ld) {

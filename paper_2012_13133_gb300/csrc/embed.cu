@@ -144,7 +144,7 @@ template <int IN>
 static void launch_rows_full(kry_ctx* ctx, const double* rin, const double* xi, double scale, double2* z, int M1,
                              int M2) {
     const int ept = (M2 >= 8192) ? 16 : 8;
-    const int G = pick_group(M2, ept, sizeof(double2), ctx->max_smem_optin);
+    const int G = pick_group(M2, ept, sizeof(double2), ctx->max_smem_optin - 1024);
     const int thr = G * (M2 / ept);
     const size_t sm = (size_t)G * (M2 + 1) * sizeof(double2);
     const int nb = (M1 + G - 1) / G;
@@ -152,7 +152,7 @@ static void launch_rows_full(kry_ctx* ctx, const double* rin, const double* xi, 
 #define KRY_ROWS(E, GG)                                                                     \
     do {                                                                                    \
         auto k = k_rows_full<E, GG, IN>;                                                    \
-        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        KRY_ALLOW_MAX_SMEM(k); \
         k<<<nb, thr, sm, ctx->stream>>>(rin, xi, scale, z, M1, M2, tw);                     \
     } while (0)
     if (ept == 8) {
@@ -167,7 +167,7 @@ static void launch_rows_full(kry_ctx* ctx, const double* rin, const double* xi, 
 template <int OUT>
 static void launch_cols_full(kry_ctx* ctx, const double2* z, double* out, int M1, int M2, int n1, int n2) {
     const int ept = (M1 >= 8192) ? 16 : 8;
-    int C = pick_group(M1, ept, sizeof(double2), ctx->max_smem_optin);
+    int C = pick_group(M1, ept, sizeof(double2), ctx->max_smem_optin - 1024);
     while (C > 1 && M2 % C) C /= 2;
     const int thr = C * (M1 / ept);
     const size_t sm = (size_t)C * (M1 + 1) * sizeof(double2);
@@ -177,7 +177,7 @@ static void launch_cols_full(kry_ctx* ctx, const double2* z, double* out, int M1
 #define KRY_COLS(E, CCV)                                                                    \
     do {                                                                                    \
         auto k = k_cols_full<E, CCV, OUT>;                                                  \
-        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        KRY_ALLOW_MAX_SMEM(k); \
         k<<<nb, thr, sm, ctx->stream>>>(z, out, M1, M2, n1, n2, tw);                        \
     } while (0)
     if (ept == 8) {

@@ -48,11 +48,23 @@ extern std::atomic<unsigned long long> g_kry_launches;
         if (!(cond)) throw KryError{status, text}; \
     } while (0)
 
+// Allow kernel k all the dynamic shared memory the device can give it (the
+// opt-in limit minus the kernel's static shared memory).  The limit is a
+// process-wide property of the kernel, so it is set once per kernel and device
+// to that maximum and never lowered: callers on several threads (server
+// slots) with different launch sizes cannot undercut each other's launches.
+void kry_allow_max_smem(const void* func);
+#define KRY_ALLOW_MAX_SMEM(k) kry_allow_max_smem(reinterpret_cast<const void*>(k))
+
 // ------------------------------------------------------------------ device buffers
 
+// Device buffer allocated stream-ordered (cudaMallocAsync / cudaFreeAsync on
+// its owner's stream), so growing or freeing it never synchronises the device
+// and never disturbs a stream capture running in another thread.
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;
+    cudaStream_t stream = nullptr;
     void ensure(size_t bytes);   // grows (never shrinks); contents are not kept
     void release();
     template <typename T>
@@ -124,6 +136,7 @@ struct kry_embed {
     int n1 = 0, n2 = 0, M1 = 0, M2 = 0;
     kry_cov cov{};
     kry_prec prec = KRY_F32;
+    cudaStream_t stream = nullptr;   // stream of the creating context (stream-ordered frees)
     // eigenvalues transposed to [M2][M1] (column-pass order) and scaled by
     // 1 / (M1 M2), FP64 always and FP32 when prec = KRY_F32
     double* lam64T = nullptr;
@@ -143,6 +156,9 @@ struct kry_embed {
 namespace kry {
 
 void init_twiddles(kry_ctx* ctx);
+
+// Release every scratch buffer of ctx (mask, twiddles and schedules stay).
+void ctx_trim(kry_ctx* ctx);
 
 // Eigenvalues Lambda = FFT2(c) of the embedding on M1 x M2 (natural order,
 // unscaled, FP64) into ctx->eig_c; returns min and max.

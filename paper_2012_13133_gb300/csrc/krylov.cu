@@ -23,7 +23,7 @@ namespace kry {
 
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
 
 static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
@@ -737,7 +737,8 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     nrm.assign(2 * nrhs, 0.0);
     *fresh = false;
     for (int it = 0; it < maxit + poll; ++it) {
-        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt);
+        // columns that have converged are not transformed (pairs of finished columns skip every pass)
+        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt, S.done);
         k_rcg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
         KRY_CHECK_LAUNCH();
         k_rcg_update<<<gv, 256, 0, st>>>(X, ldx, R, P, Q, p, S, part);

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_a(const T* __restr
                                                   int nvec, int pair0, const int* __restrict__ rowptr,
                                                   const int* __restrict__ colidx, int n1, int n2, int M2, int C,
                                                   int logC, int PS, typename cx_of<T>::type* __restrict__ slab,
-                                                  const void* tw32, const void* tw64) {
+                                                  const void* tw32, const void* tw64, const int* __restrict__ skip) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_a(const T* __restr
     const int pair = pair0 + blockIdx.y;
     const int va = 2 * pair, vb = 2 * pair + 1;
     const bool has_b = vb < nvec;
+    if (skip && skip[va] && (!has_b || skip[vb])) return;   // both columns finished (whole block)
     const Cx* tw = twiddles<T>(tw32, tw64);
     const Cx zero = cmk<Cx>((T)0, (T)0);
 
@@ -299,10 +300,14 @@ template <typename T, int CC>
 __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_b(typename cx_of<T>::type* __restrict__ slab,
                                                   const T* __restrict__ lamT, int n1, int M1, int M2, int PS,
                                                   const void* tw32, const void* tw64, int pair0, int64_t lam_stride,
-                                                  int vpt) {
+                                                  int vpt, const int* __restrict__ skip, int nvec) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
+    if (skip) {
+        const int va = 2 * (pair0 + (int)blockIdx.y), vb = va + 1;
+        if (skip[va] && (vb >= nvec || skip[vb])) return;
+    }
     const int L = M1, b = 31 - __clz(L), LT = L >> 4;
     const int c = threadIdx.x % CC, t = threadIdx.x / CC;
     const int tile = blockIdx.x;
@@ -372,7 +377,8 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
                                                   const int* __restrict__ colidx, int n1, int n2, int M2, int C,
                                                   int logC, int PS, double tau2, double* __restrict__ dots,
                                                   int ndot_stride, const void* tw32, const void* tw64,
-                                                  const double* __restrict__ tau2v, int vpt) {
+                                                  const double* __restrict__ tau2v, int vpt,
+                                                  const int* __restrict__ skip) {
     using Cx = typename cx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx* buf = reinterpret_cast<Cx*>(smem_raw);
@@ -383,6 +389,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
     const int pair = pair0 + blockIdx.y;
     const int va = 2 * pair, vb = 2 * pair + 1;
     const bool has_b = vb < nvec;
+    if (skip && skip[va] && (!has_b || skip[vb])) return;   // both columns finished (whole block)
     const Cx* tw = twiddles<T>(tw32, tw64);
     const Cx zero = cmk<Cx>((T)0, (T)0);
 
@@ -480,7 +487,7 @@ struct MvLaunch {
                   int nvec, int pair0, const int* rowptr, const int* colidx, int n1, int M2, int C, Cx* slab,
                   const void* tw32, const void* tw64) {
         auto k = k_pass_a<T, EPT, G>;
-        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KRY_ALLOW_MAX_SMEM(k);
         k<<<grid, threads, smem, s>>>(vin, ld, scale, nvec, pair0, rowptr, colidx, n1, M2, C, slab, tw32, tw64);
         KRY_CHECK_LAUNCH();
     }
@@ -488,7 +495,7 @@ struct MvLaunch {
     static void b(dim3 grid, int threads, size_t smem, cudaStream_t s, Cx* slab, const T* lamT, int n1, int M1, int M2,
                   const void* tw32, const void* tw64, int pair0 = 0, int64_t lam_stride = 0, int vpt = 0) {
         auto k = k_pass_b<T, EPT, CC>;
-        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KRY_ALLOW_MAX_SMEM(k);
         k<<<grid, threads, smem, s>>>(slab, lamT, n1, M1, M2, tw32, tw64, pair0, lam_stride, vpt);
         KRY_CHECK_LAUNCH();
     }
@@ -498,7 +505,7 @@ struct MvLaunch {
                   const int* colidx, int n1, int n2, int M2, int C, double tau2, double* dots, int nds,
                   const void* tw32, const void* tw64, const double* tau2v = nullptr, int vpt = 0) {
         auto k = k_pass_c<T, EPT, G, MODE>;
-        KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KRY_ALLOW_MAX_SMEM(k);
         k<<<grid, threads, smem, s>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2,
                                       C, tau2, dots, nds, tw32, tw64, tau2v, vpt);
         KRY_CHECK_LAUNCH();
@@ -527,7 +534,7 @@ struct MvLaunch {
 static MvSched pick_sched(kry_ctx* ctx, const MvSched& want, int M1, int M2, bool dbl) {
     MvSched s = want;
     const size_t cs = cx_size(dbl);
-    const size_t lim = (size_t)ctx->max_smem_optin;
+    const size_t lim = (size_t)ctx->max_smem_optin - 1024;   // leave room for static shared memory
     auto fix = [&](int& ept, int& grp, int L) {
         if (ept != 8 && ept != 16) ept = 8;
         if (L < ept) ept = 8;
@@ -592,7 +599,7 @@ const MvSched& sched_for(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec) {
 // Rows per block (pass A/C) and columns per block (pass B, = slab tile width).
 static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, int* C) {
     const MvSched& want = sched_for(ctx, M1, M2, dbl, nvec);
-    const size_t lim = (size_t)ctx->max_smem_optin;
+    const size_t lim = (size_t)ctx->max_smem_optin - 1024;   // leave room for static shared memory
     auto fit = [&](int L, int nt) {
         nt = std::max(1, std::min(nt, 16));
         while (nt > 1 && (nt * (L >> 4) > 512 || smem16(L, nt, dbl) > lim)) nt >>= 1;
@@ -619,7 +626,7 @@ static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, in
 template <typename T>
 static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                          int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode,
-                         typename cx_of<T>::type* slab, int ppb, int vpt) {
+                         typename cx_of<T>::type* slab, int ppb, int vpt, const int* skip) {
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
     int G, C;
@@ -641,34 +648,34 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
         dim3 gA(nbx, np), gB(M2 / C, np);
         KRY_DISPATCH_NT(G, {
             auto k = k16_pass_a<T, N_>;
-            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+            KRY_ALLOW_MAX_SMEM(k);
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
             k<<<gA, thrA, smA, st>>>(vin, ld_in, scale, nvec, pair0, rowptr, colidx, n1, n2, M2, C, logC, psA, slab,
-                                    tw32, tw64);
+                                    tw32, tw64, skip);
             KRY_CHECK_LAUNCH();
         });
         KRY_DISPATCH_NT(C, {
             auto k = k16_pass_b<T, N_>;
-            KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB));
+            KRY_ALLOW_MAX_SMEM(k);
             KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
-            k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64, pair0, e->lam_stride, vpt);
+            k<<<gB, thrB, smB, st>>>(slab, lamT, n1, M1, M2, psB, tw32, tw64, pair0, e->lam_stride, vpt, skip, nvec);
             KRY_CHECK_LAUNCH();
         });
         if (mode == 0) {
             KRY_DISPATCH_NT(G, {
                 auto k = k16_pass_c<T, N_, 0>;
-                KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+                KRY_ALLOW_MAX_SMEM(k);
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt, skip);
                 KRY_CHECK_LAUNCH();
             });
         } else {
             KRY_DISPATCH_NT(G, {
                 auto k = k16_pass_c<T, N_, 1>;
-                KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA));
+                KRY_ALLOW_MAX_SMEM(k);
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt, skip);
                 KRY_CHECK_LAUNCH();
             });
         }
@@ -677,7 +684,8 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
 
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt = 0) {
+                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt = 0,
+                       const int* skip = nullptr) {
     KRY_REQUIRE(vpt == 0 || (vpt % 2 == 0 && nvec % vpt == 0 && nvec / vpt <= e->ntheta), KRY_EINVAL,
                 "vectors per theta must be even and divide the batch");
     using Cx = typename cx_of<T>::type;
@@ -695,7 +703,8 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
             KRY_CUDA(cudaEventCreate(&ev1));
             prof_record(ctx, ev0);
         }
-        run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb, vpt);
+        run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb, vpt,
+                        skip);
         if (ctx->prof_on) {
             prof_record(ctx, ev1);
             ctx->prof_ev.push_back(ev0);
@@ -775,14 +784,14 @@ int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec) {
 
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
-               int64_t ld_out, int nvec, double* dots, int nds, int vpt) {
-    run_matvec<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, e->cov.tau2, dots, nds, 0, vpt);
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt, const int* skip) {
+    run_matvec<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, e->cov.tau2, dots, nds, 0, vpt, skip);
 }
 
 template void matvec_ex<float>(kry_ctx*, const kry_embed*, const float*, int64_t, const double*, float*, int64_t, int,
-                               double*, int, int);
+                               double*, int, int, const int*);
 template void matvec_ex<double>(kry_ctx*, const kry_embed*, const double*, int64_t, const double*, double*, int64_t,
-                                int, double*, int, int);
+                                int, double*, int, int, const int*);
 
 template <typename T>
 void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld, double) {
@@ -960,6 +969,7 @@ static double autotune_t(kry_ctx* ctx, const kry_embed* e, int nvec, MvSched* be
     const uint64_t key = sched_key(M1, M2, dbl, nvec);
     const size_t n = (size_t)nvec * ctx->p;
     DevBuf tv, to;
+    tv.stream = to.stream = ctx->stream;
     tv.ensure(n * sizeof(T));
     to.ensure(n * sizeof(T));
     k_fill_test<T><<<1024, 256, 0, ctx->stream>>>(tv.as<T>(), (int64_t)n);
@@ -971,7 +981,7 @@ static double autotune_t(kry_ctx* ctx, const kry_embed* e, int nvec, MvSched* be
         const int c = (int)std::max<size_t>(1, budget / slab_pair);
         if (c < npairs && std::find(ppbs.begin(), ppbs.end(), c) == ppbs.end()) ppbs.push_back(c);
     }
-    const size_t lim = (size_t)ctx->max_smem_optin;
+    const size_t lim = (size_t)ctx->max_smem_optin - 1024;   // leave room for static shared memory
     double best = 1e30;
     MvSched bs = dbl ? ctx->sched64 : ctx->sched32;
     const bool had = ctx->tuned.count(key) > 0;

@@ -45,6 +45,16 @@ class kry_opts(C.Structure):
 
 _P = C.c_void_p
 _DP = C.POINTER(C.c_double)
+
+
+class kry_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n1", C.c_int32), ("n2", C.c_int32), ("mask", C.c_void_p), ("y", C.c_void_p),
+                ("X", C.c_void_p), ("ncov", C.c_int32), ("cov", kry_cov), ("opts", kry_opts),
+                ("loglik", C.c_void_p), ("logdet", C.c_void_p), ("beta", C.c_void_p),
+                ("target_cells", C.c_void_p), ("target_X", C.c_void_p), ("mean", C.c_void_p)]
+
+
+KRY_REQ_LOGLIK, KRY_REQ_KRIGE = 0, 1
 # name -> (restype, argtypes)
 SIGNATURES = {
     "kry_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
@@ -66,6 +76,12 @@ SIGNATURES = {
                                    C.c_int64, _P, _P, C.c_int64, _P, _P, _P, _DP, _DP, _DP, _DP]),
     "kry_sample": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int32, C.c_int32, _P, _P]),
     "kry_sample_size": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "kry_server_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int32, C.c_int64]),
+    "kry_server_submit": (C.c_int, [_P, C.POINTER(kry_request), C.POINTER(C.c_uint64)]),
+    "kry_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(C.c_int), _DP, C.POINTER(C.c_int32),
+                                  C.c_char_p, C.c_int32]),
+    "kry_server_queued": (C.c_int64, [_P]),
+    "kry_server_destroy": (None, [_P]),
     "kry_autotune": (C.c_int, [_P, _P, C.c_int32, _DP, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32)]),
     "kry_set_schedule": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
@@ -312,3 +328,73 @@ class Context:
         out = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=xi.device)
         self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, _ptr(xi.contiguous()), _ptr(out)))
         return out
+
+
+def _np_ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Server:
+    """Continuous-batching server of the library (host buffers in, host buffers out)."""
+
+    def __init__(self, device: int = 0, nslots: int = 4, mem_budget_bytes: int = 64 << 30):
+        h = C.c_void_p()
+        st = _lib.kry_server_create(C.byref(h), device, nslots, int(mem_budget_bytes))
+        if st != KRY_OK:
+            raise KryError(st, "kry_server_create failed")
+        self.h = h
+        self._live = {}
+
+    def submit(self, kind, mask, y, X, cov, opts: Opts, target_cells=None, target_X=None) -> int:
+        """mask: (n1, n2) bool/uint8; y: (p,) float64; X: (ncov, p) float64 (column-major p x ncov);
+        target_cells: (nt,) int64 unobserved cells and target_X: (ncov, nt) for kriging."""
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        ncov = X.shape[0]
+        out = dict(loglik=np.zeros(1), logdet=np.zeros(1), beta=np.zeros(ncov))
+        keep = [m, y, X]
+        r = kry_request()
+        r.kind = kind
+        r.n1, r.n2 = m.shape
+        r.mask, r.y, r.X, r.ncov = _np_ptr(m), _np_ptr(y), _np_ptr(X), ncov
+        r.cov = make_cov(cov)
+        r.opts = opts.c()
+        r.loglik, r.logdet, r.beta = _np_ptr(out["loglik"]), _np_ptr(out["logdet"]), _np_ptr(out["beta"])
+        if kind == KRY_REQ_KRIGE:
+            tc = np.ascontiguousarray(target_cells, dtype=np.int64)
+            tX = np.ascontiguousarray(target_X, dtype=np.float64)
+            out["mean"] = np.zeros(tc.shape[0])
+            keep += [tc, tX]
+            r.target_cells, r.target_X, r.mean = _np_ptr(tc), _np_ptr(tX), _np_ptr(out["mean"])
+        t = C.c_uint64()
+        st = _lib.kry_server_submit(self.h, C.byref(r), C.byref(t))
+        if st != KRY_OK:
+            raise KryError(st, "kry_server_submit refused the request")
+        self._live[t.value] = (keep, out, r)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        rs, lat, slot = C.c_int(), C.c_double(), C.c_int32()
+        err = C.create_string_buffer(512)
+        st = _lib.kry_server_wait(self.h, ticket, timeout_s, C.byref(rs), C.byref(lat), C.byref(slot), err, 512)
+        if st != KRY_OK:
+            raise KryError(st, f"wait on ticket {ticket}")
+        keep, out, _ = self._live.pop(ticket)
+        res = {k: (v[0] if k in ("loglik", "logdet") else v) for k, v in out.items()}
+        res.update(status=rs.value, latency_ms=lat.value, slot=slot.value, error=err.value.decode())
+        return res
+
+    def queued(self) -> int:
+        return int(_lib.kry_server_queued(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.kry_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,148 @@
+"""Serving driver: a Poisson stream of likelihood and kriging requests through
+the library's continuous-batching server (kry_server_*).
+
+Requests follow the serving workload: square grids with sides drawn
+log-uniformly, masks with 10-90% missing cells (half in circular gaps like
+cloud cover, half uniform), Matern nu in {1/2, 3/2}, random range and nugget,
+and GP data drawn by the library's circulant-embedding sampler.  The stream
+is replayed against a one-slot server (one request at a time) and against a
+multi-slot server at the same arrival times; each prints p50/p99 latency and
+requests/s.
+
+  python -m paper_2012_13133_gb300.serve --n-requests 200 --slots 8
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2012_13133_gb300 import inputs as I  # noqa: E402
+
+
+def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000):
+    """Materialise request specs (inputs.serve_requests) into host arrays,
+    drawing each data set with the GPU sampler."""
+    import torch
+
+    from paper_2012_13133_gb300 import kry
+    ctx = kry.Context(device)
+    dev = torch.device("cuda", device)
+    out = []
+    for sp in specs:
+        n = sp["n"]
+        mask = I.mask_mixed(n, n, sp["frac_missing"], sp["mask_seed"])
+        cov = I.Cov(1.0, sp["range"], sp["nu"], sp["tau2"])
+        p = ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(dev))
+        M1, M2, _ = ctx.sample_size(cov)
+        xi, eps = I.data_noise(M1, M2, p, sp["data_seed"])
+        field = ctx.sample(cov, M1, M2, torch.tensor(xi, device=dev)).cpu().numpy()
+        S1, S2 = I.cell_centres(n, n)
+        X = I.covariates(S1[mask], S2[mask])
+        y = X @ np.array([1.0, 0.5, -0.5]) + field[mask] + math.sqrt(cov.tau2) * eps
+        req = dict(spec=sp, kind=kry.KRY_REQ_LOGLIK if sp["kind"] == "loglik" else kry.KRY_REQ_KRIGE,
+                   mask=mask, y=y, X=np.ascontiguousarray(X.T), cov=cov,
+                   opts=kry.Opts(prec=kry.KRY_F32, nprobe=nprobe, nsteps=nsteps, seed=sp["id"], rtol=rtol,
+                                 maxit=maxit))
+        if sp["kind"] == "krige":
+            cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+            req["target_cells"] = cells
+            req["target_X"] = np.ascontiguousarray(I.covariates(S1.ravel()[cells], S2.ravel()[cells]).T)
+        out.append(req)
+    ctx.close()
+    return out
+
+
+def replay(server, reqs, arrivals, timeout_s=3600.0):
+    """Submit request i at time arrivals[i] (seconds from start); collect results.
+    Returns (results in request order, wall seconds from first arrival to last completion)."""
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = server.submit(r["kind"], r["mask"], r["y"], r["X"], r["cov"], r["opts"],
+                                       r.get("target_cells"), r.get("target_X"))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    results = [None] * len(reqs)
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        results[i] = server.wait(tickets[i], timeout_s)
+    th.join()
+    return results, time.perf_counter() - t0
+
+
+def summarise(results, wall):
+    lat = np.array([r["latency_ms"] for r in results])
+    return {"requests": len(results), "requests_per_s": len(results) / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "wall_s": wall,
+            "status_counts": {str(k): int(v) for k, v in zip(*np.unique([r["status"] for r in results],
+                                                                        return_counts=True))}}
+
+
+def main():
+    from paper_2012_13133_gb300 import kry
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-requests", type=int, default=200)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--rate-factor", type=float, default=1.5,
+                    help="arrival rate as a multiple of the measured one-slot throughput")
+    ap.add_argument("--side-min", type=int, default=128)
+    ap.add_argument("--side-max", type=int, default=2048)
+    ap.add_argument("--budget-gb", type=float, default=96.0)
+    ap.add_argument("--seed", type=int, default=4)
+    args = ap.parse_args()
+
+    w = I.WORKLOADS["serve"]
+    specs = I.serve_requests(args.n_requests, args.seed, args.side_min, args.side_max, rate=1.0)
+    t = time.perf_counter()
+    reqs = build_requests(specs)
+    prep_s = time.perf_counter() - t
+    budget = int(args.budget_gb * (1 << 30))
+
+    # one request at a time: measure service throughput with all requests queued at t = 0
+    one = kry.Server(0, 1, budget)
+    res1, wall1 = replay(one, reqs, np.zeros(len(reqs)))
+    one.close()
+    mu1 = len(reqs) / wall1
+    rate = args.rate_factor * mu1
+    gaps = np.random.default_rng(args.seed + 1).exponential(1.0 / rate, size=len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+
+    single = kry.Server(0, 1, budget)
+    res_s, wall_s = replay(single, reqs, arrivals)
+    single.close()
+    multi = kry.Server(0, args.slots, budget)
+    res_m, wall_m = replay(multi, reqs, arrivals)
+    multi.close()
+
+    same = max(abs(a["loglik"] - b["loglik"]) / max(1.0, abs(a["loglik"]))
+               for a, b, r in zip(res_s, res_m, reqs) if r["kind"] == kry.KRY_REQ_LOGLIK) if any(
+        r["kind"] == kry.KRY_REQ_LOGLIK for r in reqs) else 0.0
+    print(json.dumps({"metric": "serving p50/p99 latency and requests/s", "workload": w.name,
+                      "n_requests": len(reqs), "arrival_rate_per_s": rate, "prep_s": prep_s,
+                      "one_slot_saturated": summarise(res1, wall1),
+                      "one_slot": summarise(res_s, wall_s), f"{args.slots}_slots": summarise(res_m, wall_m),
+                      "max_rel_loglik_diff_single_vs_mixed": same}))
+
+
+if __name__ == "__main__":
+    main()
