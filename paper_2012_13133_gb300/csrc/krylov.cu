@@ -116,6 +116,24 @@ __device__ __forceinline__ void block_sum_store(double (&v)[N], double* out, int
     }
 }
 
+// Sum of part[0..n) by one block in a fixed order (strided per-thread sums,
+// then a shuffle tree, then the warp sums in order); the result is valid in
+// thread 0.  Deterministic for a given block size.
+__device__ __forceinline__ double block_sum(const double* __restrict__ part, int n) {
+    __shared__ double ws[32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    return t;
+}
+
+static const int FIN_THREADS = 256;   // block size of the per-vector finalisers
+
 // ------------------------------------------------------------------ Lanczos
 
 struct LanczosState {
@@ -137,11 +155,9 @@ __global__ void k_lanczos_init(LanczosState S, int nprobe, int nsteps, double s0
 // alpha_j = sum of the block partials of q_j^T K q_j (fixed order).
 __global__ void k_lanczos_alpha(LanczosState S, const double* __restrict__ part, int nblk, int nprobe, int nsteps,
                                 int j) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nprobe) return;
-    double a = 0.0;
-    for (int b = 0; b < nblk; ++b) a += part[(int64_t)k * nblk + b];
-    S.alpha[(int64_t)k * nsteps + j] = a;
+    const int k = blockIdx.x;   // one block per vector
+    const double a = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x == 0) S.alpha[(int64_t)k * nsteps + j] = a;
 }
 
 // w_next = U - alpha_j s_cur W_cur - beta_{j-1} s_prev W_prev;  partial ||w_next||^2.
@@ -168,10 +184,9 @@ __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ 
 // beta_j = ||w_next||; early stop when beta_j < 1e-12 |alpha_1|; rescale.
 __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, int nblk, int nprobe, int nsteps,
                                int j) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nprobe) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+    const int k = blockIdx.x;   // one block per vector
+    const double s = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x != 0) return;
     const double bj = sqrt(s);
     const bool stopped = S.m_eff[k] < nsteps;
     if (!stopped && bj < 1e-12 * fabs(S.alpha[(int64_t)k * nsteps])) S.m_eff[k] = j + 1;
@@ -281,13 +296,13 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     auto step = [&](int j) {
         cudaStream_t st = ctx->stream;
         matvec_ex<T>(ctx, e, W[ic], p, S.s_cur, U, p, nvec, part, nblkC, vpt);
-        k_lanczos_alpha<<<(nvec + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nvec, nsteps, j);
+        k_lanczos_alpha<<<nvec, FIN_THREADS, 0, st>>>(S, part, nblkC, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
         if (j == nsteps - 1) return;
         dim3 gu(RED_BLOCKS, nvec);
         k_lanczos_update<T><<<gu, 256, 0, st>>>(U, W[ic], W[ip], W[in], p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
-        k_lanczos_beta<<<(nvec + tb - 1) / tb, tb, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
+        k_lanczos_beta<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
         const int t = ip;
         ip = ic;
@@ -371,11 +386,10 @@ __global__ void k_cg_init_scalars(CgState S, const double* __restrict__ part, in
 }
 
 __global__ void k_cg_alpha(CgState S, const double* __restrict__ part, int nblk, int nrhs) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nrhs) return;
-    double pq = 0.0;
-    for (int b = 0; b < nblk; ++b) pq += part[(int64_t)k * nblk + b];
-    S.alpha[k] = (S.done[k] || pq == 0.0) ? 0.0 : S.rr[k] / pq;
+    const int k = blockIdx.x;   // one block per right-hand side
+    const double pq = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x == 0) S.alpha[k] = (S.done[k] || pq == 0.0) ? 0.0 : S.rr[k] / pq;
+    if (k == 0 && threadIdx.x == 0) *S.ndone = 0;
 }
 
 // x += alpha p, r -= alpha q; partial ||r||^2.
@@ -400,10 +414,10 @@ __global__ void k_cg_update(T* __restrict__ X, T* __restrict__ R, const T* __res
 }
 
 __global__ void k_cg_beta(CgState S, const double* __restrict__ part, int nblk, int nrhs, int maxit) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nrhs && !S.done[k]) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
+    const int k = blockIdx.x;   // one block per right-hand side
+    const double s = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x != 0) return;
+    if (!S.done[k]) {
         S.iters[k] += 1;
         S.beta[k] = s / S.rr[k];
         S.rr[k] = s;
@@ -411,15 +425,10 @@ __global__ void k_cg_beta(CgState S, const double* __restrict__ part, int nblk, 
             S.done[k] = 1;
             S.beta[k] = 0.0;
         }
-    } else if (k < nrhs) {
+    } else {
         S.beta[k] = 0.0;
     }
-    __syncthreads();
-    if (k == 0) {
-        int nd = 0;
-        for (int i = 0; i < nrhs; ++i) nd += S.done[i];
-        *S.ndone = nd;
-    }
+    if (S.done[k]) atomicAdd(S.ndone, 1);
 }
 
 template <typename T>
@@ -475,11 +484,11 @@ static int cg_inner(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t l
     const int poll = 8;
     for (; it < maxit; ++it) {
         matvec_ex<T>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt);
-        k_cg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
+        k_cg_alpha<<<nrhs, FIN_THREADS, 0, st>>>(S, part, nblkC, nrhs);
         KRY_CHECK_LAUNCH();
         k_cg_update<T><<<gv, 256, 0, st>>>(X, R, P, Q, p, S, part);
         KRY_CHECK_LAUNCH();
-        k_cg_beta<<<1, std::max(32, ((nrhs + 31) / 32) * 32), 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
+        k_cg_beta<<<nrhs, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
         KRY_CHECK_LAUNCH();
         k_cg_pupdate<T><<<gv, 256, 0, st>>>(P, R, p, S);
         KRY_CHECK_LAUNCH();
@@ -609,11 +618,10 @@ __global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part, 
 }
 
 __global__ void k_rcg_alpha(RcgState S, const double* __restrict__ part, int nblk, int nrhs) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nrhs) return;
-    double pq = 0.0;
-    for (int b = 0; b < nblk; ++b) pq += part[(int64_t)k * nblk + b];
-    S.alpha[k] = (S.done[k] || !(pq > 0.0)) ? 0.0 : S.rr[k] / pq;
+    const int k = blockIdx.x;   // one block per right-hand side
+    const double pq = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x == 0) S.alpha[k] = (S.done[k] || !(pq > 0.0)) ? 0.0 : S.rr[k] / pq;
+    if (k == 0 && threadIdx.x == 0) *S.nwant = 0;
 }
 
 // X += alpha P (FP64), R -= alpha Q (FP32); partial ||R||^2.
@@ -639,22 +647,19 @@ __global__ void k_rcg_update(double* __restrict__ X, int64_t ldx, float* __restr
 // beta = rr_new / rr; ask for a residual replacement when r^T r fell 100x
 // (||r|| 10x) since the last one or reached the target.
 __global__ void k_rcg_beta(RcgState S, const double* __restrict__ part, int nblk, int nrhs, int maxit) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x;   // one block per right-hand side
+    const double s = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x != 0) return;
     int want = 0;
-    if (k < nrhs) {
-        if (!S.done[k]) {
-            double s = 0.0;
-            for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
-            S.iters[k] += 1;
-            S.beta[k] = (S.rr[k] > 0.0) ? s / S.rr[k] : 0.0;
-            S.rr[k] = s;
-            want = (s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit) ? 1 : 0;
-        } else {
-            S.beta[k] = 0.0;
-        }
+    if (!S.done[k]) {
+        S.iters[k] += 1;
+        S.beta[k] = (S.rr[k] > 0.0) ? s / S.rr[k] : 0.0;
+        S.rr[k] = s;
+        want = (s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit) ? 1 : 0;
+    } else {
+        S.beta[k] = 0.0;
     }
-    const int n = __syncthreads_count(want);
-    if (threadIdx.x == 0) *S.nwant = n;
+    if (want) atomicAdd(S.nwant, 1);
 }
 
 __global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S) {
@@ -739,11 +744,11 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     for (int it = 0; it < maxit + poll; ++it) {
         // columns that have converged are not transformed (pairs of finished columns skip every pass)
         matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt, S.done);
-        k_rcg_alpha<<<(nrhs + tb - 1) / tb, tb, 0, st>>>(S, part, nblkC, nrhs);
+        k_rcg_alpha<<<nrhs, FIN_THREADS, 0, st>>>(S, part, nblkC, nrhs);
         KRY_CHECK_LAUNCH();
         k_rcg_update<<<gv, 256, 0, st>>>(X, ldx, R, P, Q, p, S, part);
         KRY_CHECK_LAUNCH();
-        k_rcg_beta<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
+        k_rcg_beta<<<nrhs, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
         KRY_CHECK_LAUNCH();
         k_rcg_pupdate<<<gv, 256, 0, st>>>(P, R, p, S);
         KRY_CHECK_LAUNCH();
