@@ -230,19 +230,30 @@ def rademacher_probe(seed, k, p):
 # --------------------------------------------------------------------------------------
 
 
-def lanczos(matvec, z, m):
-    """m steps of symmetric Lanczos from q1 = z/||z||, no reorthogonalisation
-    (the paper reorthogonalises nothing, Sec. 3.2).  Stops early when
-    beta_j < 1e-12 |alpha_1|.  Returns alpha (length k) and beta (length k-1)."""
+def lanczos(matvec, z, m, reorth=False):
+    """m steps of symmetric Lanczos from q1 = z/||z||.  Stops early when
+    beta_j < 1e-12 |alpha_1|.  Returns alpha (length k) and beta (length k-1).
+
+    reorth=False is the recurrence as the paper runs it for its results (the
+    basis is not reorthogonalised, Sec. 3.2).  reorth=True orthogonalises each
+    new vector against every earlier one (classical Gram-Schmidt, applied
+    twice), the reorthogonalisation Sec. 3.2 leaves to the user: the
+    tridiagonal is then, up to rounding, the exact-arithmetic one, i.e. the
+    Jacobi matrix of the m-point Gauss rule of the spectral measure of z."""
     q = z / np.linalg.norm(z)
     q_prev = np.zeros_like(q)
     b_prev = 0.0
+    basis = [q]
     alpha, beta = [], []
     for j in range(m):
         u = matvec(q)
         a = float(q @ u)
         w = u - a * q - b_prev * q_prev
         alpha.append(a)
+        if reorth:
+            Q = np.array(basis)
+            for _ in range(2):
+                w = w - Q.T @ (Q @ w)
         b = float(np.linalg.norm(w))
         if j == m - 1:
             break
@@ -250,6 +261,8 @@ def lanczos(matvec, z, m):
             break
         beta.append(b)
         q_prev, q, b_prev = q, w / b, b
+        if reorth:
+            basis.append(q)
     return np.array(alpha), np.array(beta)
 
 
@@ -262,15 +275,15 @@ def gauss_quadrature_logdet(alpha, beta, znorm2):
     return znorm2 * float(np.sum(U[0] ** 2 * np.log(theta)))
 
 
-def slq_logdet(matvec, p, nprobe, nsteps, seed, probes=None):
+def slq_logdet(matvec, p, nprobe, nsteps, seed, probes=None, reorth=False):
     """SLQ estimate of log det K: mean over probes of the Gauss quadrature of
     z^T log(K) z.  ``probes`` overrides the Rademacher probes (e.g. the unit
-    vectors, for which the sum over all p probes is exact up to quadrature error).
-    Returns (estimate, standard error, per-probe values)."""
+    vectors, for which the sum over all p probes is exact up to quadrature error);
+    ``reorth`` as in ``lanczos``.  Returns (estimate, standard error, per-probe values)."""
     vals = []
     for k in range(nprobe):
         z = rademacher_probe(seed, k, p) if probes is None else probes(k)
-        a, b = lanczos(matvec, z, nsteps)
+        a, b = lanczos(matvec, z, nsteps, reorth)
         vals.append(gauss_quadrature_logdet(a, b, float(z @ z)))
     vals = np.array(vals)
     se = float(np.std(vals, ddof=1) / math.sqrt(nprobe)) if nprobe > 1 else 0.0
@@ -376,19 +389,19 @@ class FFTProblem:
         cols, its = zip(*(cg(self.matvec, B[:, j], tol) for j in range(B.shape[1])))
         return np.stack(cols, axis=1), max(its)
 
-    def logdet(self, nprobe, nsteps, seed, probe_ids=None):
+    def logdet(self, nprobe, nsteps, seed, probe_ids=None, reorth=False):
         ids = range(nprobe) if probe_ids is None else probe_ids
         vals = []
         for k in ids:
             z = rademacher_probe(seed, k, self.p)
-            a, b = lanczos(self.matvec, z, nsteps)
+            a, b = lanczos(self.matvec, z, nsteps, reorth)
             vals.append(gauss_quadrature_logdet(a, b, float(z @ z)))
         vals = np.array(vals)
         se = float(np.std(vals, ddof=1) / math.sqrt(len(vals))) if len(vals) > 1 else 0.0
         return float(np.mean(vals)), se, vals
 
-    def profile_loglik(self, y, X, nprobe, nsteps, seed, tol=1e-10):
-        ld, se, _ = self.logdet(nprobe, nsteps, seed)
+    def profile_loglik(self, y, X, nprobe, nsteps, seed, tol=1e-10, reorth=False):
+        ld, se, _ = self.logdet(nprobe, nsteps, seed, reorth=reorth)
         sol, _ = self.solve(np.column_stack([y, X]), tol)
         ll, beta, quad = gls_loglik(ld, sol[:, 0], sol[:, 1:], y, X)
         return dict(loglik=ll, beta=beta, logdet=ld, logdet_se=se, quad=quad)

@@ -203,6 +203,53 @@ def test_slq_quadrature_equals_quadratic_form_of_logK():
     assert O.gauss_quadrature_logdet(a, b, float(z @ z)) == pytest.approx(ref, rel=1e-9)
 
 
+def _gauss_rule_logsum_mp(nodes, m, dps=60):
+    """sum_i tau_i^2 log theta_i of the m-point Gauss rule of the uniform measure on
+    ``nodes``, by the discretised Stieltjes procedure (monic orthogonal
+    polynomials evaluated at the nodes) and the eigenvalues of the Jacobi matrix,
+    all in dps-digit arithmetic."""
+    mp = pytest.importorskip("mpmath").mp
+    mp.dps = dps
+    x = [mp.mpf(float(v)) for v in nodes]
+    w = mp.mpf(1) / len(x)
+    pi_prev, pi = [mp.mpf(0)] * len(x), [mp.mpf(1)] * len(x)
+    a, b2, nrm_prev = [], [], None
+    for k in range(m):
+        nrm = w * sum(t * t for t in pi)
+        a.append(w * sum(xi * t * t for xi, t in zip(x, pi)) / nrm)
+        bk2 = nrm / nrm_prev if nrm_prev is not None else mp.mpf(0)
+        if k > 0:
+            b2.append(bk2)
+        pi_prev, pi = pi, [(xi - a[k]) * t - bk2 * tp for xi, t, tp in zip(x, pi, pi_prev)]
+        nrm_prev = nrm
+    J = mp.matrix(m, m)
+    for i in range(m):
+        J[i, i] = a[i]
+        if i + 1 < m:
+            J[i, i + 1] = J[i + 1, i] = mp.sqrt(b2[i])
+    theta, V = mp.eigsy(J)
+    return float(sum(V[0, i] ** 2 * mp.log(theta[i]) for i in range(m)))
+
+
+def test_reorthogonalised_lanczos_is_the_gauss_rule_of_the_spectral_measure():
+    """Sec. 3.2's optional reorthogonalisation: the tridiagonal is then the
+    exact-arithmetic one, so its quadrature is the m-point Gauss rule of the
+    spectral measure of q1.  K = diag(lam) with a Rademacher start puts weight
+    1/p on every eigenvalue; the reference rule comes from the Stieltjes
+    procedure in 60-digit arithmetic (another algorithm, another precision).
+    The spectrum (condition 1e7) makes the plain FP64 recurrence lose
+    orthogonality within m = 60 steps, so the case also shows the option matters."""
+    p, m = 300, 60
+    lam = np.geomspace(1e-3, 1e4, p)
+    z = O.rademacher_probe(3, 0, p)
+    ref = _gauss_rule_logsum_mp(lam, m)
+    a, b = O.lanczos(lambda v: lam * v, z, m, reorth=True)
+    assert len(a) == m
+    assert O.gauss_quadrature_logdet(a, b, 1.0) == pytest.approx(ref, rel=1e-11, abs=1e-11)
+    a0, b0 = O.lanczos(lambda v: lam * v, z, m)
+    assert abs(O.gauss_quadrature_logdet(a0, b0, 1.0) - ref) > 1e-6 * abs(ref)
+
+
 def test_slq_nugget_only_is_exact():
     p = 50
     tau2 = 0.37
