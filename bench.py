@@ -152,7 +152,7 @@ class Problem:
         self.Xc = torch.tensor(I.covariates(S1.ravel()[cells], S2.ravel()[cells]).T.copy(), device=dev)
         self.mean = torch.empty(cells.size, dtype=torch.float64, device=dev)
         self.opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed,
-                             rtol=w.cg_tol, maxit=10000)
+                             rtol=w.cg_tol, maxit=10000, reorth=w.reorth)
         self.M1, self.M2 = I_embed(w.n1), I_embed(w.n2)
         # host copies for the end-to-end leg (pinned)
         self.y_h = self.y.cpu().pin_memory()
@@ -308,7 +308,9 @@ def run_gpu(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": workload_desc(w), "grid": [n1, n2], "embedding": [M1, M2], "p": p,
-                   "probes": w.nprobe, "lanczos_steps": w.nsteps, "kriging_cells": int(prob.cells.numel()),
+                   "probes": w.nprobe, "lanczos_steps": w.nsteps,
+                   "lanczos_basis": "partial reorthogonalisation" if w.reorth else "plain recurrence",
+                   "kriging_cells": int(prob.cells.numel()),
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "gpu_launches": int(launches),
@@ -361,7 +363,8 @@ def cpu_baseline(w, mask=None, mv_per_eval=None, budget_s=20.0):
     evals = 1.0 / (per_mv * mpe)
     return {"value": evals, "unit": "evals/s", "cores": O._WORKERS, "kind": "oracle",
             "sample": f"{n} FP64 FFT matvecs of the oracle at full size ({per_mv * 1e3:.1f} ms each, one real "
-                      f"vector each), scaled by {mpe} real-vector matvecs per evaluation "
+                      f"vector each; matvec time only, the oracle's vector updates and reorthogonalisation "
+                      f"are not counted), scaled by {mpe} real-vector matvecs per evaluation "
                       f"({'as counted in the GPU step' if mv_per_eval else 'SLQ + 4 x 2500 CG iterations + 1'})"}
 
 

@@ -82,13 +82,18 @@ typedef struct {
 
 /* Krylov settings.  nprobe Rademacher probes x nsteps Lanczos steps for the
  * log-determinant; CG to true relative residual rtol (maxit iterations at most
- * per right-hand side). */
+ * per right-hand side).  reorth: 0 = the Lanczos basis is not
+ * reorthogonalised (as the paper runs it for its results, Sec. 3.2); 1 =
+ * partial reorthogonalisation (Sec. 3.2 leaves a scheme to the user; see
+ * kry_logdet), which keeps every basis vector on the device
+ * (nprobe * nsteps * p values of the embedding's precision). */
 typedef struct {
     kry_prec prec;
     int32_t nprobe, nsteps;
     uint64_t seed;
     double rtol;
     int32_t maxit;
+    int32_t reorth;
 } kry_opts;
 
 typedef struct kry_ctx kry_ctx;       /* opaque, library-owned */
@@ -144,13 +149,20 @@ kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_de
 /* Stochastic Lanczos quadrature estimate of log det K (Sec. 3.3, stochastic
  * trace alternative): probe k has entries z_k[i] = +1 if bit 63 of
  * splitmix64(seed XOR (k * 2^32 + i)) is 0, else -1; nsteps Lanczos steps
- * from q1 = z/||z|| without reorthogonalisation (Sec. 3.2 reorthogonalises
- * nothing), stopping early when beta_j < 1e-12 |alpha_1|; Gauss quadrature
- * ||z||^2 sum_j tau_j^2 log theta_j of the tridiagonal.  *logdet = mean over
+ * from q1 = z/||z||, stopping early when beta_j < 1e-12 |alpha_1|; Gauss
+ * quadrature ||z||^2 sum_j tau_j^2 log theta_j of the tridiagonal.
+ * reorth = 0: plain three-term recurrence (the paper's runs, Sec. 3.2).
+ * reorth = 1: partial reorthogonalisation (Simon 1984): per probe, estimates
+ * of the basis' loss of orthogonality are carried by a scalar recurrence and,
+ * when one exceeds sqrt(unit roundoff) of the embedding's precision, the new
+ * basis vector and the next are orthogonalised against all earlier ones; the
+ * result then follows the exact-arithmetic Gauss rule, which the plain FP32
+ * recurrence misses by ~1e-3 on ill-conditioned K.  *logdet = mean over
  * probes, *stderr_out = standard error (NULL allowed), per_probe[nprobe] the
  * per-probe values (host, NULL allowed).  Synchronises the stream. */
 kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps,
-                      uint64_t seed, double* logdet, double* stderr_out, double* per_probe);
+                      uint64_t seed, int32_t reorth, double* logdet, double* stderr_out,
+                      double* per_probe);
 
 /* Solve K X = B for nrhs FP64 right-hand sides (column-major, leading
  * dimension ld) by CG from X = 0 until the true residual satisfies

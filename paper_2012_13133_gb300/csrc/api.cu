@@ -15,11 +15,12 @@
 
 namespace kry {
 void store_embedding(kry_ctx* ctx, kry_embed* e, int slot);
-void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_vec);
+void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth,
+                    double* per_vec);
 template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
-void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe);
+void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth, double* per_probe);
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
                 double rtol, int maxit, int vpt = 0);
 GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet);
@@ -438,14 +439,15 @@ static void mean_se(const std::vector<double>& v, double* mean, double* se) {
     if (se) *se = (n > 1) ? sqrt(q / (n - 1) / n) : 0.0;
 }
 
-kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps, uint64_t seed, double* logdet,
-                      double* stderr_out, double* per_probe) {
+kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps, uint64_t seed, int32_t reorth,
+                      double* logdet, double* stderr_out, double* per_probe) {
     return guarded(ctx, [&]() -> kry_status {
         check_embed(ctx, e);
         KRY_REQUIRE(logdet != nullptr, KRY_EINVAL, "logdet is NULL");
         KRY_REQUIRE(nprobe >= 1 && nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
+        KRY_REQUIRE(reorth == 0 || reorth == 1, KRY_EINVAL, "reorth must be 0 or 1");
         std::vector<double> vals(nprobe);
-        kry::logdet(ctx, e, nprobe, nsteps, seed, vals.data());
+        kry::logdet(ctx, e, nprobe, nsteps, seed, reorth != 0, vals.data());
         double se = 0.0;
         mean_se(vals, logdet, &se);
         if (stderr_out) *stderr_out = se;
@@ -477,6 +479,7 @@ static void check_opts(const kry_opts* o) {
     KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64, KRY_EINVAL, "opts->prec invalid");
     KRY_REQUIRE(o->nprobe >= 1 && o->nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
     KRY_REQUIRE(o->rtol > 0 && o->maxit >= 1, KRY_EINVAL, "need rtol > 0 and maxit >= 1");
+    KRY_REQUIRE(o->reorth == 0 || o->reorth == 1, KRY_EINVAL, "opts->reorth must be 0 or 1");
 }
 
 // [y, X] packed into one (p x (ncov+1)) FP64 block and its solve Z = K^-1 [y, X].
@@ -519,9 +522,9 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
                 // log-determinants: ng settings x nprobe probes in one batched Lanczos
                 std::vector<double> vals((size_t)ng * opts->nprobe);
                 if (ng > 1)
-                    kry::logdet_batched(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+                    kry::logdet_batched(ctx, e, opts->nprobe, opts->nsteps, opts->seed, opts->reorth != 0, vals.data());
                 else
-                    kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+                    kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, opts->reorth != 0, vals.data());
                 // right-hand sides [y, X] (zero-padded to ncp columns) repeated for each setting
                 ctx->zbuf.ensure((size_t)(nc + 2 * (size_t)ng * ncp) * p * sizeof(double));
                 double* V = ctx->zbuf.as<double>();
@@ -663,7 +666,7 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
         kry_status st = KRY_OK;
         try {
             std::vector<double> vals(opts->nprobe);
-            kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, vals.data());
+            kry::logdet(ctx, e, opts->nprobe, opts->nsteps, opts->seed, opts->reorth != 0, vals.data());
             double ld = 0, se = 0;
             mean_se(vals, &ld, &se);
             double *V, *Z;

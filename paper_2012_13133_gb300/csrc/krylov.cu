@@ -136,12 +136,20 @@ static const int FIN_THREADS = 256;   // block size of the per-vector finalisers
 
 // ------------------------------------------------------------------ Lanczos
 
+#define KRY_MAX_STEPS 256
+
 struct LanczosState {
     double* s_cur;    // [nprobe] scale of the current vector: q_j = s_cur * W_cur
     double* s_prev;   // [nprobe]
     double* alpha;    // [nprobe][nsteps]
     double* beta;     // [nprobe][nsteps]
     int* m_eff;       // [nprobe] Lanczos steps kept (early stop on breakdown)
+    // partial reorthogonalisation only (all NULL without it)
+    double* s_hist;   // [nprobe][nsteps] scale of every stored basis vector: q_i = s_hist[i] * W_i
+    double* omega;    // [3][nprobe][nsteps + 1] estimates of q_j^T q_k for j-1, j, j+1 (buffer j mod 3)
+    double* coef;     // [nprobe][nsteps] s_i * q_i^T w of the vector being reorthogonalised
+    int* flag;        // [nprobe] 1: reorthogonalise the new vector of this step
+    int* force;       // [nprobe] 1: the next new vector is reorthogonalised too
 };
 
 __global__ void k_lanczos_init(LanczosState S, int nprobe, int nsteps, double s0) {
@@ -150,6 +158,12 @@ __global__ void k_lanczos_init(LanczosState S, int nprobe, int nsteps, double s0
     S.s_cur[k] = s0;
     S.s_prev[k] = 0.0;
     S.m_eff[k] = nsteps;
+    if (S.s_hist) {
+        S.s_hist[(int64_t)k * nsteps] = s0;
+        S.omega[(int64_t)k * (nsteps + 1)] = 1.0;   // omega_{0,0}
+        S.flag[k] = 0;
+        S.force[k] = 0;
+    }
 }
 
 // alpha_j = sum of the block partials of q_j^T K q_j (fixed order).
@@ -194,13 +208,133 @@ __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, 
     S.beta[(int64_t)k * nsteps + j] = now_stopped ? 0.0 : bj;
     S.s_prev[k] = S.s_cur[k];
     S.s_cur[k] = now_stopped ? 0.0 : 1.0 / bj;
+    if (S.s_hist && j + 1 < nsteps) S.s_hist[(int64_t)k * nsteps + j + 1] = S.s_cur[k];
+}
+
+// ------------------------------------------------------------------ partial reorthogonalisation
+//
+// The basis may lose orthogonality (Sec. 3.2, which leaves a reorthogonalisation
+// scheme to the user); in FP32 the loss reaches the Gauss quadrature within a
+// few tens of steps.  Partial reorthogonalisation (H. D. Simon, "The Lanczos
+// algorithm with partial reorthogonalization", Math. Comp. 42, 1984) tracks
+// estimates omega_{j,k} of q_j^T q_k by a scalar recurrence derived from the
+// three-term recurrences of q_j and q_k, with a rounding term of size
+// eps (beta_k + beta_j); when the largest estimate for the new vector exceeds
+// sqrt(eps) (eps = unit roundoff of the vectors), the new vector and the one
+// after it are orthogonalised against every stored basis vector (one classical
+// Gram-Schmidt pass) and their estimates reset to eps.  Semi-orthogonality
+// (|q_j^T q_k| <= sqrt(eps)) keeps the tridiagonal equal to the projection of K
+// on the Krylov space up to O(eps ||K||) (Simon 1984).  Decisions are per
+// vector, on the device, so the launch sequence is fixed and graph-capturable.
+
+// Estimates for q_{j+1} from ||w||^2 partials (before any reorthogonalisation);
+// sets flag[k] when w is to be reorthogonalised.
+__global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int nblk, int nsteps, int j,
+                            double eps) {
+    const int k = blockIdx.x;   // one block per vector
+    const double s = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x != 0) return;
+    const int64_t ostride = (int64_t)gridDim.x * (nsteps + 1);
+    double* on = S.omega + ((j + 1) % 3) * ostride + (int64_t)k * (nsteps + 1);   // omega_{j+1, .}
+    const double* oc = S.omega + (j % 3) * ostride + (int64_t)k * (nsteps + 1);   // omega_{j, .}
+    const double* op = S.omega + ((j + 2) % 3) * ostride + (int64_t)k * (nsteps + 1);   // omega_{j-1, .}
+    const double* al = S.alpha + (int64_t)k * nsteps;
+    const double* be = S.beta + (int64_t)k * nsteps;
+    const double bj = sqrt(s);
+    if (S.m_eff[k] < nsteps || !(bj > 0.0)) {   // stopped: nothing to keep orthogonal
+        S.flag[k] = 0;
+        return;
+    }
+    const double aj = al[j];
+    double tnorm = fabs(aj) + bj;
+    for (int i = 0; i < j; ++i) tnorm = fmax(tnorm, fabs(al[i]) + be[i]);
+    double worst = 0.0;
+    for (int i = 0; i < j; ++i) {
+        double t = be[i] * oc[i + 1] + (al[i] - aj) * oc[i] - be[j - 1] * op[i];
+        if (i > 0) t += be[i - 1] * oc[i - 1];
+        t += copysign(eps * (be[i] + bj), t);
+        on[i] = t / bj;
+        worst = fmax(worst, fabs(on[i]));
+    }
+    on[j] = eps * tnorm / bj;
+    on[j + 1] = 1.0;
+    worst = fmax(worst, fabs(on[j]));
+    const int f = (S.force[k] || worst > sqrt(eps)) ? 1 : 0;
+    S.flag[k] = f;
+    S.force[k] = f && !S.force[k];   // the vector after a reorthogonalised one is reorthogonalised too
+    if (f)
+        for (int i = 0; i <= j; ++i) on[i] = eps;
+}
+
+// Partial dot products W_i^T w (i = 0..j) of each flagged vector, 8 basis
+// vectors per sweep over the block's slice of w.  Products and per-thread sums
+// are in the basis precision T (a coefficient only needs a few correct digits:
+// it removes a component of size <= sqrt(eps)), the block sums in FP64.
+// dpart rows are [nvec][nsteps + 8][nblk]: a sweep's rows past j (zeros) stay
+// in the vector's padding.
+template <typename T>
+__global__ void k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ Wn, int nvec, int64_t p, int j,
+                              const int* __restrict__ flag, int nsteps, double* __restrict__ dpart) {
+    const int k = blockIdx.y;
+    if (!flag[k]) return;
+    const T* w = Wn + (int64_t)k * p;
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+        T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < p; x += (int64_t)gridDim.x * blockDim.x) {
+            const T wv = w[x];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if (i0 + a <= j) acc[a] += Q[((int64_t)(i0 + a) * nvec + k) * p + x] * wv;
+        }
+        double accd[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) accd[a] = (double)acc[a];
+        block_sum_store<8>(accd, dpart + ((int64_t)k * (nsteps + 8) + i0) * gridDim.x + blockIdx.x, gridDim.x);
+        __syncthreads();
+    }
+}
+
+// coef_i = s_i (q_i^T w) = s_i^2 (W_i^T w), summed over the partials in a fixed order.
+__global__ void k_reorth_coef(LanczosState S, const double* __restrict__ dpart, int nblk, int nsteps, int j) {
+    const int k = blockIdx.x;
+    if (!S.flag[k]) return;
+    for (int i = 0; i <= j; ++i) {
+        const double d = block_sum(dpart + ((int64_t)k * (nsteps + 8) + i) * nblk, nblk);
+        if (threadIdx.x == 0) {
+            const double si = S.s_hist[(int64_t)k * nsteps + i];
+            S.coef[(int64_t)k * nsteps + i] = si * si * d;
+        }
+        __syncthreads();
+    }
+}
+
+// w -= sum_i coef_i W_i (in the basis precision) for flagged vectors; partial
+// ||w||^2 replaces the update's so that beta_j is the norm after
+// reorthogonalisation.
+template <typename T>
+__global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int nvec, int64_t p, int j,
+                               LanczosState S, int nsteps, double* __restrict__ part) {
+    const int k = blockIdx.y;
+    if (!S.flag[k]) return;
+    __shared__ T c[KRY_MAX_STEPS];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) c[i] = (T)S.coef[(int64_t)k * nsteps + i];
+    __syncthreads();
+    T* w = Wn + (int64_t)k * p;
+    double acc[1] = {0.0};
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < p; x += (int64_t)gridDim.x * blockDim.x) {
+        T proj = 0;
+        for (int i = 0; i <= j; ++i) proj += c[i] * Q[((int64_t)i * nvec + k) * p + x];
+        const T r = w[x] - proj;
+        w[x] = r;
+        acc[0] += (double)r * (double)r;
+    }
+    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
 // Gauss quadrature of z^T log(K) z from the Lanczos tridiagonal: implicit QL
 // iterations with Wilkinson shifts (Bowdler, Martin, Reinsch & Wilkinson,
 // "The QR and QL algorithms for symmetric matrices", Numer. Math. 1968),
 // rotating only the first row of the eigenvector matrix (Golub & Welsch 1969).
-#define KRY_MAX_STEPS 256
 __global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, double znorm2, double* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprobe) return;
@@ -261,21 +395,34 @@ __global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, doubl
 // Lanczos over nvec vectors (vector v holds probe v mod nprobe; vpt consecutive
 // vectors share one covariance setting of a batched embedding, 0 = one
 // setting).  Step 0 runs directly (it sizes every buffer); steps 1.. are
-// captured into one CUDA graph and replayed as one launch.
+// captured into one CUDA graph and replayed as one launch.  Without
+// reorthogonalisation three basis vectors rotate through three buffers; with it
+// every basis vector is kept ([nsteps][nvec][p]) for the Gram-Schmidt passes.
 template <typename T>
 static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprobe, int nsteps, uint64_t seed,
-                           double* per_vec, int vpt) {
+                           double* per_vec, int vpt, bool reorth) {
     const bool dbl = sizeof(T) == 8;
     const int64_t p = ctx->p;
     const int nblkC = matvec_num_partials(ctx, e, dbl, nvec);
     const size_t vbytes = (size_t)nvec * p * sizeof(T);
-    for (int b = 0; b < 4; ++b) ctx->work[b].ensure(vbytes);
+    ctx->work[0].ensure(vbytes);
     T* U = ctx->work[0].as<T>();
-    T* W[3] = {ctx->work[1].as<T>(), ctx->work[2].as<T>(), ctx->work[3].as<T>()};
+    T* Q = nullptr;   // basis store with reorthogonalisation
+    T* W[3] = {nullptr, nullptr, nullptr};
+    if (reorth) {
+        ctx->work[1].ensure(vbytes * nsteps);
+        Q = ctx->work[1].as<T>();
+    } else {
+        for (int b = 1; b < 4; ++b) ctx->work[b].ensure(vbytes);
+        for (int b = 0; b < 3; ++b) W[b] = ctx->work[b + 1].as<T>();
+    }
+    auto basis = [&](int i) -> T* { return reorth ? Q + (size_t)i * nvec * p : W[i % 3]; };
     const int nred = std::max(nblkC, RED_BLOCKS);
     ctx->work[4].ensure((size_t)nvec * nred * sizeof(double));
     double* part = ctx->work[4].as<double>();
-    ctx->scal.ensure((size_t)nvec * (2 * nsteps + 4) * sizeof(double) + nvec * sizeof(double));
+    const size_t nsc = (size_t)nvec * (2 * nsteps + 4) + nvec;
+    const size_t npro = reorth ? (size_t)nvec * (2 * nsteps + 3 * (nsteps + 1)) : 0;
+    ctx->scal.ensure((nsc + npro) * sizeof(double));
     double* sc = ctx->scal.as<double>();
     LanczosState S;
     S.s_cur = sc;
@@ -283,31 +430,52 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     S.alpha = sc + 2 * nvec;
     S.beta = S.alpha + (size_t)nvec * nsteps;
     double* res = S.beta + (size_t)nvec * nsteps;
-    ctx->work[5].ensure((size_t)nvec * sizeof(int));
+    ctx->work[5].ensure((size_t)nvec * 3 * sizeof(int));
     S.m_eff = ctx->work[5].as<int>();
+    S.s_hist = S.omega = S.coef = nullptr;
+    S.flag = S.force = nullptr;
+    double* dpart = nullptr;
+    if (reorth) {
+        S.s_hist = sc + nsc;
+        S.coef = S.s_hist + (size_t)nvec * nsteps;
+        S.omega = S.coef + (size_t)nvec * nsteps;
+        S.flag = S.m_eff + nvec;
+        S.force = S.flag + nvec;
+        ctx->work[6].ensure((size_t)nvec * (nsteps + 8) * RED_BLOCKS * sizeof(double));
+        dpart = ctx->work[6].as<double>();
+    }
+    const double eps = dbl ? 1.1102230246251565e-16 : 5.9604644775390625e-08;   // unit roundoff of T
 
     const int tb = 256;
     k_lanczos_init<<<(nvec + tb - 1) / tb, tb, 0, ctx->stream>>>(S, nvec, nsteps, 1.0 / sqrt((double)p));
     KRY_CHECK_LAUNCH();
     dim3 gp((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nvec);
-    k_probes<T><<<gp, 256, 0, ctx->stream>>>(W[0], p, nprobe, seed);
+    k_probes<T><<<gp, 256, 0, ctx->stream>>>(basis(0), p, nprobe, seed);
     KRY_CHECK_LAUNCH();
-    int ip = 2, ic = 0, in = 1;   // W indices: previous, current, next
     auto step = [&](int j) {
         cudaStream_t st = ctx->stream;
-        matvec_ex<T>(ctx, e, W[ic], p, S.s_cur, U, p, nvec, part, nblkC, vpt);
+        T* Wc = basis(j);
+        T* Wp = basis(j > 0 ? j - 1 : 0);
+        matvec_ex<T>(ctx, e, Wc, p, S.s_cur, U, p, nvec, part, nblkC, vpt);
         k_lanczos_alpha<<<nvec, FIN_THREADS, 0, st>>>(S, part, nblkC, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
         if (j == nsteps - 1) return;
+        T* Wn = basis(j + 1);
         dim3 gu(RED_BLOCKS, nvec);
-        k_lanczos_update<T><<<gu, 256, 0, st>>>(U, W[ic], W[ip], W[in], p, S, nsteps, j, part);
+        k_lanczos_update<T><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
+        if (reorth) {
+            k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps);
+            KRY_CHECK_LAUNCH();
+            k_reorth_dots<T><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+            KRY_CHECK_LAUNCH();
+            k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j);
+            KRY_CHECK_LAUNCH();
+            k_reorth_apply<T><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+            KRY_CHECK_LAUNCH();
+        }
         k_lanczos_beta<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
-        const int t = ip;
-        ip = ic;
-        ic = in;
-        in = t;
     };
     step(0);
     if (nsteps > 1)
@@ -320,25 +488,28 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
-void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_probe) {
+void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth,
+            double* per_probe) {
     KRY_REQUIRE(nsteps >= 1 && nsteps <= KRY_MAX_STEPS, KRY_EINVAL, "nsteps must be in [1, 256]");
     KRY_REQUIRE(nprobe >= 1, KRY_EINVAL, "nprobe must be >= 1");
     if (e->prec == KRY_F64)
-        lanczos_logdet<double>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0);
+        lanczos_logdet<double>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0, reorth);
     else
-        lanczos_logdet<float>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0);
+        lanczos_logdet<float>(ctx, e, nprobe, nprobe, nsteps, seed, per_probe, 0, reorth);
 }
 
 // Batched form: ntheta settings of a batched embedding x nprobe probes each
 // (nprobe even), per_vec[ntheta * nprobe].
-void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, double* per_vec) {
+void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth,
+                    double* per_vec) {
     KRY_REQUIRE(nsteps >= 1 && nsteps <= KRY_MAX_STEPS, KRY_EINVAL, "nsteps must be in [1, 256]");
     KRY_REQUIRE(nprobe >= 2 && nprobe % 2 == 0, KRY_EINVAL, "batched log-det needs an even probe count");
     const int nvec = e->ntheta * nprobe;
+    const int vpt = e->ntheta > 1 ? nprobe : 0;
     if (e->prec == KRY_F64)
-        lanczos_logdet<double>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, e->ntheta > 1 ? nprobe : 0);
+        lanczos_logdet<double>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, vpt, reorth);
     else
-        lanczos_logdet<float>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, e->ntheta > 1 ? nprobe : 0);
+        lanczos_logdet<float>(ctx, e, nvec, nprobe, nsteps, seed, per_vec, vpt, reorth);
 }
 
 // ------------------------------------------------------------------ CG

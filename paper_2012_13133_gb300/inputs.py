@@ -51,6 +51,7 @@ class Workload:
     nsteps: int = 50
     probe_seed: int = 0
     cg_tol: float = 1e-8
+    reorth: int = 0              # Lanczos basis: 0 plain recurrence, 1 partial reorthogonalisation
     extra: dict = field(default_factory=dict)
 
 
@@ -60,17 +61,17 @@ WORKLOADS = {
                        nprobe=20, nsteps=50, probe_seed=0, cg_tol=1e-8,
                        extra={"n_sites": 100, "site_seed": 1}),
     "grid1024": Workload("grid1024", 1024, 1024, Cov(1.0, 0.05, 1.5, 0.05), "uniform", 0.5, 2, 20,
-                         nprobe=64, nsteps=60, probe_seed=2, cg_tol=1e-6),
+                         nprobe=64, nsteps=60, probe_seed=2, cg_tol=1e-6, reorth=1),
     "search512": Workload("search512", 512, 512, Cov(1.0, 0.08, 1.0, 0.1), "uniform", 0.3, 3, 30,
-                          nprobe=32, nsteps=50, probe_seed=3, cg_tol=1e-6,
+                          nprobe=32, nsteps=50, probe_seed=3, cg_tol=1e-6, reorth=1,
                           extra={"ranges": [0.02 * (k + 1) for k in range(8)],
                                  "nus": [0.5, 1.0, 1.5, 2.5]}),
     "serve": Workload("serve", 0, 0, Cov(), "mixed", 0.0, 4, 40,
-                      nprobe=16, nsteps=50, probe_seed=4, cg_tol=1e-6,
+                      nprobe=16, nsteps=50, probe_seed=4, cg_tol=1e-6, reorth=1,
                       extra={"n_requests": 2000, "side_min": 128, "side_max": 2048}),
     "large4096": Workload("large4096", 4096, 4096,
                           Cov(1.0, 0.05, 0.5, 0.05, angle=math.radians(30.0), ratio=3.0),
-                          "circles", 0.3, 5, 50, nprobe=32, nsteps=80, probe_seed=5, cg_tol=1e-6,
+                          "circles", 0.3, 5, 50, nprobe=32, nsteps=80, probe_seed=5, cg_tol=1e-6, reorth=1,
                           extra={"n_var_cells": 10000, "var_seed": 6}),
 }
 

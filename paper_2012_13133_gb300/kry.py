@@ -40,7 +40,7 @@ class kry_cov(C.Structure):
 
 class kry_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("nprobe", C.c_int32), ("nsteps", C.c_int32), ("seed", C.c_uint64),
-                ("rtol", C.c_double), ("maxit", C.c_int32)]
+                ("rtol", C.c_double), ("maxit", C.c_int32), ("reorth", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -65,7 +65,7 @@ SIGNATURES = {
     "kry_embed_free": (None, [_P]),
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
     "kry_matvec_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
-    "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, _DP, _DP, _DP]),
+    "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, _DP, _DP, _DP]),
     "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32,
                             C.POINTER(C.c_int32), _DP]),
     "kry_profile_loglik": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(kry_cov), C.c_int32, C.POINTER(kry_opts),
@@ -116,8 +116,12 @@ def launch_count() -> int:
 
 
 def _ptr(t):
+    """Device pointer of a tensor the library reads as a dense array.  The
+    library takes plain pointers, so strided views must never reach it."""
     if t is None:
         return None
+    if not t.is_contiguous():
+        raise ValueError("tensor passed to libkry must be contiguous (call .contiguous())")
     return C.c_void_p(t.data_ptr())
 
 
@@ -141,9 +145,10 @@ class Opts:
     seed: int = 0
     rtol: float = 1e-6
     maxit: int = 5000
+    reorth: int = 0   # 1: partial reorthogonalisation of the Lanczos basis
 
     def c(self) -> kry_opts:
-        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit)
+        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.reorth)
 
 
 class Embed:
@@ -222,26 +227,26 @@ class Context:
     def matvec(self, emb: Embed, v, out=None):
         """v: (nvec, p) or (p,) CUDA tensor (float32 for KRY_F32, float64 for KRY_F64)."""
         squeeze = v.dim() == 1
-        V = v.reshape(1, -1) if squeeze else v
-        assert V.is_contiguous() and V.shape[1] == self.p
+        V = (v.reshape(1, -1) if squeeze else v).contiguous()
+        assert V.shape[1] == self.p
         if out is None:
-            out = self.torch.empty_like(V)
+            out = self.torch.empty(V.shape, dtype=V.dtype, device=V.device)
         self._check(_lib.kry_matvec(self.h, emb.handle, _ptr(V), _ptr(out), V.shape[0], self.p))
         return out.reshape(-1) if squeeze else out
 
-    def logdet(self, emb: Embed, nprobe: int, nsteps: int, seed: int):
+    def logdet(self, emb: Embed, nprobe: int, nsteps: int, seed: int, reorth: int = 0):
         ld, se = C.c_double(), C.c_double()
         per = np.zeros(nprobe)
-        self._check(_lib.kry_logdet(self.h, emb.handle, nprobe, nsteps, C.c_uint64(seed), C.byref(ld), C.byref(se),
-                                    _np_dp(per)))
+        self._check(_lib.kry_logdet(self.h, emb.handle, nprobe, nsteps, C.c_uint64(seed), reorth, C.byref(ld),
+                                    C.byref(se), _np_dp(per)))
         return ld.value, se.value, per
 
     def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, X=None):
         """B: (nrhs, p) float64 CUDA tensor.  Returns (X, iters, relres, status)."""
         squeeze = B.dim() == 1
-        Bm = B.reshape(1, -1) if squeeze else B
+        Bm = (B.reshape(1, -1) if squeeze else B).contiguous()
         if X is None:
-            X = self.torch.empty_like(Bm)
+            X = self.torch.empty(Bm.shape, dtype=Bm.dtype, device=Bm.device)
         it, rr = C.c_int32(), C.c_double()
         st = self._check(_lib.kry_solve(self.h, emb.handle, _ptr(Bm), _ptr(X), Bm.shape[0], self.p, rtol, maxit,
                                         C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
@@ -249,6 +254,7 @@ class Context:
 
     def profile_loglik(self, y, X, thetas, opts: Opts):
         """y: (p,) float64 CUDA; X: (ncov, p) float64 CUDA (column-major p x ncov)."""
+        y, X = y.contiguous(), X.contiguous()
         ncov = X.shape[0]
         n = len(thetas)
         arr = (kry_cov * n)(*[make_cov(t) for t in thetas])
@@ -261,6 +267,8 @@ class Context:
     def krige(self, cov, opts: Opts, y, X, cells=None, Xc=None, sites=None, Xs=None, variances=False):
         """cells: (ncell,) int64 CUDA; Xc: (ncov, ncell) float64; sites: (nsite, 2) float64; Xs: (ncov, nsite)."""
         torch = self.torch
+        y, X = y.contiguous(), X.contiguous()
+        cells, Xc, sites, Xs = (None if t is None else t.contiguous() for t in (cells, Xc, sites, Xs))
         ncov = X.shape[0]
         ncell = 0 if cells is None else cells.shape[0]
         nsite = 0 if sites is None else sites.shape[0]
@@ -299,6 +307,8 @@ class Context:
                      mean_cells=None):
         """Profile log-likelihood and kriging means for one covariance setting (one shared solve)."""
         torch = self.torch
+        y, X = y.contiguous(), X.contiguous()
+        cells, Xc, sites, Xs = (None if t is None else t.contiguous() for t in (cells, Xc, sites, Xs))
         ncov = X.shape[0]
         ncell = 0 if cells is None else cells.shape[0]
         nsite = 0 if sites is None else sites.shape[0]

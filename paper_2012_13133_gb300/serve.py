@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 from paper_2012_13133_gb300 import inputs as I  # noqa: E402
 
 
-def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000):
+def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000, reorth=1):
     """Materialise request specs (inputs.serve_requests) into host arrays,
     drawing each data set with the GPU sampler."""
     import torch
@@ -53,7 +53,7 @@ def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000)
         req = dict(spec=sp, kind=kry.KRY_REQ_LOGLIK if sp["kind"] == "loglik" else kry.KRY_REQ_KRIGE,
                    mask=mask, y=y, X=np.ascontiguousarray(X.T), cov=cov,
                    opts=kry.Opts(prec=kry.KRY_F32, nprobe=nprobe, nsteps=nsteps, seed=sp["id"], rtol=rtol,
-                                 maxit=maxit))
+                                 maxit=maxit, reorth=reorth))
         if sp["kind"] == "krige":
             cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
             req["target_cells"] = cells

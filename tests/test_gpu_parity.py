@@ -254,6 +254,42 @@ def test_logdet_fp32_same_probes(ctx, n1, n2, cov, frac):
     assert np.allclose(per, per_o, rtol=1e-3)
 
 
+REORTH_CASE = (128, 128, I.Cov(1.0, 0.1, 1.5, 0.01), 0.3, 80)   # plain FP64 recurrence off by ~6e-3 here
+
+
+@pytest.fixture(scope="module")
+def reorth_oracle():
+    n1, n2, cov, frac, m = REORTH_CASE
+    mask = I.mask_uniform(n1, n2, frac, 3)
+    P = O.FFTProblem(n1, n2, mask, cov)
+    return mask, P.logdet(6, m, 7, reorth=True)[2]
+
+
+def test_logdet_partial_reorth_fp64_follows_exact_lanczos(ctx, reorth_oracle):
+    """Partial reorthogonalisation in FP64 keeps the basis semi-orthogonal, so
+    each probe's quadrature is the exact-arithmetic Gauss rule (oracle: full
+    reorthogonalisation) to far below the tolerance, on a case where the plain
+    recurrence is off by ~6e-3."""
+    n1, n2, cov, frac, m = REORTH_CASE
+    mask, per_o = reorth_oracle
+    set_mask(ctx, mask)
+    emb = ctx.embed(cov, kry.KRY_F64)
+    _, _, per = ctx.logdet(emb, 6, m, 7, reorth=1)
+    assert np.allclose(per, per_o, rtol=1e-8, atol=0), np.max(np.abs(per / per_o - 1))
+    emb.free()
+
+
+def test_logdet_partial_reorth_fp32_within_tolerance(ctx, reorth_oracle):
+    n1, n2, cov, frac, m = REORTH_CASE
+    mask, per_o = reorth_oracle
+    set_mask(ctx, mask)
+    emb = ctx.embed(cov, kry.KRY_F32)
+    ld, _, per = ctx.logdet(emb, 6, m, 7, reorth=1)
+    assert np.allclose(per, per_o, rtol=1e-3, atol=0), np.max(np.abs(per / per_o - 1))
+    assert abs(ld - np.mean(per_o)) <= 1e-3 * abs(np.mean(per_o))
+    emb.free()
+
+
 def test_logdet_nugget_only_is_exact(ctx):
     n1, n2 = 20, 20
     mask = I.mask_uniform(n1, n2, 0.5, 1)
@@ -313,10 +349,11 @@ def test_profile_loglik_batch_of_thetas_fp32(ctx):
         assert res["logdet"][t] == pytest.approx(ref["logdet"], rel=1e-3), th
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_batched_thetas_equal_individual_calls(ctx, prec):
+@pytest.mark.parametrize("prec,reorth", [("f32", 0), ("f64", 0), ("f32", 1)])
+def test_batched_thetas_equal_individual_calls(ctx, prec, reorth):
     """The batched search (all settings in shared launches) gives each setting the
-    same log-likelihood as a call for that setting alone."""
+    same log-likelihood as a call for that setting alone (reorthogonalisation
+    decisions are per vector, so they do not depend on the batch either)."""
     n1, n2 = 96, 80
     mask = I.mask_uniform(n1, n2, 0.3, 5)
     p = set_mask(ctx, mask)
@@ -327,7 +364,7 @@ def test_batched_thetas_equal_individual_calls(ctx, prec):
     yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
     thetas = [I.Cov(1.0, r, nu, 0.1 if nu != 2.5 else 0.05) for r in (0.04, 0.1) for nu in (0.5, 1.0, 2.5)]
     opts = kry.Opts(prec=kry.KRY_F32 if prec == "f32" else kry.KRY_F64, nprobe=8, nsteps=30, seed=7, rtol=1e-8,
-                    maxit=4000)
+                    maxit=4000, reorth=reorth)
     batch = ctx.profile_loglik(yt, Xt, thetas, opts)
     assert batch["status"] == kry.KRY_OK
     for t, th in enumerate(thetas):
