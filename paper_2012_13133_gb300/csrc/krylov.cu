@@ -11,6 +11,7 @@
 // accumulated in FP64 per block and reduced in a fixed order by one small
 // kernel, so results do not depend on scheduling.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -266,25 +267,58 @@ __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int
         for (int i = 0; i <= j; ++i) on[i] = eps;
 }
 
+// VW consecutive elements of type T through one 16-byte access (VW = 16 /
+// sizeof(T)), or one element (VW = 1).  The caller guarantees alignment.
+template <typename T, int VW>
+__device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&out)[VW]) {
+    if constexpr (VW * sizeof(T) == 16) {
+        const int4 q = *reinterpret_cast<const int4*>(src);
+        memcpy(out, &q, 16);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) out[e] = src[e];
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void store_vec(T* __restrict__ dst, const T (&in)[VW]) {
+    if constexpr (VW * sizeof(T) == 16) {
+        int4 q;
+        memcpy(&q, in, 16);
+        *reinterpret_cast<int4*>(dst) = q;
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) dst[e] = in[e];
+    }
+}
+
 // Partial dot products W_i^T w (i = 0..j) of each flagged vector, 8 basis
-// vectors per sweep over the block's slice of w.  Products and per-thread sums
-// are in the basis precision T (a coefficient only needs a few correct digits:
-// it removes a component of size <= sqrt(eps)), the block sums in FP64.
-// dpart rows are [nvec][nsteps + 8][nblk]: a sweep's rows past j (zeros) stay
-// in the vector's padding.
-template <typename T>
+// vectors per sweep over the block's slice of w, VW elements per access.
+// Products and per-thread sums are in the basis precision T (a coefficient only
+// needs a few correct digits: it removes a component of size <= sqrt(eps)), the
+// block sums in FP64.  dpart rows are [nvec][nsteps + 8][nblk]: a sweep's rows
+// past j (zeros) stay in the vector's padding.
+template <typename T, int VW>
 __global__ void k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ Wn, int nvec, int64_t p, int j,
                               const int* __restrict__ flag, int nsteps, double* __restrict__ dpart) {
     const int k = blockIdx.y;
     if (!flag[k]) return;
     const T* w = Wn + (int64_t)k * p;
+    const int64_t nv = p / VW;
     for (int i0 = 0; i0 <= j; i0 += 8) {
         T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < p; x += (int64_t)gridDim.x * blockDim.x) {
-            const T wv = w[x];
+        for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv;
+             xv += (int64_t)gridDim.x * blockDim.x) {
+            T wv[VW];
+            load_vec<T, VW>(w + xv * VW, wv);
 #pragma unroll
             for (int a = 0; a < 8; ++a)
-                if (i0 + a <= j) acc[a] += Q[((int64_t)(i0 + a) * nvec + k) * p + x] * wv;
+                if (i0 + a <= j) {
+                    T qv[VW];
+                    load_vec<T, VW>(Q + ((int64_t)(i0 + a) * nvec + k) * p + xv * VW, qv);
+#pragma unroll
+                    for (int e = 0; e < VW; ++e) acc[a] += qv[e] * wv[e];
+                }
         }
         double accd[8];
 #pragma unroll
@@ -308,10 +342,10 @@ __global__ void k_reorth_coef(LanczosState S, const double* __restrict__ dpart, 
     }
 }
 
-// w -= sum_i coef_i W_i (in the basis precision) for flagged vectors; partial
-// ||w||^2 replaces the update's so that beta_j is the norm after
-// reorthogonalisation.
-template <typename T>
+// w -= sum_i coef_i W_i (in the basis precision) for flagged vectors, VW
+// elements per access; partial ||w||^2 replaces the update's so that beta_j is
+// the norm after reorthogonalisation.
+template <typename T, int VW>
 __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int nvec, int64_t p, int j,
                                LanczosState S, int nsteps, double* __restrict__ part) {
     const int k = blockIdx.y;
@@ -320,13 +354,27 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
     for (int i = threadIdx.x; i <= j; i += blockDim.x) c[i] = (T)S.coef[(int64_t)k * nsteps + i];
     __syncthreads();
     T* w = Wn + (int64_t)k * p;
+    const int64_t nv = p / VW;
     double acc[1] = {0.0};
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < p; x += (int64_t)gridDim.x * blockDim.x) {
-        T proj = 0;
-        for (int i = 0; i <= j; ++i) proj += c[i] * Q[((int64_t)i * nvec + k) * p + x];
-        const T r = w[x] - proj;
-        w[x] = r;
-        acc[0] += (double)r * (double)r;
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        T proj[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) proj[e] = 0;
+#pragma unroll 4
+        for (int i = 0; i <= j; ++i) {
+            T qv[VW];
+            load_vec<T, VW>(Q + ((int64_t)i * nvec + k) * p + xv * VW, qv);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) proj[e] += c[i] * qv[e];
+        }
+        T r[VW];
+        load_vec<T, VW>(w + xv * VW, r);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            r[e] -= proj[e];
+            acc[0] += (double)r[e] * (double)r[e];
+        }
+        store_vec<T, VW>(w + xv * VW, r);
     }
     block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
@@ -467,11 +515,18 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
         if (reorth) {
             k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps);
             KRY_CHECK_LAUNCH();
-            k_reorth_dots<T><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+            constexpr int VW = 16 / sizeof(T);   // 16-byte accesses when every vector start is 16-byte aligned
+            if (p % VW == 0)
+                k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+            else
+                k_reorth_dots<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
             KRY_CHECK_LAUNCH();
             k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j);
             KRY_CHECK_LAUNCH();
-            k_reorth_apply<T><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+            if (p % VW == 0)
+                k_reorth_apply<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+            else
+                k_reorth_apply<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
             KRY_CHECK_LAUNCH();
         }
         k_lanczos_beta<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
