@@ -56,6 +56,11 @@ static void prof_clear(kry_ctx* ctx) {
     ctx->prof_ev.clear();
     ctx->prof_nvec.clear();
     ctx->prof_dbl.clear();
+    for (int d = 0; d < 2; ++d) {
+        ctx->prof_ms_acc[d] = 0.0;
+        ctx->prof_calls_acc[d] = 0;
+        ctx->prof_vec_acc[d] = 0;
+    }
 }
 
 void DevBuf::ensure(size_t bytes) {
@@ -712,9 +717,10 @@ kry_status kry_profile_read(kry_ctx* ctx, int32_t prec, int64_t* calls, int64_t*
             ++c;
             v += ctx->prof_nvec[i];
         }
-        *calls = c;
-        *vectors = v;
-        *total_ms = ms;
+        const int d = prec == KRY_F64 ? 1 : 0;
+        *calls = c + ctx->prof_calls_acc[d];
+        *vectors = v + ctx->prof_vec_acc[d];
+        *total_ms = ms + ctx->prof_ms_acc[d];
         return KRY_OK;
     });
 }

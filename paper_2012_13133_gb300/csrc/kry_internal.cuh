@@ -128,6 +128,9 @@ struct kry_ctx {
     std::vector<cudaEvent_t> prof_ev;     // start/stop pairs
     std::vector<int> prof_nvec;
     std::vector<int> prof_dbl;
+    double prof_ms_acc[2] = {0.0, 0.0};   // [FP32, FP64] matvec time harvested from replayed graphs
+    int64_t prof_calls_acc[2] = {0, 0};
+    int64_t prof_vec_acc[2] = {0, 0};
 };
 
 struct kry_embed {

@@ -93,6 +93,73 @@ static void run_captured(kry_ctx* ctx, F&& fn) {
     KRY_CUDA(cudaEventDestroy(join));
 }
 
+// A launch sequence captured once into a CUDA graph (on the library's capture
+// stream) and replayed on ctx->stream as often as needed.  Replays add the
+// captured kernel count to the launch counter.  With profiling on, the matvec
+// event pairs recorded during capture are re-recorded by every replay; the
+// caller synchronises the stream after a replay and calls harvest(), which adds
+// their times to the context's totals.
+struct Replay {
+    kry_ctx* ctx = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+    std::vector<cudaEvent_t> ev;   // start/stop pairs owned by the graph's profiling nodes
+    std::vector<int> nvec, dbl;
+    explicit Replay(kry_ctx* c) : ctx(c) {}
+    Replay(const Replay&) = delete;
+    Replay& operator=(const Replay&) = delete;
+    ~Replay() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    template <class F>
+    void capture(F&& fn) {
+        if (!ctx->cap_stream) KRY_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = ctx->stream, cap = ctx->cap_stream;
+        const unsigned long long n0 = g_kry_launches.load();
+        const size_t p0 = ctx->prof_nvec.size();
+        cudaGraph_t graph = nullptr;
+        ctx->stream = cap;
+        KRY_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+        try {
+            fn();
+        } catch (...) {
+            cudaStreamEndCapture(cap, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            ctx->stream = user;
+            throw;
+        }
+        ctx->stream = user;
+        // the profiling pairs recorded by the capture belong to the graph from now on
+        ev.assign(ctx->prof_ev.begin() + 2 * p0, ctx->prof_ev.end());
+        nvec.assign(ctx->prof_nvec.begin() + p0, ctx->prof_nvec.end());
+        dbl.assign(ctx->prof_dbl.begin() + p0, ctx->prof_dbl.end());
+        ctx->prof_ev.resize(2 * p0);
+        ctx->prof_nvec.resize(p0);
+        ctx->prof_dbl.resize(p0);
+        KRY_CUDA(cudaStreamEndCapture(cap, &graph));
+        const cudaError_t err = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        KRY_CUDA(err);
+        kernels = g_kry_launches.load() - n0;
+        g_kry_launches.fetch_sub(kernels);   // counted when replayed
+    }
+    void launch() {
+        KRY_CUDA(cudaGraphLaunch(exec, ctx->stream));
+        g_kry_launches.fetch_add(kernels);
+    }
+    // After the stream has been synchronised following launch().
+    void harvest() {
+        for (size_t i = 0; i < nvec.size(); ++i) {
+            float t = 0.f;
+            KRY_CUDA(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+            ctx->prof_ms_acc[dbl[i]] += t;
+            ctx->prof_calls_acc[dbl[i]] += 1;
+            ctx->prof_vec_acc[dbl[i]] += nvec[i];
+        }
+    }
+};
+
 // ------------------------------------------------------------------ block reduction helper
 
 template <int N>
@@ -135,6 +202,31 @@ __device__ __forceinline__ double block_sum(const double* __restrict__ part, int
 
 static const int FIN_THREADS = 256;   // block size of the per-vector finalisers
 
+// VW consecutive elements of type T through one 16-byte access (VW = 16 /
+// sizeof(T)), or one element (VW = 1).  The caller guarantees alignment.
+template <typename T, int VW>
+__device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&out)[VW]) {
+    if constexpr (VW * sizeof(T) == 16) {
+        const int4 q = *reinterpret_cast<const int4*>(src);
+        memcpy(out, &q, 16);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) out[e] = src[e];
+    }
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ void store_vec(T* __restrict__ dst, const T (&in)[VW]) {
+    if constexpr (VW * sizeof(T) == 16) {
+        int4 q;
+        memcpy(&q, in, 16);
+        *reinterpret_cast<int4*>(dst) = q;
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) dst[e] = in[e];
+    }
+}
+
 // ------------------------------------------------------------------ Lanczos
 
 #define KRY_MAX_STEPS 256
@@ -176,7 +268,8 @@ __global__ void k_lanczos_alpha(LanczosState S, const double* __restrict__ part,
 }
 
 // w_next = U - alpha_j s_cur W_cur - beta_{j-1} s_prev W_prev;  partial ||w_next||^2.
-template <typename T>
+// VW elements per access when every vector start is 16-byte aligned.
+template <typename T, int VW>
 __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ Wc, const T* __restrict__ Wp,
                                  T* __restrict__ Wn, int64_t p, LanczosState S, int nsteps, int j,
                                  double* __restrict__ part) {
@@ -185,13 +278,25 @@ __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ 
     const T ca = (T)(a * S.s_cur[k]);
     const T cb = (T)((j > 0 ? S.beta[(int64_t)k * nsteps + j - 1] : 0.0) * S.s_prev[k]);
     const int64_t off = (int64_t)k * p;
+    const int64_t nv = p / VW;
     double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        T u[VW], wc[VW], wp[VW];
+        load_vec<T, VW>(U + off + xv * VW, u);
+        load_vec<T, VW>(Wc + off + xv * VW, wc);
         // at j = 0 there is no previous vector (its buffer is not initialised)
-        const T wp = (j > 0) ? Wp[off + i] : (T)0;
-        const T w = U[off + i] - ca * Wc[off + i] - cb * wp;
-        Wn[off + i] = w;
-        acc[0] += (double)w * (double)w;
+        if (j > 0) {
+            load_vec<T, VW>(Wp + off + xv * VW, wp);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) wp[e] = (T)0;
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            u[e] = u[e] - ca * wc[e] - cb * wp[e];
+            acc[0] += (double)u[e] * (double)u[e];
+        }
+        store_vec<T, VW>(Wn + off + xv * VW, u);
     }
     block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
@@ -265,31 +370,6 @@ __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int
     S.force[k] = f && !S.force[k];   // the vector after a reorthogonalised one is reorthogonalised too
     if (f)
         for (int i = 0; i <= j; ++i) on[i] = eps;
-}
-
-// VW consecutive elements of type T through one 16-byte access (VW = 16 /
-// sizeof(T)), or one element (VW = 1).  The caller guarantees alignment.
-template <typename T, int VW>
-__device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&out)[VW]) {
-    if constexpr (VW * sizeof(T) == 16) {
-        const int4 q = *reinterpret_cast<const int4*>(src);
-        memcpy(out, &q, 16);
-    } else {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) out[e] = src[e];
-    }
-}
-
-template <typename T, int VW>
-__device__ __forceinline__ void store_vec(T* __restrict__ dst, const T (&in)[VW]) {
-    if constexpr (VW * sizeof(T) == 16) {
-        int4 q;
-        memcpy(&q, in, 16);
-        *reinterpret_cast<int4*>(dst) = q;
-    } else {
-#pragma unroll
-        for (int e = 0; e < VW; ++e) dst[e] = in[e];
-    }
 }
 
 // Partial dot products W_i^T w (i = 0..j) of each flagged vector, 8 basis
@@ -510,12 +590,15 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
         if (j == nsteps - 1) return;
         T* Wn = basis(j + 1);
         dim3 gu(RED_BLOCKS, nvec);
-        k_lanczos_update<T><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
+        constexpr int VW = 16 / sizeof(T);   // 16-byte accesses when every vector start is 16-byte aligned
+        if (p % VW == 0)
+            k_lanczos_update<T, VW><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
+        else
+            k_lanczos_update<T, 1><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
         if (reorth) {
             k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps);
             KRY_CHECK_LAUNCH();
-            constexpr int VW = 16 / sizeof(T);   // 16-byte accesses when every vector start is 16-byte aligned
             if (p % VW == 0)
                 k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
             else
@@ -800,15 +883,18 @@ static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int
 // true FP64 residual.
 
 struct RcgState {
-    double* rr;       // [nrhs] current r^T r
+    double* rr[2];    // [nrhs] r^T r, double-buffered: iteration it reads rr[it & 1], writes rr[(it + 1) & 1]
     double* rr_ref;   // [nrhs] r^T r at the last replacement
     double* thr2;     // [nrhs] (rtol ||b||)^2
-    double* alpha;    // [nrhs]
-    double* beta;     // [nrhs]
     int* done;        // [nrhs]
     int* iters;       // [nrhs]
     int* nwant;       // [1] columns asking for a replacement (or done)
 };
+
+static const int CG_BLOCKS = 304;   // blocks per right-hand side of the CG vector kernels (2 per SM)
+
+// r^T r buffer of parity par (a select, not an indexed load from the parameter struct)
+__device__ __forceinline__ double* rr_buf(const RcgState& S, int par) { return par ? S.rr[1] : S.rr[0]; }
 
 // X = 0 (FP64), R = (float) B, P = R; partials of ||B||^2 (exact) per column.
 __global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, double* __restrict__ X, int64_t ldx,
@@ -832,81 +918,131 @@ __global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part, 
     if (k < nrhs) {
         double s = 0.0;
         for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
-        S.rr[k] = s;
+        S.rr[0][k] = s;
         S.rr_ref[k] = s;
         S.thr2[k] = tol[k] * tol[k] * s;
         S.done[k] = (s == 0.0) ? 1 : 0;
         S.iters[k] = 0;
-        S.alpha[k] = 0.0;
-        S.beta[k] = 0.0;
     }
     if (k == 0) *S.nwant = 0;
 }
 
-__global__ void k_rcg_alpha(RcgState S, const double* __restrict__ part, int nblk, int nrhs) {
-    const int k = blockIdx.x;   // one block per right-hand side
-    const double pq = block_sum(part + (int64_t)k * nblk, nblk);
-    if (threadIdx.x == 0) S.alpha[k] = (S.done[k] || !(pq > 0.0)) ? 0.0 : S.rr[k] / pq;
-    if (k == 0 && threadIdx.x == 0) *S.nwant = 0;
+// alpha = r^T r / p^T K p from the matvec's partials; every block of the
+// column sums them in the same fixed order, so all blocks agree.
+__device__ __forceinline__ double rcg_alpha(const RcgState& S, const double* __restrict__ part_pq, int nblkC, int k,
+                                            int par) {
+    __shared__ double a_sh;
+    const double pq = block_sum(part_pq + (int64_t)k * nblkC, nblkC);
+    if (threadIdx.x == 0) a_sh = (S.done[k] || !(pq > 0.0)) ? 0.0 : rr_buf(S, par)[k] / pq;
+    __syncthreads();
+    return a_sh;
 }
 
-// X += alpha P (FP64), R -= alpha Q (FP32); partial ||R||^2.
+// X += alpha P (FP64), R -= alpha Q (FP32); partial ||R||^2.  VW elements per
+// access (16-byte loads of R, P, Q; two of X) when the caller has checked alignment.
+template <int VW>
 __global__ void k_rcg_update(double* __restrict__ X, int64_t ldx, float* __restrict__ R, const float* __restrict__ P,
-                             const float* __restrict__ Q, int64_t p, RcgState S, double* __restrict__ part) {
+                             const float* __restrict__ Q, int64_t p, RcgState S, const double* __restrict__ part_pq,
+                             int nblkC, double* __restrict__ part_rr, int par) {
     const int k = blockIdx.y;
-    const double a = S.alpha[k];
+    const double a = rcg_alpha(S, part_pq, nblkC, k, par);
+    if (k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *S.nwant = 0;
     const float af = (float)a;
     const bool act = !S.done[k];
+    float* Rk = R + (int64_t)k * p;
+    const float* Pk = P + (int64_t)k * p;
+    const float* Qk = Q + (int64_t)k * p;
+    double* Xk = X + (int64_t)k * ldx;
+    const int64_t nv = p / VW;
     double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
-        float r = R[(int64_t)k * p + i];
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        float r[VW];
+        load_vec<float, VW>(Rk + xv * VW, r);
         if (act) {
-            X[(int64_t)k * ldx + i] += a * (double)P[(int64_t)k * p + i];
-            r -= af * Q[(int64_t)k * p + i];
-            R[(int64_t)k * p + i] = r;
+            float pv[VW], qv[VW];
+            double xx[VW];
+            load_vec<float, VW>(Pk + xv * VW, pv);
+            load_vec<float, VW>(Qk + xv * VW, qv);
+            if constexpr (VW == 4) {
+                double x0[2], x1[2];
+                load_vec<double, 2>(Xk + xv * VW, x0);
+                load_vec<double, 2>(Xk + xv * VW + 2, x1);
+                xx[0] = x0[0], xx[1] = x0[1], xx[2] = x1[0], xx[3] = x1[1];
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) xx[e] = Xk[xv * VW + e];
+            }
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                xx[e] += a * (double)pv[e];
+                r[e] -= af * qv[e];
+            }
+            if constexpr (VW == 4) {
+                const double x0[2] = {xx[0], xx[1]}, x1[2] = {xx[2], xx[3]};
+                store_vec<double, 2>(Xk + xv * VW, x0);
+                store_vec<double, 2>(Xk + xv * VW + 2, x1);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VW; ++e) Xk[xv * VW + e] = xx[e];
+            }
+            store_vec<float, VW>(Rk + xv * VW, r);
         }
-        acc[0] += (double)r * (double)r;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[0] += (double)r[e] * (double)r[e];
     }
-    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+    block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
-// beta = rr_new / rr; ask for a residual replacement when r^T r fell 100x
-// (||r|| 10x) since the last one or reached the target.
-__global__ void k_rcg_beta(RcgState S, const double* __restrict__ part, int nblk, int nrhs, int maxit) {
-    const int k = blockIdx.x;   // one block per right-hand side
-    const double s = block_sum(part + (int64_t)k * nblk, nblk);
-    if (threadIdx.x != 0) return;
-    int want = 0;
-    if (!S.done[k]) {
-        S.iters[k] += 1;
-        S.beta[k] = (S.rr[k] > 0.0) ? s / S.rr[k] : 0.0;
-        S.rr[k] = s;
-        want = (s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit) ? 1 : 0;
-    } else {
-        S.beta[k] = 0.0;
-    }
-    if (want) atomicAdd(S.nwant, 1);
-}
-
-__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S) {
+// beta = r_new^T r_new / r^T r (every block sums the update's partials in the
+// same order), P = R + beta P.  Block 0 of each column records r_new^T r_new
+// for the next iteration, counts the iteration and asks for a residual
+// replacement when r^T r fell 100x (||r|| 10x) since the last one or reached
+// the target.
+template <int VW>
+__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S,
+                              const double* __restrict__ part_rr, int nblk, int par, int maxit) {
     const int k = blockIdx.y;
+    __shared__ double b_sh;
+    const double s = block_sum(part_rr + (int64_t)k * nblk, nblk);
+    if (threadIdx.x == 0) {
+        const bool act = !S.done[k];
+        const double rr = rr_buf(S, par)[k];
+        b_sh = (act && rr > 0.0) ? s / rr : 0.0;
+        if (act && blockIdx.x == 0) {
+            S.iters[k] += 1;
+            rr_buf(S, par ^ 1)[k] = s;
+            const bool want = s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit;
+            if (want) atomicAdd(S.nwant, 1);
+        }
+    }
+    __syncthreads();
     if (S.done[k]) return;
-    const float b = (float)S.beta[k];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
-        P[(int64_t)k * p + i] = R[(int64_t)k * p + i] + b * P[(int64_t)k * p + i];
+    const float b = (float)b_sh;
+    float* Pk = P + (int64_t)k * p;
+    const float* Rk = R + (int64_t)k * p;
+    const int64_t nv = p / VW;
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        float r[VW], pv[VW];
+        load_vec<float, VW>(Rk + xv * VW, r);
+        load_vec<float, VW>(Pk + xv * VW, pv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) pv[e] = r[e] + b * pv[e];
+        store_vec<float, VW>(Pk + xv * VW, pv);
+    }
 }
 
-// Residual replacement: R = (float) R64, rr = rr_ref = ||R64||^2; done when
-// ||R64|| <= rtol ||B|| or the iteration budget is spent.
+// Residual replacement: R = (float) R64, rr = rr_ref = ||R64||^2 (into the
+// buffer the next iteration reads); done when ||R64|| <= rtol ||B|| or the
+// iteration budget is spent.
 __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
-                              const double* __restrict__ norms, RcgState S, int maxit) {
+                              const double* __restrict__ norms, RcgState S, int maxit, int par) {
     const int k = blockIdx.y;
     if (S.done[k]) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
         R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rn = norms[2 * k];
-        S.rr[k] = rn * rn;
+        rr_buf(S, par)[k] = rn * rn;
         S.rr_ref[k] = rn * rn;
         if (rn * rn <= S.thr2[k] || S.iters[k] >= maxit || !(rn == rn)) S.done[k] = 1;
     }
@@ -936,17 +1072,18 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     float* P = ctx->work[8].as<float>();
     float* Q = ctx->work[9].as<float>();
     const int nblkC = matvec_num_partials(ctx, e, false, nrhs);
-    ctx->work[10].ensure((size_t)nrhs * std::max(nblkC, RED_BLOCKS) * sizeof(double));
-    double* part = ctx->work[10].as<double>();
+    const int npq = std::max(nblkC, RED_BLOCKS);
+    ctx->work[10].ensure((size_t)nrhs * (npq + CG_BLOCKS) * sizeof(double));
+    double* part = ctx->work[10].as<double>();      // matvec partials (p^T K p), and the start's ||B||^2
+    double* part_rr = part + (size_t)nrhs * npq;    // update partials (r^T r)
     ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);
     char* sb = ctx->work[11].as<char>();
     RcgState S;
-    S.rr = reinterpret_cast<double*>(sb);
-    S.rr_ref = S.rr + nrhs;
+    S.rr[0] = reinterpret_cast<double*>(sb);
+    S.rr[1] = S.rr[0] + nrhs;
+    S.rr_ref = S.rr[1] + nrhs;
     S.thr2 = S.rr_ref + nrhs;
-    S.alpha = S.thr2 + nrhs;
-    S.beta = S.alpha + nrhs;
-    S.done = reinterpret_cast<int*>(S.beta + nrhs);
+    S.done = reinterpret_cast<int*>(S.thr2 + nrhs + nrhs);
     S.iters = S.done + nrhs;
     S.nwant = S.iters + nrhs;
     ctx->tolbuf.ensure(nrhs * sizeof(double));
@@ -957,8 +1094,10 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     ctx->kxbuf.ensure((size_t)nrhs * p * sizeof(double));
 
     dim3 gv(RED_BLOCKS, nrhs);
-    const int tb = 128;
+    dim3 gc(CG_BLOCKS, nrhs);
     const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
+    // 16-byte accesses when every column start is 16-byte aligned (X is the caller's buffer)
+    const bool vec = p % 4 == 0 && ldx % 2 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
     k_rcg_start<<<gv, 256, 0, st>>>(B, ldb, X, ldx, R, P, p, part);
     KRY_CHECK_LAUNCH();
     k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, ctx->tolbuf.as<double>());
@@ -967,25 +1106,47 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     const int poll = 8;
     nrm.assign(2 * nrhs, 0.0);
     *fresh = false;
-    for (int it = 0; it < maxit + poll; ++it) {
+    // one CG iteration of parity par, on ctx->stream (the capture stream while capturing)
+    auto iterate = [&](int par) {
+        cudaStream_t s2 = ctx->stream;
         // columns that have converged are not transformed (pairs of finished columns skip every pass)
         matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt, S.done);
-        k_rcg_alpha<<<nrhs, FIN_THREADS, 0, st>>>(S, part, nblkC, nrhs);
+        if (vec)
+            k_rcg_update<4><<<gc, 256, 0, s2>>>(X, ldx, R, P, Q, p, S, part, nblkC, part_rr, par);
+        else
+            k_rcg_update<1><<<gc, 256, 0, s2>>>(X, ldx, R, P, Q, p, S, part, nblkC, part_rr, par);
         KRY_CHECK_LAUNCH();
-        k_rcg_update<<<gv, 256, 0, st>>>(X, ldx, R, P, Q, p, S, part);
+        if (vec)
+            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, CG_BLOCKS, par, maxit);
+        else
+            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, CG_BLOCKS, par, maxit);
         KRY_CHECK_LAUNCH();
-        k_rcg_beta<<<nrhs, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nrhs, maxit);
-        KRY_CHECK_LAUNCH();
-        k_rcg_pupdate<<<gv, 256, 0, st>>>(P, R, p, S);
-        KRY_CHECK_LAUNCH();
-        if ((it + 1) % poll == 0) {
+    };
+    // Iterations run in blocks of `poll` (an even count, so every block has the
+    // same parity pattern).  The first block runs directly (it sizes every
+    // buffer); later blocks replay one captured graph.
+    Replay block(ctx);
+    for (int it0 = 0; it0 < maxit + poll; it0 += poll) {
+        if (it0 == 0 || !ctx->use_graphs) {
+            for (int i = 0; i < poll; ++i) iterate(i & 1);
+        } else {
+            if (!block.exec)
+                block.capture([&]() {
+                    for (int i = 0; i < poll; ++i) iterate(i & 1);
+                });
+            block.launch();
+        }
+        const int it = it0 + poll - 1;   // last iteration of the block
+        const int par = it & 1;
+        {
             KRY_CUDA(cudaMemcpyAsync(hflag, S.nwant, sizeof(int), cudaMemcpyDeviceToHost, st));
             KRY_CUDA(cudaStreamSynchronize(st));
+            if (block.exec) block.harvest();
             if (*hflag > 0) {
                 // residual replacement for every column still running
                 true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
                 double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
-                k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit);
+                k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit, par ^ 1);
                 KRY_CHECK_LAUNCH();
                 k_count_done<<<1, 1, 0, st>>>(S, nrhs);
                 KRY_CHECK_LAUNCH();

@@ -1,9 +1,11 @@
-"""Profiling driver for the covariance matvec kernels.
+"""Profiling driver for the covariance matvec kernels and the CG loop.
 
 Sets up one workload (mask, FP32 embedding), then issues `--reps` calls of
 kry_matvec on `--nvec` vectors and prints the mean CUDA-event time per call and
-the model bytes per call.  Small and self-contained so that an ncu capture of
-its kernels ends quickly, e.g.
+the model bytes per call.  With `--cg-iters N` it instead runs `--reps` CG
+solves of `--nvec` right-hand sides stopped after N iterations (a tolerance no
+solve reaches) and prints the time per iteration.  Small and self-contained so
+that an ncu capture of its kernels ends quickly, e.g.
 
   ncu --set full --clock-control none -k regex:k_pass -c 3 \
       python -m paper_2012_13133_gb300.profile_matvec --workload grid1024 --nvec 8 --reps 2
@@ -34,6 +36,7 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--autotune", action="store_true", help="autotune the schedule for this batch first")
+    ap.add_argument("--cg-iters", type=int, default=0, help="time CG iterations instead of matvec calls")
     args = ap.parse_args()
 
     w = I.WORKLOADS[args.workload]
@@ -45,6 +48,25 @@ def main():
     dt = torch.float32 if args.prec == "f32" else torch.float64
     emb = ctx.embed(w.cov, prec)
     tuned = ctx.autotune(emb, args.nvec) if args.autotune else None
+    if args.cg_iters:
+        B = torch.tensor(I.normals((args.nvec, p), 1), device=dev)
+        X = torch.empty_like(B)
+        ctx.solve(emb, B, rtol=1e-30, maxit=args.cg_iters, X=X)   # warm-up
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        times = []
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, iters, _, _ = ctx.solve(emb, B, rtol=1e-30, maxit=args.cg_iters, X=X)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / max(1, iters))
+        print(json.dumps({"workload": w.name, "nvec": args.nvec, "prec": args.prec, "schedule": tuned,
+                          "cg_iters": args.cg_iters, "ms_per_iteration": float(np.mean(times)),
+                          "launches": kry.launch_count()}))
+        ctx.close()
+        return
     V = torch.tensor(I.normals((args.nvec, p), 1), dtype=dt, device=dev)
     out = torch.empty_like(V)
     ctx.matvec(emb, V, out)                      # warm-up (allocates the slab)
