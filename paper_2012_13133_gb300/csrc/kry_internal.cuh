@@ -103,7 +103,7 @@ struct kry_ctx {
 
     // scratch
     DevBuf slab32, slab64;        // FFT intermediates
-    DevBuf work[12];              // Krylov vectors and partials
+    DevBuf work[13];              // Krylov vectors and partials
     DevBuf scal;                  // FP64 Krylov scalars
     DevBuf eig_c, eig_z;          // eigenvalue computation
     DevBuf red;                   // reduction partials

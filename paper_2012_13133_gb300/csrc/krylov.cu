@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "fft.cuh"
 #include "kry_internal.cuh"
 #include "matern.cuh"
@@ -279,7 +280,7 @@ __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ 
     const T cb = (T)((j > 0 ? S.beta[(int64_t)k * nsteps + j - 1] : 0.0) * S.s_prev[k]);
     const int64_t off = (int64_t)k * p;
     const int64_t nv = p / VW;
-    double acc[1] = {0.0};
+    DotAcc<T> nrm;
     for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
         T u[VW], wc[VW], wp[VW];
         load_vec<T, VW>(U + off + xv * VW, u);
@@ -294,10 +295,11 @@ __global__ void k_lanczos_update(const T* __restrict__ U, const T* __restrict__ 
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             u[e] = u[e] - ca * wc[e] - cb * wp[e];
-            acc[0] += (double)u[e] * (double)u[e];
+            nrm.add_prod(u[e], u[e]);
         }
         store_vec<T, VW>(Wn + off + xv * VW, u);
     }
+    double acc[1] = {nrm.value()};
     block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
@@ -435,7 +437,7 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
     __syncthreads();
     T* w = Wn + (int64_t)k * p;
     const int64_t nv = p / VW;
-    double acc[1] = {0.0};
+    DotAcc<T> nrm;
     for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
         T proj[VW];
 #pragma unroll
@@ -452,10 +454,11 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
             r[e] -= proj[e];
-            acc[0] += (double)r[e] * (double)r[e];
+            nrm.add_prod(r[e], r[e]);
         }
         store_vec<T, VW>(w + xv * VW, r);
     }
+    double acc[1] = {nrm.value()};
     block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
@@ -896,14 +899,16 @@ static const int CG_BLOCKS = 304;   // blocks per right-hand side of the CG vect
 // r^T r buffer of parity par (a select, not an indexed load from the parameter struct)
 __device__ __forceinline__ double* rr_buf(const RcgState& S, int par) { return par ? S.rr[1] : S.rr[0]; }
 
-// X = 0 (FP64), R = (float) B, P = R; partials of ||B||^2 (exact) per column.
-__global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, double* __restrict__ X, int64_t ldx,
+// X = 0 (a double-float pair Xh + Xl), R = (float) B, P = R; partials of
+// ||B||^2 (exact) per column.
+__global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, float* __restrict__ Xh, float* __restrict__ Xl,
                             float* __restrict__ R, float* __restrict__ P, int64_t p, double* __restrict__ part) {
     const int k = blockIdx.y;
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
         const double b = B[(int64_t)k * ldb + i];
-        X[(int64_t)k * ldx + i] = 0.0;
+        Xh[(int64_t)k * p + i] = 0.f;
+        Xl[(int64_t)k * p + i] = 0.f;
         const float r = (float)b;
         R[(int64_t)k * p + i] = r;
         P[(int64_t)k * p + i] = r;
@@ -938,59 +943,55 @@ __device__ __forceinline__ double rcg_alpha(const RcgState& S, const double* __r
     return a_sh;
 }
 
-// X += alpha P (FP64), R -= alpha Q (FP32); partial ||R||^2.  VW elements per
-// access (16-byte loads of R, P, Q; two of X) when the caller has checked alignment.
+// X += alpha P in double-float (Xh + Xl, FP32 instructions only), R -= alpha Q
+// (FP32); partial ||R||^2 accumulated in double-float.  VW elements per
+// 16-byte access (the internal vectors are 16-byte aligned when p % 4 == 0).
 template <int VW>
-__global__ void k_rcg_update(double* __restrict__ X, int64_t ldx, float* __restrict__ R, const float* __restrict__ P,
-                             const float* __restrict__ Q, int64_t p, RcgState S, const double* __restrict__ part_pq,
-                             int nblkC, double* __restrict__ part_rr, int par) {
+__global__ void k_rcg_update(float* __restrict__ Xh, float* __restrict__ Xl, float* __restrict__ R,
+                             const float* __restrict__ P, const float* __restrict__ Q, int64_t p, RcgState S,
+                             const double* __restrict__ part_pq, int nblkC, double* __restrict__ part_rr, int par) {
     const int k = blockIdx.y;
     const double a = rcg_alpha(S, part_pq, nblkC, k, par);
     if (k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *S.nwant = 0;
     const float af = (float)a;
+    float ahi, alo;
+    df_split(a, ahi, alo);
     const bool act = !S.done[k];
-    float* Rk = R + (int64_t)k * p;
-    const float* Pk = P + (int64_t)k * p;
-    const float* Qk = Q + (int64_t)k * p;
-    double* Xk = X + (int64_t)k * ldx;
+    const int64_t off = (int64_t)k * p;
     const int64_t nv = p / VW;
-    double acc[1] = {0.0};
+    DFAcc nrm;
     for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off + xv * VW;
         float r[VW];
-        load_vec<float, VW>(Rk + xv * VW, r);
+        load_vec<float, VW>(R + o, r);
         if (act) {
-            float pv[VW], qv[VW];
-            double xx[VW];
-            load_vec<float, VW>(Pk + xv * VW, pv);
-            load_vec<float, VW>(Qk + xv * VW, qv);
-            if constexpr (VW == 4) {
-                double x0[2], x1[2];
-                load_vec<double, 2>(Xk + xv * VW, x0);
-                load_vec<double, 2>(Xk + xv * VW + 2, x1);
-                xx[0] = x0[0], xx[1] = x0[1], xx[2] = x1[0], xx[3] = x1[1];
-            } else {
-#pragma unroll
-                for (int e = 0; e < VW; ++e) xx[e] = Xk[xv * VW + e];
-            }
+            float pv[VW], qv[VW], xh[VW], xl[VW];
+            load_vec<float, VW>(P + o, pv);
+            load_vec<float, VW>(Q + o, qv);
+            load_vec<float, VW>(Xh + o, xh);
+            load_vec<float, VW>(Xl + o, xl);
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
-                xx[e] += a * (double)pv[e];
+                df_axpy(xh[e], xl[e], ahi, alo, pv[e]);
                 r[e] -= af * qv[e];
             }
-            if constexpr (VW == 4) {
-                const double x0[2] = {xx[0], xx[1]}, x1[2] = {xx[2], xx[3]};
-                store_vec<double, 2>(Xk + xv * VW, x0);
-                store_vec<double, 2>(Xk + xv * VW + 2, x1);
-            } else {
-#pragma unroll
-                for (int e = 0; e < VW; ++e) Xk[xv * VW + e] = xx[e];
-            }
-            store_vec<float, VW>(Rk + xv * VW, r);
+            store_vec<float, VW>(Xh + o, xh);
+            store_vec<float, VW>(Xl + o, xl);
+            store_vec<float, VW>(R + o, r);
         }
 #pragma unroll
-        for (int e = 0; e < VW; ++e) acc[0] += (double)r[e] * (double)r[e];
+        for (int e = 0; e < VW; ++e) nrm.add_prod(r[e], r[e]);
     }
+    double acc[1] = {nrm.value()};
     block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
+}
+
+// X = Xh + Xl in FP64 (the caller's layout, leading dimension ldx).
+__global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t p,
+                            double* __restrict__ X, int64_t ldx) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)k * ldx + i] = (double)Xh[(int64_t)k * p + i] + (double)Xl[(int64_t)k * p + i];
 }
 
 // beta = r_new^T r_new / r^T r (every block sums the update's partials in the
@@ -1092,13 +1093,19 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     ctx->work[4].ensure((size_t)nrhs * p * sizeof(double));
     double* R64 = ctx->work[4].as<double>();
     ctx->kxbuf.ensure((size_t)nrhs * p * sizeof(double));
+    ctx->work[12].ensure(2 * vb);
+    float* Xh = ctx->work[12].as<float>();   // the solution as a double-float pair
+    float* Xl = Xh + (size_t)nrhs * p;
 
     dim3 gv(RED_BLOCKS, nrhs);
     dim3 gc(CG_BLOCKS, nrhs);
     const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
-    // 16-byte accesses when every column start is 16-byte aligned (X is the caller's buffer)
-    const bool vec = p % 4 == 0 && ldx % 2 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
-    k_rcg_start<<<gv, 256, 0, st>>>(B, ldb, X, ldx, R, P, p, part);
+    const bool vec = p % 4 == 0;   // 16-byte accesses: every column start is 16-byte aligned
+    auto to_f64 = [&]() {
+        k_df_to_f64<<<gv, 256, 0, st>>>(Xh, Xl, p, X, ldx);
+        KRY_CHECK_LAUNCH();
+    };
+    k_rcg_start<<<gv, 256, 0, st>>>(B, ldb, Xh, Xl, R, P, p, part);
     KRY_CHECK_LAUNCH();
     k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, ctx->tolbuf.as<double>());
     KRY_CHECK_LAUNCH();
@@ -1112,9 +1119,9 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
         // columns that have converged are not transformed (pairs of finished columns skip every pass)
         matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt, S.done);
         if (vec)
-            k_rcg_update<4><<<gc, 256, 0, s2>>>(X, ldx, R, P, Q, p, S, part, nblkC, part_rr, par);
+            k_rcg_update<4><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part, nblkC, part_rr, par);
         else
-            k_rcg_update<1><<<gc, 256, 0, s2>>>(X, ldx, R, P, Q, p, S, part, nblkC, part_rr, par);
+            k_rcg_update<1><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part, nblkC, part_rr, par);
         KRY_CHECK_LAUNCH();
         if (vec)
             k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, CG_BLOCKS, par, maxit);
@@ -1144,6 +1151,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             if (block.exec) block.harvest();
             if (*hflag > 0) {
                 // residual replacement for every column still running
+                to_f64();
                 true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
                 double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
                 k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit, par ^ 1);
@@ -1161,6 +1169,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             }
         }
     }
+    if (!*fresh) to_f64();   // after a converged replacement X already holds this solution
     std::vector<int> its(nrhs);
     KRY_CUDA(cudaMemcpyAsync(its.data(), S.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
     KRY_CUDA(cudaStreamSynchronize(st));

@@ -25,6 +25,7 @@
 #include <mutex>
 #include <string>
 
+#include "dfloat.cuh"
 #include "fft.cuh"
 #include "fft16.cuh"
 #include "kry_internal.cuh"
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
     fft_smem<Cx, true, EPT>(rb, L, tl, twiddles<T>(tw32, tw64));
 
     const int row = row0 + g;
-    double da = 0.0, db = 0.0;
+    DotAcc<T> acc_a, acc_b;
     if (row < n1) {
         if (MODE == 0) {
             const T sa = scale ? (T)scale[va] : (T)1;
@@ -191,12 +192,12 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
                 const T xa = pa[q] * sa;
                 const T ya = z.x + t2 * xa;
                 oa[q] = ya;
-                da += (double)xa * (double)ya;
+                acc_a.add_prod(xa, ya);
                 if (has_b) {
                     const T xb = pb[q] * sb;
                     const T yb = z.y + t2 * xb;
                     ob[q] = yb;
-                    db += (double)xb * (double)yb;
+                    acc_b.add_prod(xb, yb);
                 }
             }
         } else {
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(EPT >= 16 ? 512 : 1024) k_pass_c(const typenam
         }
     }
     if (MODE == 0 && dots != nullptr) {
+        double da = acc_a.value(), db = acc_b.value();
         // block reduction of (da, db) in a fixed order; blocks narrower than a
         // warp (short rows) reduce serially through shared memory
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
     kry16::transform<Cx, true>(b, v, t, tw, ld_g, ld_s, st_s, st_n, false, true);
     __syncthreads();
 
-    double da = 0.0, db = 0.0;
+    DotAcc<T> acc_a, acc_b;
     if (row < n1) {
         if (MODE == 0) {
             const T sa = scale ? (T)scale[va] : (T)1;
@@ -423,12 +425,12 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
                 const T xa = pa[q] * sa;
                 const T ya = z.x + t2 * xa;
                 oa[q] = ya;
-                da += (double)xa * (double)ya;
+                acc_a.add_prod(xa, ya);
                 if (has_b) {
                     const T xb = pb[q] * sb;
                     const T yb = z.y + t2 * xb;
                     ob[q] = yb;
-                    db += (double)xb * (double)yb;
+                    acc_b.add_prod(xb, yb);
                 }
             }
         } else {
@@ -442,6 +444,7 @@ __global__ void __launch_bounds__(512, KRY_K16_MINB) k16_pass_c(const typename c
         }
     }
     if (MODE == 0 && dots != nullptr) {
+        double da = acc_a.value(), db = acc_b.value();
         // rows are interleaved across lanes (g fastest); the block reduction
         // sums every row's products of the block in a fixed order
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
