@@ -36,7 +36,9 @@ from paper_2012_13133_gb300 import inputs as I  # noqa: E402
 WORKLOAD = "grid1024"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "matvec_grid1024.md")
 KERNEL_SOURCES = ["paper_2012_13133_gb300/csrc/matvec.cu", "paper_2012_13133_gb300/csrc/fft.cuh",
-                  "paper_2012_13133_gb300/csrc/fft16.cuh"]
+                  "paper_2012_13133_gb300/csrc/fft16.cuh", "paper_2012_13133_gb300/csrc/fftspec.cuh",
+                  "paper_2012_13133_gb300/csrc/mvspec.cuh", "paper_2012_13133_gb300/csrc/mvspec_a.cu",
+                  "paper_2012_13133_gb300/csrc/mvspec_b.cu", "paper_2012_13133_gb300/csrc/mvspec_c.cu"]
 
 
 def kernel_hash():

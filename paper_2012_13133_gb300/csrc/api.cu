@@ -3,6 +3,7 @@
 // kernels of embed.cu, matvec.cu and krylov.cu.  No computation of the hot
 // path happens on the host beyond scalar bookkeeping.
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -320,7 +321,7 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         KRY_CUDA(cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
         // every scratch buffer is stream-ordered on the context stream; keep freed
         // pool memory cached in this process instead of returning it at each sync
-        DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->slab32,
+        DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                           &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
                           &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
         for (DevBuf* b : bufs) b->stream = ctx->stream;
@@ -331,6 +332,8 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         KRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
         KRY_CUDA(cudaMallocHost(&ctx->host_pinned, 4096 * sizeof(double)));
         kry::init_twiddles(ctx);
+        const char* gen = getenv("KRY_MATVEC_GENERIC");
+        ctx->use_spec = !(gen && gen[0] == '1');
         KRY_CUDA(cudaStreamSynchronize(ctx->stream));
         return KRY_OK;
     });
@@ -348,7 +351,7 @@ void kry_destroy(kry_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->slab32,
+    DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                       &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
                       &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
     for (DevBuf* b : bufs) b->release();

@@ -15,6 +15,7 @@
 #include "fft.cuh"
 #include "kry_internal.cuh"
 #include "matern.cuh"
+#include "mvspec.cuh"
 
 namespace kry {
 
@@ -34,6 +35,8 @@ void init_twiddles(kry_ctx* ctx) {
     ctx->tw32.ensure(KRY_TWN * sizeof(float2));
     k_twiddles<<<(KRY_TWN + 255) / 256, 256, 0, ctx->stream>>>(ctx->tw64.as<double2>(), ctx->tw32.as<float2>());
     KRY_CHECK_LAUNCH();
+    ctx->twt32.ensure((size_t)kspec::TWT_ROWS * 16 * sizeof(float2));
+    kspec::fill_stage_twiddles(ctx->twt32.as<float2>(), ctx->stream);
 }
 
 // ------------------------------------------------------------------ lag covariance

@@ -98,8 +98,13 @@ struct kry_ctx {
     DevBuf colidx;   // int32 [p]: column of each observed cell
     DevBuf cellidx;  // int32 [p]: row-major cell index of each observed cell
 
-    // shared twiddle tables, W[k] = exp(-2 pi i k / KRY_TWN)
-    DevBuf tw32, tw64;
+    // shared twiddle tables, W[k] = exp(-2 pi i k / KRY_TWN), and the FP32
+    // stage table of the specialised passes (row Ns - 1 + k: W_{16 Ns}^{k m})
+    DevBuf tw32, tw64, twt32;
+    // FP32 matvecs use the length-specialised passes where they apply (set
+    // KRY_MATVEC_GENERIC=1 in the environment to time the generic radix-16
+    // passes instead; both compute the same transform)
+    bool use_spec = true;
 
     // scratch
     DevBuf slab32, slab64;        // FFT intermediates

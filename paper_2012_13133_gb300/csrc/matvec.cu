@@ -28,6 +28,7 @@
 #include "dfloat.cuh"
 #include "fft.cuh"
 #include "fft16.cuh"
+#include "mvspec.cuh"
 #include "kry_internal.cuh"
 
 namespace kry {
@@ -603,15 +604,18 @@ const MvSched& sched_for(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec) {
 static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, int* C) {
     const MvSched& want = sched_for(ctx, M1, M2, dbl, nvec);
     const size_t lim = (size_t)ctx->max_smem_optin - 1024;   // leave room for static shared memory
+    // the length-specialised FP32 passes run up to 8 transforms per block
+    const int ntmax = (!dbl && ctx->use_spec) ? 8 : 16;
     auto fit = [&](int L, int nt) {
-        nt = std::max(1, std::min(nt, 16));
-        while (nt > 1 && (nt * (L >> 4) > 512 || smem16(L, nt, dbl) > lim)) nt >>= 1;
+        nt = std::max(1, std::min(nt, ntmax));
+        while (nt > 1 && (nt * (L >> 4) > (ntmax == 8 ? 1024 : 512) || smem16(L, nt, dbl) > lim)) nt >>= 1;
         return nt;
     };
     int g = want.g16 > 0 ? want.g16 : std::max(1, 256 / (M2 >> 4));
     int c = want.c16 > 0 ? want.c16 : std::max(1, 512 / (M1 >> 4));
     *G = fit(M2, g);
     *C = std::min(fit(M1, c), M2);
+    if (ntmax == 8) *C = std::min(*C, std::max(1, M2 >> 4));   // specialised pass A/C need C <= M2 / 16
 }
 
 #define KRY_DISPATCH_NT(NTV, ...)                                  \
@@ -646,6 +650,24 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
     const size_t smA = smem16(M2, G, dbl), smB = smem16(M1, C, dbl);
     const int nbx = (n1 + G - 1) / G;
     const int logC = ilog2(C);
+    if constexpr (sizeof(T) == 4) {
+        if (mode == 0 && ctx->use_spec && kspec::supported(M1, M2, G, C)) {
+            kspec::SpecArgs a{};
+            a.vin = vin; a.ld_in = ld_in; a.scale = scale; a.vout = vout; a.ld_out = ld_out;
+            a.nvec = nvec; a.rowptr = rowptr; a.colidx = colidx;
+            a.n1 = n1; a.n2 = n2; a.M1 = M1; a.M2 = M2; a.G = G; a.C = C; a.logC = logC;
+            a.slab = slab; a.lamT = lamT; a.lam_stride = e->lam_stride; a.vpt = vpt;
+            a.tau2 = tau2; a.tau2v = e->tau2_dev; a.dots = dots; a.nds = nds;
+            a.twt = ctx->twt32.as<float4>(); a.skip = skip;
+            for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
+                a.pair0 = pair0;
+                a.np = std::min(ppb, npairs - pair0);
+                KRY_REQUIRE(kspec::launch_a(a, st) && kspec::launch_b(a, st) && kspec::launch_c(a, st),
+                            KRY_EUNSUPPORTED, "no specialised matvec pass for this shape");
+            }
+            return;
+        }
+    }
     for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
         const int np = std::min(ppb, npairs - pair0);
         dim3 gA(nbx, np), gB(M2 / C, np);
@@ -990,10 +1012,12 @@ static double autotune_t(kry_ctx* ctx, const kry_embed* e, int nvec, MvSched* be
     const bool had = ctx->tuned.count(key) > 0;
     const MvSched prev = had ? ctx->tuned[key] : bs;
     if (use16(M1, M2)) {
+        const bool spec = !dbl && ctx->use_spec;
+        const int tmax = spec ? 1024 : 512;
         for (int g : {1, 2, 4, 8, 16}) {
-            if (g * (M2 >> 4) > 512 || smem16(M2, g, dbl) > lim) continue;
+            if (g * (M2 >> 4) > tmax || smem16(M2, g, dbl) > lim || (spec && g > 8)) continue;
             for (int c : {1, 2, 4, 8, 16}) {
-                if (c * (M1 >> 4) > 512 || smem16(M1, c, dbl) > lim || c > M2) continue;
+                if (c * (M1 >> 4) > tmax || smem16(M1, c, dbl) > lim || c > M2 || (spec && (c > 8 || c > (M2 >> 4)))) continue;
                 for (int ppb : ppbs) {
                     MvSched cand = bs;
                     cand.g16 = g;
