@@ -218,6 +218,12 @@ static void check_embed(kry_ctx* ctx, const kry_embed* e) {
     require_mask(ctx);
 }
 
+// True if FP32 matvecs on this embedding run the length-specialised passes
+// (their column pass reads the permuted eigenvalue copy lam32P).
+static bool spec_column_pass(const kry_ctx* ctx, const kry_embed* e) {
+    return ctx->use_spec && e->M1 >= 64 && e->M2 >= 64 && e->M1 <= 8192 && e->M2 <= 8192;
+}
+
 static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     check_cov(cov);
     require_mask(ctx);
@@ -237,10 +243,12 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
         const size_t MM = (size_t)e->M1 * e->M2;
         dev_alloc((void**)&e->lam64T, MM * sizeof(double), ctx->stream);
         if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, MM * sizeof(float), ctx->stream);
+        if (prec == KRY_F32 && spec_column_pass(ctx, e)) dev_alloc((void**)&e->lam32P, MM * sizeof(float), ctx->stream);
         kry::store_embedding(ctx, e, 0);
     } catch (...) {
         if (e->lam64T) cudaFreeAsync(e->lam64T, ctx->stream);
         if (e->lam32T) cudaFreeAsync(e->lam32T, ctx->stream);
+        if (e->lam32P) cudaFreeAsync(e->lam32P, ctx->stream);
         delete e;
         throw;
     }
@@ -253,6 +261,7 @@ static void free_embed(kry_embed* e, cudaStream_t s) {
     if (!e) return;
     if (e->lam64T) cudaFreeAsync(e->lam64T, s);
     if (e->lam32T) cudaFreeAsync(e->lam32T, s);
+    if (e->lam32P) cudaFreeAsync(e->lam32P, s);
     if (e->tau2_dev) cudaFreeAsync(e->tau2_dev, s);
     delete e;
 }
@@ -281,6 +290,8 @@ static kry_embed* make_embed_batch(kry_ctx* ctx, const kry_cov* thetas, int nthe
     try {
         dev_alloc((void**)&e->lam64T, ntheta * MM * sizeof(double), ctx->stream);
         if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, ntheta * MM * sizeof(float), ctx->stream);
+        if (prec == KRY_F32 && spec_column_pass(ctx, e))
+            dev_alloc((void**)&e->lam32P, ntheta * MM * sizeof(float), ctx->stream);
         dev_alloc((void**)&e->tau2_dev, ntheta * sizeof(double), ctx->stream);
         std::vector<double> t2(ntheta);
         for (int t = 0; t < ntheta; ++t) {

@@ -272,8 +272,11 @@ void compute_eigs(kry_ctx* ctx, const kry_cov& cov, int n1, int n2, double dx1, 
 }
 
 // lamT[j][k] = lam[k][j] * scale (FP64 and optionally FP32), 32 x 32 tiles.
+// With t32p != NULL also the column-permuted FP32 copy: row k = t + m M1/16 of
+// column j goes to t32p[j M1 + 16 t + m].
 __global__ void k_transpose_scale(const double* __restrict__ lam, int M1, int M2, double scale,
-                                  double* __restrict__ t64, float* __restrict__ t32) {
+                                  double* __restrict__ t64, float* __restrict__ t32, float* __restrict__ t32p) {
+    const int lt = M1 >> 4;
     __shared__ double tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -287,6 +290,7 @@ __global__ void k_transpose_scale(const double* __restrict__ lam, int M1, int M2
             const double v = tile[threadIdx.x][r] * scale;
             t64[(int64_t)j * M1 + k] = v;
             if (t32) t32[(int64_t)j * M1 + k] = (float)v;
+            if (t32p) t32p[(int64_t)j * M1 + (k % lt) * 16 + k / lt] = (float)v;
         }
     }
 }
@@ -297,7 +301,8 @@ void store_embedding(kry_ctx* ctx, kry_embed* e, int slot) {
     const int64_t off = (int64_t)slot * e->M1 * e->M2;
     k_transpose_scale<<<grid, blk, 0, ctx->stream>>>(ctx->eig_c.as<double>(), e->M1, e->M2,
                                                      1.0 / ((double)e->M1 * (double)e->M2), e->lam64T + off,
-                                                     e->lam32T ? e->lam32T + off : nullptr);
+                                                     e->lam32T ? e->lam32T + off : nullptr,
+                                                     e->lam32P ? e->lam32P + off : nullptr);
     KRY_CHECK_LAUNCH();
 }
 

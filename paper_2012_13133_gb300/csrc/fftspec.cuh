@@ -14,8 +14,8 @@
 //    per-thread base plus an immediate offset.
 //  * Twiddles.  Stage s (radix 16, stride Ns > 1) multiplies input m of
 //    butterfly k = t mod Ns by W_{16 Ns}^{k m}.  A per-stage table holds the 16
-//    twiddles of each k contiguously, row Ns - 1 + k, so a thread loads its 15
-//    twiddles with eight 16-byte loads and forms none of them by products.
+//    twiddles of each k contiguously, row Ns - 1 + k, so a thread's twiddle
+//    loads are few 16-byte loads from one 128-byte row (see KRY_KS_TW).
 //  * Pruning.  First stages whose upper half of inputs is zero (zero-padded
 //    rows and columns, M >= 2n) run half-input DFTs; last stages whose upper
 //    half of outputs is discarded (rows >= n1 after the inverse column pass,
@@ -52,16 +52,69 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 w, bool conj) {
                 : make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
 
+// Twiddle scheme of a radix-16 stage (loads are the scarce resource of these
+// passes, FP32 arithmetic is not):
+//   0: load all 15 twiddles (eight 16-byte loads);
+//   1: load W^1..W^4, W^8, W^12 (five 16-byte loads) and form the other nine
+//      as one product each;
+//   2: load W^1, W^4, W^5 (two 16-byte loads) and form the other twelve with
+//      at most two products each (fastest on GB300: 64-vector 1024^2 matvec
+//      1.18 / 1.08 / 0.97 ms for schemes 0 / 1 / 2).
+#ifndef KRY_KS_TW
+#define KRY_KS_TW 2
+#endif
+
 // v[m] *= W^{k m} (m = 1..15) from one 16-entry table row (forward twiddles;
 // the inverse transform uses their conjugates).
 template <bool INV>
 __device__ __forceinline__ void twiddle16(float2* v, const float4* __restrict__ row) {
+#if KRY_KS_TW == 2
+    const float4 a = __ldg(row), c = __ldg(row + 2);
+    const float2 w1 = make_float2(a.z, a.w), w4 = make_float2(c.x, c.y), w5 = make_float2(c.z, c.w);
+    const float2 w2 = cmulf(w1, w1, false), w3 = cmulf(w4, w1, true), w6 = cmulf(w5, w1, false);
+    const float2 w8 = cmulf(w4, w4, false), w9 = cmulf(w4, w5, false), w10 = cmulf(w5, w5, false);
+    v[1] = cmulf(v[1], w1, INV);
+    v[2] = cmulf(v[2], w2, INV);
+    v[3] = cmulf(v[3], w3, INV);
+    v[4] = cmulf(v[4], w4, INV);
+    v[5] = cmulf(v[5], w5, INV);
+    v[6] = cmulf(v[6], w6, INV);
+    v[7] = cmulf(v[7], cmulf(w4, w3, false), INV);
+    v[8] = cmulf(v[8], w8, INV);
+    v[9] = cmulf(v[9], w9, INV);
+    v[10] = cmulf(v[10], w10, INV);
+    v[11] = cmulf(v[11], cmulf(w5, w6, false), INV);
+    v[12] = cmulf(v[12], cmulf(w8, w4, false), INV);
+    v[13] = cmulf(v[13], cmulf(w8, w5, false), INV);
+    v[14] = cmulf(v[14], cmulf(w10, w4, false), INV);
+    v[15] = cmulf(v[15], cmulf(w10, w5, false), INV);
+#elif KRY_KS_TW == 1
+    const float4 a = __ldg(row), b = __ldg(row + 1), c = __ldg(row + 2), d = __ldg(row + 4), e = __ldg(row + 6);
+    const float2 w1 = make_float2(a.z, a.w), w2 = make_float2(b.x, b.y), w3 = make_float2(b.z, b.w);
+    const float2 w4 = make_float2(c.x, c.y), w8 = make_float2(d.x, d.y), w12 = make_float2(e.x, e.y);
+    v[1] = cmulf(v[1], w1, INV);
+    v[2] = cmulf(v[2], w2, INV);
+    v[3] = cmulf(v[3], w3, INV);
+    v[4] = cmulf(v[4], w4, INV);
+    v[5] = cmulf(v[5], cmulf(w4, w1, false), INV);
+    v[6] = cmulf(v[6], cmulf(w4, w2, false), INV);
+    v[7] = cmulf(v[7], cmulf(w4, w3, false), INV);
+    v[8] = cmulf(v[8], w8, INV);
+    v[9] = cmulf(v[9], cmulf(w8, w1, false), INV);
+    v[10] = cmulf(v[10], cmulf(w8, w2, false), INV);
+    v[11] = cmulf(v[11], cmulf(w8, w3, false), INV);
+    v[12] = cmulf(v[12], w12, INV);
+    v[13] = cmulf(v[13], cmulf(w12, w1, false), INV);
+    v[14] = cmulf(v[14], cmulf(w12, w2, false), INV);
+    v[15] = cmulf(v[15], cmulf(w12, w3, false), INV);
+#else
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 w = __ldg(row + q);
         if (q > 0) v[2 * q] = cmulf(v[2 * q], make_float2(w.x, w.y), INV);
         v[2 * q + 1] = cmulf(v[2 * q + 1], make_float2(w.z, w.w), INV);
     }
+#endif
 }
 
 // Outputs X[0..7] of a 16-point DFT (4 x 4 as in kry16::dft16; the second

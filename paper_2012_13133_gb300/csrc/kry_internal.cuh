@@ -149,6 +149,11 @@ struct kry_embed {
     // 1 / (M1 M2), FP64 always and FP32 when prec = KRY_F32
     double* lam64T = nullptr;
     float* lam32T = nullptr;
+    // FP32 eigenvalues for the length-specialised column pass: the same
+    // [M2][M1] blocks with each column permuted so that the 16 values one
+    // thread multiplies (rows t + m M1/16, m < 16) are contiguous at 16 t + m
+    // (NULL when that pass does not apply)
+    float* lam32P = nullptr;
     double lam_min = 0, lam_max = 0;
     // several covariance settings in one embedding (batched likelihood
     // search): ntheta eigenvalue blocks lam_stride elements apart, per-theta

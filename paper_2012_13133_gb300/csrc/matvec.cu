@@ -656,7 +656,8 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
             a.vin = vin; a.ld_in = ld_in; a.scale = scale; a.vout = vout; a.ld_out = ld_out;
             a.nvec = nvec; a.rowptr = rowptr; a.colidx = colidx;
             a.n1 = n1; a.n2 = n2; a.M1 = M1; a.M2 = M2; a.G = G; a.C = C; a.logC = logC;
-            a.slab = slab; a.lamT = lamT; a.lam_stride = e->lam_stride; a.vpt = vpt;
+            KRY_REQUIRE(e->lam32P != nullptr, KRY_EINVAL, "embedding lacks the permuted eigenvalues");
+            a.slab = slab; a.lamP = e->lam32P; a.lam_stride = e->lam_stride; a.vpt = vpt;
             a.tau2 = tau2; a.tau2v = e->tau2_dev; a.dots = dots; a.nds = nds;
             a.twt = ctx->twt32.as<float4>(); a.skip = skip;
             for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {

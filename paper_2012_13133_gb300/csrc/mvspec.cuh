@@ -7,7 +7,8 @@
 // Layouts (identical to the generic radix-16 passes, so the two can be mixed):
 //  * slab: per complex pair an n1 x M2 complex intermediate, stored in column
 //    tiles slab[pair][tile][i][c], c < C, tile = column / C;
-//  * lamT: eigenvalues transposed to [M2][M1], scaled by 1 / (M1 M2);
+//  * lamP: eigenvalues transposed to [M2][M1], scaled by 1 / (M1 M2), each
+//    column permuted so that row t + m L/16 sits at 16 t + m;
 //  * twt: stage twiddle table, row Ns - 1 + k (Ns a power of two <= 512,
 //    k < Ns) holds W_{16 Ns}^{k m}, m = 0..15, W_n = exp(-2 pi i / n).
 #pragma once
@@ -69,9 +70,14 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
         const float sbv = (scale && has_b) ? (float)scale[vb] : 1.f;
         const float* pa = vin + (int64_t)va * ld;
         const float* pb = vin + (int64_t)vb * ld;
-        const int q1 = rowptr[row + 1];
-        for (int q = rowptr[row] + t; q < q1; q += LT)
-            sb[soff<PS, NT>(colidx[q])] = make_float2(pa[q] * sa, has_b ? pb[q] * sbv : 0.f);
+        // a row holds at most n2 <= L/2 = 8 L/16 observed cells: a fixed-trip
+        // predicated loop lets every load of the row issue before the stores
+        const int q0 = rowptr[row] + t, q1 = rowptr[row + 1];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = q0 + i * LT;
+            if (q < q1) sb[soff<PS, NT>(colidx[q])] = make_float2(pa[q] * sa, has_b ? pb[q] * sbv : 0.f);
+        }
     }
     __syncthreads();
 
@@ -101,7 +107,7 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
 // inverse column FFT starting from registers, keep rows < n1.
 template <int B, int NT>
 __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
-    ks_pass_b(float2* __restrict__ slab, const float* __restrict__ lamT, int n1, int M2,
+    ks_pass_b(float2* __restrict__ slab, const float* __restrict__ lamP, int n1, int M2,
               const float4* __restrict__ twt, int pair0, int64_t lam_stride, int vpt, const int* __restrict__ skip,
               int nvec) {
     using P = Plan<B>;
@@ -134,11 +140,15 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
 
     // eigenvalue multiply
     const int theta = vpt ? (2 * (pair0 + (int)blockIdx.y)) / vpt : 0;
-    const float* lam = lamT + theta * lam_stride + (int64_t)(tile * NT + c) * L + t;
+    // column-permuted eigenvalues: slot m of thread t at 16 t + m
+    const float4* lam = reinterpret_cast<const float4*>(lamP + theta * lam_stride + (int64_t)(tile * NT + c) * L) + 4 * t;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const float l = __ldg(lam + m * LT);
-        v[m] = make_float2(v[m].x * l, v[m].y * l);
+    for (int q = 0; q < 4; ++q) {
+        const float4 l = __ldg(lam + q);
+        v[4 * q] = make_float2(v[4 * q].x * l.x, v[4 * q].y * l.x);
+        v[4 * q + 1] = make_float2(v[4 * q + 1].x * l.y, v[4 * q + 1].y * l.y);
+        v[4 * q + 2] = make_float2(v[4 * q + 2].x * l.z, v[4 * q + 2].y * l.z);
+        v[4 * q + 3] = make_float2(v[4 * q + 3].x * l.w, v[4 * q + 3].y * l.w);
     }
 
     // inverse, first stage fed from registers: input position t + c lives in slot c / (L/16)
@@ -177,6 +187,7 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
     const float2 zero = make_float2(0.f, 0.f);
     const int tb = soff<PS, NT>(t);
     const bool live = row < n1;
+    const int q0 = live ? rowptr[row] + t : 0, q1 = live ? rowptr[row + 1] : 0;   // read early
 
     const int64_t tstride = (int64_t)n1 * C;
     const float2* in = slab + (int64_t)blockIdx.y * n1 * (int64_t)(L) + (int64_t)row * C +
@@ -204,18 +215,22 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
         const float* pb = vin + (int64_t)vb * ld_in;
         float* oa = vout + (int64_t)va * ld_out;
         float* ob = vout + (int64_t)vb * ld_out;
-        const int q1 = rowptr[row + 1];
-        for (int q = rowptr[row] + t; q < q1; q += LT) {
-            const float2 z = sb[soff<PS, NT>(colidx[q])];
-            const float xa = pa[q] * sa;
-            const float ya = z.x + t2 * xa;
-            oa[q] = ya;
-            acc_a.add_prod(xa, ya);
-            if (has_b) {
-                const float xb = pb[q] * sbv;
-                const float yb = z.y + t2 * xb;
-                ob[q] = yb;
-                acc_b.add_prod(xb, yb);
+        // at most n2 <= 8 L/16 cells per row: fixed-trip predicated loop
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = q0 + i * LT;
+            if (q < q1) {
+                const float2 z = sb[soff<PS, NT>(colidx[q])];
+                const float xa = pa[q] * sa;
+                const float ya = z.x + t2 * xa;
+                oa[q] = ya;
+                acc_a.add_prod(xa, ya);
+                if (has_b) {
+                    const float xb = pb[q] * sbv;
+                    const float yb = z.y + t2 * xb;
+                    ob[q] = yb;
+                    acc_b.add_prod(xb, yb);
+                }
             }
         }
     }
@@ -265,7 +280,7 @@ struct SpecArgs {
     int n1, n2, M1, M2;
     int G, C, logC;
     float2* slab;
-    const float* lamT;
+    const float* lamP;   // column-permuted FP32 eigenvalues (kry_embed::lam32P)
     int64_t lam_stride;
     int vpt;
     double tau2;

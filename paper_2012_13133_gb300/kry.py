@@ -15,7 +15,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libkry.so")
+# KRY_LIBRARY names another build of the same library (e.g. a variant built with other flags)
+LIB_PATH = os.environ.get("KRY_LIBRARY") or os.path.join(_PKG, "libkry.so")
 
 KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ENOTPSD, KRY_ENOCONV, KRY_ENAN, KRY_ETIMEOUT, KRY_ECUDA, KRY_EUNSUPPORTED = range(9)
 STATUS_NAMES = ["KRY_OK", "KRY_EINVAL", "KRY_ENOMEM", "KRY_ENOTPSD", "KRY_ENOCONV", "KRY_ENAN", "KRY_ETIMEOUT",

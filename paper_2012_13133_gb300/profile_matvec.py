@@ -7,7 +7,7 @@ solves of `--nvec` right-hand sides stopped after N iterations (a tolerance no
 solve reaches) and prints the time per iteration.  Small and self-contained so
 that an ncu capture of its kernels ends quickly, e.g.
 
-  ncu --set full --clock-control none -k regex:k_pass -c 3 \
+  ncu --set full --clock-control none -k regex:ks_pass -c 3 \
       python -m paper_2012_13133_gb300.profile_matvec --workload grid1024 --nvec 8 --reps 2
 """
 from __future__ import annotations
@@ -36,6 +36,7 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--autotune", action="store_true", help="autotune the schedule for this batch first")
+    ap.add_argument("--sched", default="", help="fixed schedule 'rows,cols,pairs' per block/batch (no autotune)")
     ap.add_argument("--cg-iters", type=int, default=0, help="time CG iterations instead of matvec calls")
     args = ap.parse_args()
 
@@ -48,6 +49,10 @@ def main():
     dt = torch.float32 if args.prec == "f32" else torch.float64
     emb = ctx.embed(w.cov, prec)
     tuned = ctx.autotune(emb, args.nvec) if args.autotune else None
+    if args.sched:
+        g, c, ppb = (int(x) for x in args.sched.split(","))
+        ctx.set_schedule(emb, args.nvec, g, c, ppb)
+        tuned = {"rows_per_block": g, "cols_per_block": c, "pairs_per_batch": ppb}
     if args.cg_iters:
         B = torch.tensor(I.normals((args.nvec, p), 1), device=dev)
         X = torch.empty_like(B)
