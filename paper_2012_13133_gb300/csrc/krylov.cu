@@ -244,6 +244,7 @@ struct LanczosState {
     double* coef;     // [nprobe][nsteps] s_i * q_i^T w of the vector being reorthogonalised
     int* flag;        // [nprobe] 1: reorthogonalise the new vector of this step
     int* force;       // [nprobe] 1: the next new vector is reorthogonalised too
+    double* pre2;     // [nprobe] ||w||^2 before the Gram-Schmidt pass of a flagged vector
 };
 
 __global__ void k_lanczos_init(LanczosState S, int nprobe, int nsteps, double s0) {
@@ -327,10 +328,16 @@ __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, 
 // algorithm with partial reorthogonalization", Math. Comp. 42, 1984) tracks
 // estimates omega_{j,k} of q_j^T q_k by a scalar recurrence derived from the
 // three-term recurrences of q_j and q_k, with a rounding term of size
-// eps (beta_k + beta_j); when the largest estimate for the new vector exceeds
-// sqrt(eps) (eps = unit roundoff of the vectors), the new vector and the one
-// after it are orthogonalised against every stored basis vector (one classical
-// Gram-Schmidt pass) and their estimates reset to eps.  Semi-orthogonality
+// eps_round (beta_k + beta_j); when the largest estimate for the new vector
+// exceeds sqrt(eps) (eps = unit roundoff of the vectors), the new vector and
+// the one after it are orthogonalised against every stored basis vector
+// (classical Gram-Schmidt, repeated once when it cancels most of the vector)
+// and their estimates reset to eps.  The rounding term uses
+// eps_round = eps log2(M1 M2): the local error of a step is that of the FFT
+// matvec, which grows with the log of the transform size.  With eps alone,
+// FP32 runs on smooth long-range covariances (512^2 grid, range >= 0.1)
+// lost orthogonality unnoticed: per-probe values up to 3% off the FP64 run,
+// some NaN; with eps_round they agree to 2e-5 at 5% more time.  Semi-orthogonality
 // (|q_j^T q_k| <= sqrt(eps)) keeps the tridiagonal equal to the projection of K
 // on the Krylov space up to O(eps ||K||) (Simon 1984).  Decisions are per
 // vector, on the device, so the launch sequence is fixed and graph-capturable.
@@ -338,7 +345,7 @@ __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, 
 // Estimates for q_{j+1} from ||w||^2 partials (before any reorthogonalisation);
 // sets flag[k] when w is to be reorthogonalised.
 __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int nblk, int nsteps, int j,
-                            double eps) {
+                            double eps, double eps_round) {
     const int k = blockIdx.x;   // one block per vector
     const double s = block_sum(part + (int64_t)k * nblk, nblk);
     if (threadIdx.x != 0) return;
@@ -360,18 +367,33 @@ __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int
     for (int i = 0; i < j; ++i) {
         double t = be[i] * oc[i + 1] + (al[i] - aj) * oc[i] - be[j - 1] * op[i];
         if (i > 0) t += be[i - 1] * oc[i - 1];
-        t += copysign(eps * (be[i] + bj), t);
+        t += copysign(eps_round * (be[i] + bj), t);
         on[i] = t / bj;
         worst = fmax(worst, fabs(on[i]));
     }
-    on[j] = eps * tnorm / bj;
+    on[j] = eps_round * tnorm / bj;
     on[j + 1] = 1.0;
     worst = fmax(worst, fabs(on[j]));
     const int f = (S.force[k] || worst > sqrt(eps)) ? 1 : 0;
     S.flag[k] = f;
+    S.pre2[k] = s;
     S.force[k] = f && !S.force[k];   // the vector after a reorthogonalised one is reorthogonalised too
     if (f)
         for (int i = 0; i <= j; ++i) on[i] = eps;
+}
+
+// "Twice is enough" (Kahan; Parlett, The Symmetric Eigenvalue Problem, 1980,
+// Sec. 6-9): a flagged vector whose norm fell below 1/sqrt(2) of its norm
+// before the Gram-Schmidt pass lost most of itself to cancellation, and its
+// rounding errors are then large relative to what is left; it stays flagged
+// for a second pass, every other vector is unflagged.
+__global__ void k_reorth_again(LanczosState S, const double* __restrict__ part, int nblk) {
+    const int k = blockIdx.x;   // one block per vector
+    if (!S.flag[k]) return;
+    const double s = block_sum(part + (int64_t)k * nblk, nblk);
+    if (threadIdx.x != 0) return;
+    S.flag[k] = (s < 0.5 * S.pre2[k]) ? 1 : 0;
+    S.pre2[k] = s;
 }
 
 // Partial dot products W_i^T w (i = 0..j) of each flagged vector, 8 basis
@@ -552,7 +574,7 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     ctx->work[4].ensure((size_t)nvec * nred * sizeof(double));
     double* part = ctx->work[4].as<double>();
     const size_t nsc = (size_t)nvec * (2 * nsteps + 4) + nvec;
-    const size_t npro = reorth ? (size_t)nvec * (2 * nsteps + 3 * (nsteps + 1)) : 0;
+    const size_t npro = reorth ? (size_t)nvec * (2 * nsteps + 3 * (nsteps + 1) + 1) : 0;
     ctx->scal.ensure((nsc + npro) * sizeof(double));
     double* sc = ctx->scal.as<double>();
     LanczosState S;
@@ -563,19 +585,24 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     double* res = S.beta + (size_t)nvec * nsteps;
     ctx->work[5].ensure((size_t)nvec * 3 * sizeof(int));
     S.m_eff = ctx->work[5].as<int>();
-    S.s_hist = S.omega = S.coef = nullptr;
+    S.s_hist = S.omega = S.coef = S.pre2 = nullptr;
     S.flag = S.force = nullptr;
     double* dpart = nullptr;
     if (reorth) {
         S.s_hist = sc + nsc;
         S.coef = S.s_hist + (size_t)nvec * nsteps;
         S.omega = S.coef + (size_t)nvec * nsteps;
+        S.pre2 = S.omega + (size_t)3 * nvec * (nsteps + 1);
         S.flag = S.m_eff + nvec;
         S.force = S.flag + nvec;
         ctx->work[6].ensure((size_t)nvec * (nsteps + 8) * RED_BLOCKS * sizeof(double));
         dpart = ctx->work[6].as<double>();
     }
     const double eps = dbl ? 1.1102230246251565e-16 : 5.9604644775390625e-08;   // unit roundoff of T
+    // rounding term of the omega recurrence: the local error of one Lanczos step
+    // is dominated by the FFT matvec, whose error grows like log2 of the
+    // transform size (eps log2(M1 M2) ||K||, not eps ||K||)
+    const double eps_round = eps * std::log2((double)e->M1 * (double)e->M2);
 
     const int tb = 256;
     k_lanczos_init<<<(nvec + tb - 1) / tb, tb, 0, ctx->stream>>>(S, nvec, nsteps, 1.0 / sqrt((double)p));
@@ -600,20 +627,32 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
             k_lanczos_update<T, 1><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
         if (reorth) {
-            k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps);
+            k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps, eps_round);
             KRY_CHECK_LAUNCH();
             if (p % VW == 0)
                 k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
             else
                 k_reorth_dots<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
             KRY_CHECK_LAUNCH();
-            k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j);
-            KRY_CHECK_LAUNCH();
-            if (p % VW == 0)
-                k_reorth_apply<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
-            else
-                k_reorth_apply<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
-            KRY_CHECK_LAUNCH();
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    // second Gram-Schmidt pass for vectors that lost most of their norm
+                    k_reorth_again<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS);
+                    KRY_CHECK_LAUNCH();
+                    if (p % VW == 0)
+                        k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+                    else
+                        k_reorth_dots<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+                    KRY_CHECK_LAUNCH();
+                }
+                k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j);
+                KRY_CHECK_LAUNCH();
+                if (p % VW == 0)
+                    k_reorth_apply<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+                else
+                    k_reorth_apply<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+                KRY_CHECK_LAUNCH();
+            }
         }
         k_lanczos_beta<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
