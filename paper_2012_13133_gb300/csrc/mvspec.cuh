@@ -61,24 +61,34 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
     const float2 zero = make_float2(0.f, 0.f);
     const int tb = soff<PS, NT>(t);
 
-#pragma unroll
-    for (int i = 0; i < 8; ++i)   // positions t + i L/16 cover [0, L/2), which holds [0, n2)
-        if (t + i * LT < n2) sb[tb + soff<PS, NT>(i * LT)] = zero;
-    __syncthreads();
+    // The row's observed cells are loaded into registers first (a row holds at
+    // most n2 <= L/2 = 8 L/16 of them, so a fixed-trip predicated loop covers
+    // it), and their latency overlaps the zero fill.
+    int col[8];
+    float2 val[8];
     if (row < n1) {
         const float sa = scale ? (float)scale[va] : 1.f;
         const float sbv = (scale && has_b) ? (float)scale[vb] : 1.f;
         const float* pa = vin + (int64_t)va * ld;
         const float* pb = vin + (int64_t)vb * ld;
-        // a row holds at most n2 <= L/2 = 8 L/16 observed cells: a fixed-trip
-        // predicated loop lets every load of the row issue before the stores
         const int q0 = rowptr[row] + t, q1 = rowptr[row + 1];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int q = q0 + i * LT;
-            if (q < q1) sb[soff<PS, NT>(colidx[q])] = make_float2(pa[q] * sa, has_b ? pb[q] * sbv : 0.f);
+            col[i] = q < q1 ? colidx[q] : -1;
+            val[i] = q < q1 ? make_float2(pa[q] * sa, has_b ? pb[q] * sbv : 0.f) : zero;
         }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) col[i] = -1;
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)   // positions t + i L/16 cover [0, L/2), which holds [0, n2)
+        if (t + i * LT < n2) sb[tb + soff<PS, NT>(i * LT)] = zero;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (col[i] >= 0) sb[soff<PS, NT>(col[i])] = val[i];
     __syncthreads();
 
     // global store of output position p = t + c (c a multiple of L/16 >= C)
