@@ -63,17 +63,19 @@ def model_bytes_per_vector(n1, n2, M1, M2, p):
 
 
 def read_traffic():
-    """Measured DRAM bytes per real vector of the matvec from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+    """(DRAM bytes per real vector, batch width it was measured at) of the
+    matvec from the committed ncu summary, if it was taken on the current
+    kernel sources; None otherwise."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_real_vector:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_hash():
+    n = re.search(r"measured_vectors_per_launch:\s*([0-9]+)", txt)
+    if not m or not t or not n or m.group(1) != kernel_hash():
         return None
-    return float(t.group(1))
+    return float(t.group(1)), int(n.group(1))
 
 
 class ClockSampler:
@@ -284,11 +286,19 @@ def run_gpu(args, rank, world, local_rank):
     if prof32["calls"] > 0 and prof32["ms"] > 0:
         alg = bytes_vec * prof32["vectors"] + 4.0 * M1 * M2 * prof32["calls"]
         achieved = alg / (prof32["ms"] / 1000.0) / 1e9
-        traffic_vec = read_traffic()
+        measured = read_traffic()
         per_launch_vectors = prof32["vectors"] / prof32["calls"]
+        # ncu traffic per launch scaled to this run's mean batch: the per-vector
+        # part (slab, vectors, indices) grows with the batch, the eigenvalues
+        # are read once per launch
+        lam_bytes = 4.0 * M1 * M2
+        traffic = None
+        if measured is not None:
+            per_vec, nv_meas = measured
+            traffic = round((per_vec - lam_bytes / nv_meas) * per_launch_vectors + lam_bytes)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "traffic": (None if traffic_vec is None else round(traffic_vec * per_launch_vectors)),
+                "traffic": traffic,
                 "kernel": "FP32 3-pass FFT matvec (passes A+B+C of one call)",
                 "launches": prof32["calls"], "mean_vectors_per_launch": round(per_launch_vectors, 2),
                 "mean_launch_ms": round(prof32["ms"] / prof32["calls"], 4),
@@ -316,6 +326,7 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "gpu_launches": int(launches),
+        "library_launches_before_timed": int(launches0),
         "clocks": clk,
         "e2e": e2e,
         "wall_s": round(wall, 3),

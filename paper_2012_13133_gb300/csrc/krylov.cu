@@ -933,7 +933,11 @@ struct RcgState {
     int* nwant;       // [1] columns asking for a replacement (or done)
 };
 
-static const int CG_BLOCKS = 304;   // blocks per right-hand side of the CG vector kernels (2 per SM)
+// Blocks per right-hand side of the CG vector kernels: 304 (two per SM) for a
+// few right-hand sides, fewer for many, so that a batch keeps about 1216
+// blocks (a block then covers more elements instead of more blocks paying the
+// per-block reductions).
+static int cg_blocks(int nrhs) { return std::max(8, std::min(304, 1216 / std::max(1, nrhs))); }
 
 // r^T r buffer of parity par (a select, not an indexed load from the parameter struct)
 __device__ __forceinline__ double* rr_buf(const RcgState& S, int par) { return par ? S.rr[1] : S.rr[0]; }
@@ -990,8 +994,10 @@ __global__ void k_rcg_update(float* __restrict__ Xh, float* __restrict__ Xl, flo
                              const float* __restrict__ P, const float* __restrict__ Q, int64_t p, RcgState S,
                              const double* __restrict__ part_pq, int nblkC, double* __restrict__ part_rr, int par) {
     const int k = blockIdx.y;
-    const double a = rcg_alpha(S, part_pq, nblkC, k, par);
     if (k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *S.nwant = 0;
+    // finished columns keep x and r (their r^T r partials are never read)
+    if (S.done[k]) return;
+    const double a = rcg_alpha(S, part_pq, nblkC, k, par);
     const float af = (float)a;
     float ahi, alo;
     df_split(a, ahi, alo);
@@ -1042,6 +1048,7 @@ template <int VW>
 __global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S,
                               const double* __restrict__ part_rr, int nblk, int par, int maxit) {
     const int k = blockIdx.y;
+    if (S.done[k]) return;   // finished columns: no bookkeeping, P unchanged
     __shared__ double b_sh;
     const double s = block_sum(part_rr + (int64_t)k * nblk, nblk);
     if (threadIdx.x == 0) {
@@ -1113,7 +1120,8 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     float* Q = ctx->work[9].as<float>();
     const int nblkC = matvec_num_partials(ctx, e, false, nrhs);
     const int npq = std::max(nblkC, RED_BLOCKS);
-    ctx->work[10].ensure((size_t)nrhs * (npq + CG_BLOCKS) * sizeof(double));
+    const int nbc = cg_blocks(nrhs);
+    ctx->work[10].ensure((size_t)nrhs * (npq + nbc) * sizeof(double));
     double* part = ctx->work[10].as<double>();      // matvec partials (p^T K p), and the start's ||B||^2
     double* part_rr = part + (size_t)nrhs * npq;    // update partials (r^T r)
     ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);
@@ -1137,7 +1145,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     float* Xl = Xh + (size_t)nrhs * p;
 
     dim3 gv(RED_BLOCKS, nrhs);
-    dim3 gc(CG_BLOCKS, nrhs);
+    dim3 gc(nbc, nrhs);
     const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
     const bool vec = p % 4 == 0;   // 16-byte accesses: every column start is 16-byte aligned
     auto to_f64 = [&]() {
@@ -1163,9 +1171,9 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             k_rcg_update<1><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part, nblkC, part_rr, par);
         KRY_CHECK_LAUNCH();
         if (vec)
-            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, CG_BLOCKS, par, maxit);
+            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, nbc, par, maxit);
         else
-            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, CG_BLOCKS, par, maxit);
+            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, nbc, par, maxit);
         KRY_CHECK_LAUNCH();
     };
     // Iterations run in blocks of `poll` (an even count, so every block has the

@@ -1,0 +1,103 @@
+"""Timing driver for the workloads the benchmark does not time.
+
+  python -m paper_2012_13133_gb300.measure --workload search512   # batched vs one setting at a time
+  python -m paper_2012_13133_gb300.measure --workload large4096   # log-likelihood + kriging means, wall time
+  python -m paper_2012_13133_gb300.measure --workload tiny32      # FP64 evaluations per second
+
+Inputs are the seeded synthetic workloads of ``inputs.WORKLOADS``, resident on
+the device before timing; each timed call is bracketed by device
+synchronisation.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2012_13133_gb300 import inputs as I  # noqa: E402
+
+
+def problem(ctx, w, dev, prec_data=None):
+    import torch
+    mask = I.make_mask(w)
+    p = ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(dev))
+    S1, S2 = I.cell_centres(w.n1, w.n2)
+    X = I.covariates(S1[mask], S2[mask])
+    M1, M2, _ = ctx.sample_size(w.cov)
+    xi, eps = I.data_noise(M1, M2, p, w.data_seed)
+    field = ctx.sample(w.cov, M1, M2, torch.tensor(xi, device=dev)).cpu().numpy()
+    y = X @ np.array(w.beta) + field[mask] + math.sqrt(w.cov.tau2) * eps
+    return mask, p, torch.tensor(y, device=dev), torch.tensor(X.T.copy(), device=dev), S1, S2
+
+
+def timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t
+
+
+def main():
+    import torch
+
+    from paper_2012_13133_gb300 import kry
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32"])
+    args = ap.parse_args()
+    w = I.WORKLOADS[args.workload]
+    dev = torch.device("cuda:0")
+    ctx = kry.Context(0)
+    mask, p, y, X, S1, S2 = problem(ctx, w, dev)
+    out = {"workload": args.workload, "grid": [w.n1, w.n2], "p": p}
+    if args.workload == "search512":
+        thetas = [I.Cov(1.0, r, nu, w.cov.tau2) for r in w.extra["ranges"] for nu in w.extra["nus"]]
+        opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,
+                        maxit=30000, reorth=w.reorth)
+        ctx.profile_loglik(y, X, thetas[:2], opts)                       # warm-up
+        batch, tb = timed(lambda: ctx.profile_loglik(y, X, thetas, opts))
+        singles, ts = timed(lambda: [ctx.profile_loglik(y, X, [t], opts) for t in thetas])
+        diff = max(abs(batch["loglik"][k] - s["loglik"][0]) / abs(s["loglik"][0]) for k, s in enumerate(singles))
+        best = int(np.argmax(batch["loglik"]))
+        out.update({"settings": len(thetas), "probes": w.nprobe, "lanczos_steps": w.nsteps,
+                    "batched_s": tb, "one_at_a_time_s": ts, "batched_evals_per_s": len(thetas) / tb,
+                    "one_at_a_time_evals_per_s": len(thetas) / ts, "max_rel_loglik_diff": diff,
+                    "best_setting": {"range": thetas[best].range, "nu": thetas[best].nu},
+                    "status": int(batch["status"])})
+    elif args.workload == "large4096":
+        opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,
+                        maxit=60000, reorth=w.reorth)
+        cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+        Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+        ct, xt = torch.tensor(cells, device=dev), torch.tensor(Xc.T.copy(), device=dev)
+        emb = ctx.embed(w.cov, kry.KRY_F32)
+        tuned = {str(nv): ctx.autotune(emb, nv) for nv in (w.nprobe, 4)}
+        emb.free()
+        res, t = timed(lambda: ctx.loglik_krige(w.cov, opts, y, X, cells=ct, Xc=xt))
+        out.update({"probes": w.nprobe, "lanczos_steps": w.nsteps, "kriging_cells": int(cells.size),
+                    "loglik_krige_s": t, "loglik": res["loglik"], "status": int(res["status"]),
+                    "tuned_schedules": tuned})
+    else:
+        opts = kry.Opts(prec=kry.KRY_F64, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,
+                        maxit=20000, reorth=w.reorth)
+        ctx.profile_loglik(y, X, [w.cov], opts)
+        n = 20
+        _, t = timed(lambda: [ctx.profile_loglik(y, X, [w.cov], opts) for _ in range(n)])
+        out.update({"evals_per_s": n / t, "precision": "f64"})
+    ctx.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
