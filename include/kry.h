@@ -153,9 +153,11 @@ kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_de
  * quadrature ||z||^2 sum_j tau_j^2 log theta_j of the tridiagonal.
  * reorth = 0: plain three-term recurrence (the paper's runs, Sec. 3.2).
  * reorth = 1: partial reorthogonalisation (Simon 1984): per probe, estimates
- * of the basis' loss of orthogonality are carried by a scalar recurrence and,
+ * of the basis' loss of orthogonality are carried by a scalar recurrence whose
+ * rounding term is that of the FFT matvec (unit roundoff x log2(M1 M2)) and,
  * when one exceeds sqrt(unit roundoff) of the embedding's precision, the new
- * basis vector and the next are orthogonalised against all earlier ones; the
+ * basis vector and the next are orthogonalised against all earlier ones (a
+ * second Gram-Schmidt pass when the first cancels most of the vector); the
  * result then follows the exact-arithmetic Gauss rule, which the plain FP32
  * recurrence misses by ~1e-3 on ill-conditioned K.  *logdet = mean over
  * probes, *stderr_out = standard error (NULL allowed), per_probe[nprobe] the
