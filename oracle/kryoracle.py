@@ -412,6 +412,97 @@ class FFTProblem:
 
 
 # --------------------------------------------------------------------------------------
+# BCCB log-determinant approximation (Sec. 3.3) and its range derivative (Appendix A,
+# Eq. circ_diag and Eq. trace_approx)
+# --------------------------------------------------------------------------------------
+
+
+def matern_dr(r, nu):
+    """d/dr of the Matern correlation rho_nu(r) (Sec. 2).  Closed forms for nu = 1/2, 3/2,
+    5/2 (x = sqrt(2 nu) r: -e^-x; -sqrt(3) x e^-x; -sqrt(5) x (1 + x) e^-x / 3); otherwise
+    d/dx [x^nu K_nu(x)] = -x^nu K_{nu-1}(x) (DLMF 10.29.4) gives
+    -2^(1-nu)/Gamma(nu) sqrt(2 nu) x^nu K_{nu-1}(x)."""
+    r = np.asarray(r, dtype=np.float64)
+    s = math.sqrt(2.0 * nu)
+    x = s * r
+    if nu == 0.5:
+        return -np.exp(-x)
+    if nu == 1.5:
+        return -s * x * np.exp(-x)
+    if nu == 2.5:
+        return -s * x * (1.0 + x) * np.exp(-x) / 3.0
+    out = np.zeros_like(x)
+    pos = x > 0
+    xp = x[pos]
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        val = -(2.0 ** (1.0 - nu) / scipy.special.gamma(nu)) * s * xp ** nu * scipy.special.kv(nu - 1.0, xp)
+    out[pos] = np.where(np.isfinite(val), val, 0.0)
+    if nu < 0.5:
+        out[~pos] = -np.inf
+    elif nu == 0.5:
+        out[~pos] = -1.0
+    return out
+
+
+def covariance_drange(h1, h2, cov):
+    """d/d(range) of sigma^2 rho(d / range): with r = d / range, dr / d(range) = -r / range."""
+    r = scaled_distance(h1, h2, cov)
+    return cov.sigma2 * matern_dr(r, cov.nu) * (-r / cov.range)
+
+
+def _torus_first_row(n1, n2, M1, M2, cov, fn):
+    """First row of the block-circulant extension on an M1 x M2 torus of the BTTB matrix with
+    entries fn(lag): minimal-image lags, the two images of a lag of exactly M/2 averaged
+    (no such lag on an odd torus)."""
+    def images(M):
+        j = np.arange(M)
+        a = np.where(2 * j <= M, j, j - M)
+        b = np.where(2 * j < M, j, j - M)
+        return a.astype(np.float64), b.astype(np.float64)
+    a1, b1 = images(M1)
+    a2, b2 = images(M2)
+    c = np.zeros((M1, M2))
+    for l1 in (a1, b1):
+        for l2 in (a2, b2):
+            c += fn(l1[:, None] / n1, l2[None, :] / n2, cov)
+    return 0.25 * c
+
+
+def bccb_logdet(n1, n2, cov, reading="scaled", floor_rel=2.220446049250313e-16):
+    """Approximate log det Sigma(theta) of the n1 x n2 BTTB covariance (no nugget) and its
+    derivative dL with respect to the range, from the eigenvalues D1 of a block-circulant
+    extension and D2 of the extension of d Sigma / d(range) (Eq. circ_diag): log det ~ sum
+    log D1, dL ~ sum D2 / D1 (Eq. trace_approx).  Readings of Sec. 3.3's formula:
+
+      "literal": the paper's (2 n1 - 1) x (2 n2 - 1) extension, frequencies p < n1, q < n2
+                 (the formula's sums over p = 1..n1, q = 1..n2 with omega = exp(-2 pi i/(2n-1)));
+      "scaled":  the matvec's power-of-two M1 x M2 extension, all frequencies, scaled by
+                 n1 n2 / (M1 M2).
+
+    Eigenvalues below floor_rel * max are reset to that value before the log (the
+    "forcefully resetting" recourse of Sec. 3.6) and contribute no derivative term.
+    Returns (logdet, dL)."""
+    N = n1 * n2
+    if reading == "literal":
+        M1, M2 = 2 * n1 - 1, 2 * n2 - 1
+    elif reading == "scaled":
+        M1, M2 = embed_size(n1), embed_size(n2)
+    else:
+        raise ValueError(reading)
+    d1 = scipy.fft.fft2(_torus_first_row(n1, n2, M1, M2, cov, covariance), workers=_WORKERS).real
+    d2 = scipy.fft.fft2(_torus_first_row(n1, n2, M1, M2, cov, covariance_drange), workers=_WORKERS).real
+    if reading == "literal":
+        d1, d2, scale = d1[:n1, :n2], d2[:n1, :n2], 1.0
+    else:
+        scale = N / float(M1 * M2)
+    f = floor_rel * float(d1.max())
+    keep = d1 > f
+    ld = scale * float(np.sum(np.log(np.where(keep, d1, f))))
+    dl = scale * float(np.sum(np.where(keep, d2 / np.where(keep, d1, 1.0), 0.0)))
+    return ld, dl
+
+
+# --------------------------------------------------------------------------------------
 # Circulant-embedding sampling (bootstrap of Sec. 3.5; negative-eigenvalue caveat of Sec. 3.6)
 # --------------------------------------------------------------------------------------
 

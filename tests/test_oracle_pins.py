@@ -404,3 +404,70 @@ def test_sample_embed_size_grows_until_psd():
     assert M1 > 2 * n
     lam2, _ = O.embedding_eigs(O.lag_covariance(n, n, M1, M2, cov))
     assert lam2.min() >= -1e-10 * lam2.max()
+
+
+# ---------------------------------------------------------------- BCCB log-determinant (Sec. 3.3, Appendix A)
+
+@pytest.mark.parametrize("nu", [0.5, 1.0, 1.5, 2.5, 0.8, 3.3])
+def test_matern_range_derivative_matches_difference_quotients(nu):
+    r = np.linspace(0.01, 3.0, 9)
+    h = 1e-6
+    fd = (O.matern(r + h, nu) - O.matern(r - h, nu)) / (2 * h)
+    assert np.max(np.abs(fd - O.matern_dr(r, nu))) <= 1e-8
+    cov = I.Cov(1.7, 0.2, nu, 0.0, angle=0.4, ratio=1.5)
+    h1, h2 = np.array([0.05, 0.3, 0.0]), np.array([0.1, -0.2, 0.07])
+    hr = 1e-7
+    fd = (O.covariance(h1, h2, I.Cov(1.7, 0.2 + hr, nu, 0.0, angle=0.4, ratio=1.5)) -
+          O.covariance(h1, h2, I.Cov(1.7, 0.2 - hr, nu, 0.0, angle=0.4, ratio=1.5))) / (2 * hr)
+    assert np.allclose(fd, O.covariance_drange(h1, h2, cov), rtol=1e-6, atol=1e-9)
+
+
+def test_bccb_eigenvalues_give_exact_logdet_and_trace_of_the_circulant():
+    """Eq. circ_diag: a BCCB matrix is diagonalised by the 2-D Fourier matrix, so its log
+    determinant is the sum of log D1 and trace(C^-1 dC) = sum D2 / D1 (Eq. trace_approx),
+    exactly; checked against the dense circulant."""
+    M1, M2 = 8, 16
+    cov = I.Cov(1.3, 0.2, 1.0, 0.0, angle=0.5, ratio=2.0)
+    c = O._torus_first_row(4, 8, M1, M2, cov, O.covariance)
+    dc = O._torus_first_row(4, 8, M1, M2, cov, O.covariance_drange)
+    i1, i2 = (a.ravel() for a in np.meshgrid(np.arange(M1), np.arange(M2), indexing="ij"))
+    C = c[(i1[:, None] - i1[None, :]) % M1, (i2[:, None] - i2[None, :]) % M2]
+    dC = dc[(i1[:, None] - i1[None, :]) % M1, (i2[:, None] - i2[None, :]) % M2]
+    d1, d2 = np.fft.fft2(c).real, np.fft.fft2(dc).real
+    sign, logabs = np.linalg.slogdet(C)
+    assert sign > 0 and np.sum(np.log(d1)) == pytest.approx(logabs, rel=1e-12)
+    assert np.sum(d2 / d1) == pytest.approx(np.trace(np.linalg.solve(C, dC)), rel=1e-10)
+
+
+@pytest.mark.parametrize("reading", ["literal", "scaled"])
+def test_bccb_logdet_white_noise_limit_is_exact(reading):
+    """A range far below the cell spacing makes Sigma = sigma^2 I: both readings give
+    n log sigma^2 and a zero range derivative."""
+    n1, n2, s2 = 12, 10, 2.5
+    ld, dl = O.bccb_logdet(n1, n2, I.Cov(s2, 1e-9, 0.5, 0.0), reading)
+    assert ld == pytest.approx(n1 * n2 * math.log(s2), rel=1e-12)
+    assert abs(dl) <= 1e-9
+
+
+@pytest.mark.parametrize("reading", ["literal", "scaled"])
+def test_bccb_range_derivative_is_the_derivative_of_the_logdet(reading):
+    base = dict(sigma2=1.0, nu=1.3, tau2=0.0, angle=0.3, ratio=1.5)
+    rng, h = 0.12, 1e-5
+    lp = O.bccb_logdet(24, 20, I.Cov(range=rng + h, **base), reading)[0]
+    lm = O.bccb_logdet(24, 20, I.Cov(range=rng - h, **base), reading)[0]
+    dl = O.bccb_logdet(24, 20, I.Cov(range=rng, **base), reading)[1]
+    assert dl == pytest.approx((lp - lm) / (2 * h), rel=1e-6)
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5])
+@pytest.mark.parametrize("reading", ["literal", "scaled"])
+def test_bccb_logdet_error_shrinks_as_the_grid_grows(nu, reading):
+    """The approximation is exact only asymptotically (Sec. 3.3, after Kent & Mardia 1996):
+    with the range fixed in cells, the relative error against the dense log det falls as the
+    grid grows."""
+    errs = []
+    for n in (8, 16, 32):
+        cov = I.Cov(1.0, 4.0 / n, nu, 0.0)
+        exact = np.linalg.slogdet(O.dense_K(n, n, np.ones((n, n), bool), cov))[1]
+        errs.append(abs(O.bccb_logdet(n, n, cov, reading)[0] - exact) / abs(exact))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.025
