@@ -235,6 +235,25 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
 kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
                       const double* xi_dev, double* out_dev);
 
+/* BCCB approximation of the log-determinant of the latent covariance
+ * Sigma(theta) on the n1 x n2 grid of the last kry_set_mask (Sec. 3.3,
+ * "Log-determinant approximation"), and of its derivative with respect to the
+ * range (Appendix A, Eq. circ_diag and Eq. trace_approx):
+ *   *logdet = (n1 n2 / (M1 M2)) sum_k log D1_k,
+ *   *dlogdet_drange = (n1 n2 / (M1 M2)) sum_k D2_k / D1_k,
+ * D1 and D2 the eigenvalues (2-D FFT of the first row) of the block-circulant
+ * extensions of Sigma and d Sigma / d(range) on the matvec's M1 x M2 torus
+ * (M_d the smallest power of two >= 2 n_d; the paper's formula uses a
+ * (2 n_d - 1)-point extension and its first n1 x n2 frequencies, a reading
+ * this build does not take because that length is not a power of two).
+ * sigma2, range, nu and anisotropy come from cov; its nugget tau2 is not part
+ * of Sigma and is ignored.  Eigenvalues below 2^-52 max D1 are reset to that
+ * value before the log (the Sec. 3.6 recourse) and add no derivative term.
+ * FP64 throughout.  dlogdet_drange may be NULL (no derivative computed).
+ * Errors: KRY_EINVAL without a mask or for bad cov; KRY_ENAN for a non-finite
+ * result.  Synchronises the stream. */
+kry_status kry_bccb_logdet(kry_ctx* ctx, const kry_cov* cov, double* logdet, double* dlogdet_drange);
+
 /* Smallest torus for kry_sample: starting from M_d = smallest power of two
  * >= 2 n_d, doubles both sides (at most 3 times, never past 8192) until
  * min(Lambda) >= -1e-10 max(Lambda).  Returns KRY_ENOTPSD with the largest

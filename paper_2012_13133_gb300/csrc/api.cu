@@ -99,7 +99,7 @@ namespace kry {
 void ctx_trim(kry_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+    DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
                       &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
@@ -333,7 +333,7 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         // every scratch buffer is stream-ordered on the context stream; keep freed
         // pool memory cached in this process instead of returning it at each sync
         DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
-                          &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+                          &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
                           &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
         for (DevBuf* b : bufs) b->stream = ctx->stream;
         for (auto& b : ctx->work) b.stream = ctx->stream;
@@ -363,7 +363,7 @@ void kry_destroy(kry_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
-                      &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->red, &ctx->tolbuf,
+                      &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
                       &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
@@ -771,6 +771,20 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2, 
                         (M1 & (M1 - 1)) == 0 && (M2 & (M2 - 1)) == 0,
                     KRY_EINVAL, "M1, M2 must be powers of two with 2 n_d <= M_d <= 8192");
         kry::sample_field(ctx, *cov, M1, M2, xi_dev, out_dev);
+        return KRY_OK;
+    });
+}
+
+kry_status kry_bccb_logdet(kry_ctx* ctx, const kry_cov* cov, double* logdet, double* dlogdet_drange) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_cov(cov);
+        require_mask(ctx);
+        KRY_REQUIRE(logdet != nullptr, KRY_EINVAL, "logdet must not be NULL");
+        KRY_REQUIRE(2 * (int64_t)ctx->n1 <= KRY_MAX_M && 2 * (int64_t)ctx->n2 <= KRY_MAX_M, KRY_EUNSUPPORTED,
+                    "grid too large for the embedding");
+        kry::bccb_logdet(ctx, *cov, dlogdet_drange != nullptr, logdet, dlogdet_drange);
+        if (!isfinite(*logdet) || (dlogdet_drange && !isfinite(*dlogdet_drange)))
+            return fail(ctx, KRY_ENAN, "BCCB log-determinant is NaN/Inf");
         return KRY_OK;
     });
 }

@@ -50,6 +50,21 @@ __device__ __forceinline__ double cov_at(const CovDev& p, double l1, double l2) 
     return p.sigma2 * kry_matern(r, p.nu);
 }
 
+// d/d(range) of sigma^2 rho(d / range): with r = d / range, dr / d(range) = -r / range.
+__device__ __forceinline__ double cov_drange_at(const CovDev& p, double l1, double l2) {
+    const double r = kry_scaled_dist(l1 * p.dx1, l2 * p.dx2, p.ca, p.sa, p.ratio, p.inv_range);
+    if (r <= 0.0) return 0.0;
+    return p.sigma2 * kry_matern_dr(r, p.nu) * (-r * p.inv_range);
+}
+
+template <bool DRANGE>
+__device__ __forceinline__ double lag_entry(const CovDev& p, double l1, double l2) {
+    return DRANGE ? cov_drange_at(p, l1, l2) : cov_at(p, l1, l2);
+}
+
+// First row of the block-circulant extension of the covariance (DRANGE: of
+// its range derivative) on the M1 x M2 torus.
+template <bool DRANGE = false>
 __global__ void k_lag_cov(double* __restrict__ c, int M1, int M2, CovDev p) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)M1 * M2) return;
@@ -61,13 +76,14 @@ __global__ void k_lag_cov(double* __restrict__ c, int M1, int M2, CovDev p) {
     const int b2 = (2 * j2 < M2) ? j2 : j2 - M2;
     double v;
     if (a1 == b1 && a2 == b2) {
-        v = cov_at(p, a1, a2);
+        v = lag_entry<DRANGE>(p, a1, a2);
     } else if (a1 == b1) {
-        v = 0.5 * (cov_at(p, a1, a2) + cov_at(p, a1, b2));
+        v = 0.5 * (lag_entry<DRANGE>(p, a1, a2) + lag_entry<DRANGE>(p, a1, b2));
     } else if (a2 == b2) {
-        v = 0.5 * (cov_at(p, a1, a2) + cov_at(p, b1, a2));
+        v = 0.5 * (lag_entry<DRANGE>(p, a1, a2) + lag_entry<DRANGE>(p, b1, a2));
     } else {
-        v = 0.25 * (cov_at(p, a1, a2) + cov_at(p, a1, b2) + cov_at(p, b1, a2) + cov_at(p, b1, b2));
+        v = 0.25 * (lag_entry<DRANGE>(p, a1, a2) + lag_entry<DRANGE>(p, a1, b2) + lag_entry<DRANGE>(p, b1, a2) +
+                    lag_entry<DRANGE>(p, b1, b2));
     }
     c[idx] = v;
 }
@@ -269,6 +285,88 @@ void compute_eigs(kry_ctx* ctx, const kry_cov& cov, int n1, int n2, double dx1, 
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));
     *lam_min = ctx->host_pinned[0];
     *lam_max = ctx->host_pinned[1];
+}
+
+// ------------------------------------------------------------------ BCCB log-determinant
+//
+// Sec. 3.3's approximation log det Sigma ~ sum log D1 and its range
+// derivative dL ~ sum D2 / D1 (Appendix A, Eq. circ_diag and Eq.
+// trace_approx), D1 and D2 the eigenvalues of the block-circulant extensions
+// of Sigma and d Sigma / d(range).  Reading: the matvec's power-of-two
+// M1 x M2 torus, all frequencies, scaled by n1 n2 / (M1 M2) (the paper's
+// (2n - 1)-point extension is not a power of two).  Eigenvalues below
+// eps * max D1 are reset to that value (Sec. 3.6) and add no derivative term.
+
+// Per-block sums of log(max(D1, floor)) and, where D1 > floor, D2 / D1.
+__global__ void k_bccb_partials(const double* __restrict__ d1, const double* __restrict__ d2, int64_t n,
+                                double floor_v, double* __restrict__ part) {
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double l = d1[i];
+        const bool keep = l > floor_v;
+        a += log(keep ? l : floor_v);
+        if (keep && d2) b += d2[i] / l;
+    }
+    __shared__ double sa[256], sb[256];
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sa[threadIdx.x] += sa[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sa[0];
+        part[2 * blockIdx.x + 1] = sb[0];
+    }
+}
+
+__global__ void k_bccb_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    out[0] = a;
+    out[1] = b;
+}
+
+void bccb_logdet(kry_ctx* ctx, const kry_cov& cov, bool deriv, double* logdet, double* dlogdet) {
+    const int n1 = ctx->n1, n2 = ctx->n2;
+    int M1 = 1, M2 = 1;
+    while (M1 < 2 * n1) M1 <<= 1;
+    while (M2 < 2 * n2) M2 <<= 1;
+    const int64_t MM = (int64_t)M1 * M2;
+    double lo, hi;
+    compute_eigs(ctx, cov, n1, n2, ctx->dx1, ctx->dx2, M1, M2, &lo, &hi);   // D1 in eig_c
+    double* d1 = ctx->eig_c.as<double>();
+    double* d2 = nullptr;
+    if (deriv) {
+        ctx->eig_d.ensure(MM * sizeof(double));
+        d2 = ctx->eig_d.as<double>();
+        k_lag_cov<true><<<(unsigned)((MM + 255) / 256), 256, 0, ctx->stream>>>(d2, M1, M2,
+                                                                            cov_dev(cov, ctx->dx1, ctx->dx2));
+        KRY_CHECK_LAUNCH();
+        double2* z = ctx->eig_z.as<double2>();
+        launch_rows_full<0>(ctx, d2, nullptr, 0.0, z, M1, M2);
+        launch_cols_full<0>(ctx, z, d2, M1, M2, 0, 0);   // D2 (real part) back into d2
+    }
+    const int nb = 256;
+    ctx->red.ensure((2 * nb + 2) * sizeof(double));
+    double* part = ctx->red.as<double>();
+    k_bccb_partials<<<nb, 256, 0, ctx->stream>>>(d1, d2, MM, 2.220446049250313e-16 * hi, part);
+    KRY_CHECK_LAUNCH();
+    k_bccb_final<<<1, 1, 0, ctx->stream>>>(part, nb, part + 2 * nb);
+    KRY_CHECK_LAUNCH();
+    KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, part + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    const double scale = (double)n1 * (double)n2 / (double)MM;
+    *logdet = scale * ctx->host_pinned[0];
+    if (dlogdet) *dlogdet = scale * ctx->host_pinned[1];
 }
 
 // lamT[j][k] = lam[k][j] * scale (FP64 and optionally FP32), 32 x 32 tiles.

@@ -110,7 +110,7 @@ struct kry_ctx {
     DevBuf slab32, slab64;        // FFT intermediates
     DevBuf work[13];              // Krylov vectors and partials
     DevBuf scal;                  // FP64 Krylov scalars
-    DevBuf eig_c, eig_z;          // eigenvalue computation
+    DevBuf eig_c, eig_z, eig_d;   // eigenvalue computation (eig_d: derivative eigenvalues)
     DevBuf red;                   // reduction partials
     DevBuf tolbuf, kxbuf;         // CG tolerances, FP64 residual matvec output
     DevBuf cbuf, sbuf;            // kriging-variance right-hand sides and solutions
@@ -190,6 +190,10 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
                      int64_t ld, int vpt = 0);
 
 void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out);
+
+// BCCB approximation of log det Sigma (no nugget) on the mask's grid and, if
+// deriv, of its range derivative (Sec. 3.3, Appendix A).
+void bccb_logdet(kry_ctx* ctx, const kry_cov& cov, bool deriv, double* logdet, double* dlogdet);
 
 int smem_limit(kry_ctx* ctx);
 

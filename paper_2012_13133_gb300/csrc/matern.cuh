@@ -41,6 +41,20 @@ __device__ __forceinline__ double kry_matern(double r, double nu) {
     return exp(lpre) * kry_besselk_trap(nu, x);
 }
 
+// d rho_nu / dr (Sec. 2).  Closed forms for nu = 1/2, 3/2, 5/2; otherwise
+// d/dx [x^nu K_nu(x)] = -x^nu K_{nu-1}(x) (DLMF 10.29.4) with K_{nu-1} = K_{|nu-1|}
+// (K is even in its order), evaluated by the same trapezoidal rule.
+__device__ __forceinline__ double kry_matern_dr(double r, double nu) {
+    const double s = sqrt(2.0 * nu);
+    const double x = s * r;
+    if (nu == 0.5) return -exp(-x);
+    if (nu == 1.5) return -s * x * exp(-x);
+    if (nu == 2.5) return -s * x * (1.0 + x) * exp(-x) * (1.0 / 3.0);
+    if (x <= 0.0 || x > 745.0) return 0.0;
+    const double lpre = (1.0 - nu) * 0.69314718055994530942 - lgamma(nu) + nu * log(x);
+    return -s * exp(lpre) * kry_besselk_trap(fabs(nu - 1.0), x);
+}
+
 // Scaled lag d / range under geometric anisotropy: rotate by angle (ca, sa),
 // stretch the minor axis by ratio.
 __device__ __forceinline__ double kry_scaled_dist(double h1, double h2, double ca, double sa, double ratio,

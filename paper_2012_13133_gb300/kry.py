@@ -89,6 +89,7 @@ SIGNATURES = {
     "kry_profile_enable": (C.c_int, [_P, C.c_int]),
     "kry_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _DP]),
     "kry_launch_count": (C.c_uint64, []),
+    "kry_bccb_logdet": (C.c_int, [_P, C.POINTER(kry_cov), _DP, _DP]),
 }
 
 
@@ -339,6 +340,14 @@ class Context:
         out = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=xi.device)
         self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, _ptr(xi.contiguous()), _ptr(out)))
         return out
+
+    def bccb_logdet(self, cov, derivative=True):
+        """BCCB approximation of log det Sigma (no nugget) on the mask's grid and its range
+        derivative (None when derivative=False)."""
+        ld, dl = C.c_double(), C.c_double()
+        self._check(_lib.kry_bccb_logdet(self.h, C.byref(make_cov(cov)), C.byref(ld),
+                                         C.byref(dl) if derivative else None))
+        return ld.value, (dl.value if derivative else None)
 
 
 def _np_ptr(a):

@@ -3,6 +3,7 @@
   python -m paper_2012_13133_gb300.measure --workload search512   # batched vs one setting at a time
   python -m paper_2012_13133_gb300.measure --workload large4096   # log-likelihood + kriging means, wall time
   python -m paper_2012_13133_gb300.measure --workload tiny32      # FP64 evaluations per second
+  python -m paper_2012_13133_gb300.measure --workload grid1024 --bccb   # BCCB log-det + derivative
 
 Inputs are the seeded synthetic workloads of ``inputs.WORKLOADS``, resident on
 the device before timing; each timed call is bracketed by device
@@ -54,14 +55,22 @@ def main():
     from paper_2012_13133_gb300 import kry
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32"])
+    ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32", "grid1024"])
+    ap.add_argument("--bccb", action="store_true", help="time the BCCB log-det and its range derivative")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
     ctx = kry.Context(0)
     mask, p, y, X, S1, S2 = problem(ctx, w, dev)
     out = {"workload": args.workload, "grid": [w.n1, w.n2], "p": p}
-    if args.workload == "search512":
+    if args.bccb:
+        ctx.bccb_logdet(w.cov)
+        reps = 5
+        (ld, dl), t = timed(lambda: [ctx.bccb_logdet(w.cov) for _ in range(reps)][-1])
+        out.update({"bccb_logdet": ld, "bccb_dlogdet_drange": dl, "ms_per_call": 1e3 * t / reps})
+    elif args.workload == "grid1024":
+        raise SystemExit("grid1024 is timed by bench.py; use --bccb here")
+    elif args.workload == "search512":
         thetas = [I.Cov(1.0, r, nu, w.cov.tau2) for r in w.extra["ranges"] for nu in w.extra["nus"]]
         opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,
                         maxit=30000, reorth=w.reorth)

@@ -99,3 +99,11 @@ def test_loglik_krige_assembles_its_parts_at_full_size(problem):
     mc = res["mean_cells"].cpu().numpy()
     assert np.all(np.isfinite(mc)) and mc.shape == (cells.size,)
     emb.free()
+
+
+def test_bccb_logdet_at_full_size(problem):
+    """BCCB log-det and range derivative of the grid1024 covariance (2048^2 torus) vs the oracle."""
+    ld, dl = problem["ctx"].bccb_logdet(W.cov)
+    ref_ld, ref_dl = O.bccb_logdet(W.n1, W.n2, W.cov, "scaled")
+    assert ld == pytest.approx(ref_ld, rel=1e-9)
+    assert dl == pytest.approx(ref_dl, rel=1e-7)

@@ -459,3 +459,23 @@ def test_argument_errors(ctx):
     emb = ctx.embed(I.Cov(1.0, 0.1, 1.5, 0.01), kry.KRY_F64)
     X, iters, relres, st = ctx.solve(emb, torch.ones((1, p), dtype=torch.float64, device=DEV), rtol=1e-12, maxit=1)
     assert st == kry.KRY_ENOCONV and relres > 1e-12 and torch.isfinite(X).all()
+
+
+@pytest.mark.parametrize("n1,n2,cov", [
+    (32, 32, I.Cov(1.0, 0.1, 0.5, 0.1)),
+    (37, 53, I.Cov(2.0, 0.15, 1.5, 0.05)),
+    (50, 70, I.Cov(1.0, 0.08, 0.5, 0.05, angle=math.radians(30), ratio=3.0)),
+    (64, 40, I.Cov(1.0, 0.1, 1.0, 0.2)),                     # general nu: Bessel K_nu and K_{nu-1}
+    (48, 48, I.Cov(1.3, 0.12, 2.5, 0.0)),
+    (6, 5, I.Cov(0.7, 0.3, 0.8, 0.0, angle=0.2, ratio=1.7)),
+])
+def test_bccb_logdet_matches_oracle(ctx, n1, n2, cov):
+    """BCCB log-det of Sigma and its range derivative (Sec. 3.3, Appendix A), scaled reading on
+    the power-of-two torus, against the FP64 oracle."""
+    set_mask(ctx, make_mask(n1, n2, 0.3, "uniform"))
+    ld, dl = ctx.bccb_logdet(cov)
+    ref_ld, ref_dl = O.bccb_logdet(n1, n2, cov, "scaled")
+    assert ld == pytest.approx(ref_ld, rel=1e-9)
+    assert dl == pytest.approx(ref_dl, rel=1e-7)
+    ld2, none = ctx.bccb_logdet(cov, derivative=False)
+    assert ld2 == ld and none is None

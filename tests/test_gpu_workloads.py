@@ -201,3 +201,11 @@ def test_large4096_probe_quadrature_matches_oracle(large):
     P = O.FFTProblem(W5.n1, W5.n2, large["mask"], W5.cov)
     _, _, ref = P.logdet(W5.nprobe, W5.nsteps, W5.probe_seed, probe_ids=[0], reorth=True)
     assert per[0] == pytest.approx(ref[0], rel=1e-3)
+
+
+def test_large4096_bccb_logdet_matches_oracle(large):
+    """BCCB log-det and range derivative on the 8192^2 torus (anisotropic exponential)."""
+    ld, dl = large["ctx"].bccb_logdet(W5.cov)
+    ref_ld, ref_dl = O.bccb_logdet(W5.n1, W5.n2, W5.cov, "scaled")
+    assert ld == pytest.approx(ref_ld, rel=1e-9)
+    assert dl == pytest.approx(ref_dl, rel=1e-7)
