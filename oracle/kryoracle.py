@@ -529,6 +529,29 @@ def sample_field(n1, n2, M1, M2, cov, xi):
     return scipy.fft.fft2(z, workers=_WORKERS).real[:n1, :n2]
 
 
+def bootstrap_kriging_variance(n1, n2, mask, cov, targets, xis, epss):
+    """Parametric-bootstrap MSE of the kriging prediction of x at grid cells ``targets`` (flat
+    row-major indices), theta and beta known (Sec. 3.5, Eq. bootstrap_uq): replicate b draws
+    x_b from the white noise xis[b] with the circulant-embedding sampler, forms
+    y_b - X beta = A x_b + tau eps_b (epss[b]: p standard normals), predicts
+    x_hat_b = sigma^2 Sigma_{t,o} K^-1 (y_b - X beta) and the estimate is
+    mean_b (x_b(t) - x_hat_b(t))^2.  The MSE of y at a target adds tau^2 (its nugget noise is
+    independent of everything else)."""
+    mask = np.asarray(mask, bool)
+    M1, M2 = xis.shape[-2:]
+    K = dense_K(n1, n2, mask, cov)
+    L = scipy.linalg.cho_factor(K, lower=True)
+    S1, S2 = coords(n1, n2)
+    t_sites = np.stack([S1.ravel()[targets], S2.ravel()[targets]], axis=1)
+    C = dense_sigma(t_sites, observed_sites(n1, n2, mask), cov)        # (m, p)
+    acc = np.zeros(len(targets))
+    for xi, eps in zip(xis, epss):
+        x = sample_field(n1, n2, M1, M2, cov, xi)
+        w = scipy.linalg.cho_solve(L, x[mask] + math.sqrt(cov.tau2) * eps)
+        acc += (x.ravel()[targets] - C @ w) ** 2
+    return acc / len(xis)
+
+
 def make_data(n1, n2, mask, cov, beta, xi, eps):
     """y = X beta + x(obs) + tau eps with x the circulant-embedding GP sample of
     white noise ``xi`` (shape (2, M1, M2); Eq. obs_mod with A = row selection).

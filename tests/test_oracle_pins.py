@@ -471,3 +471,28 @@ def test_bccb_logdet_error_shrinks_as_the_grid_grows(nu, reading):
         exact = np.linalg.slogdet(O.dense_K(n, n, np.ones((n, n), bool), cov))[1]
         errs.append(abs(O.bccb_logdet(n, n, cov, reading)[0] - exact) / abs(exact))
     assert errs[2] < errs[1] < errs[0] and errs[2] < 0.025
+
+
+# ---------------------------------------------------------------- parametric bootstrap (Sec. 3.5)
+
+def test_bootstrap_variance_converges_to_the_kriging_variance():
+    """Eq. bootstrap_uq estimates the classical kriging variance: E (x(t) - x_hat(t))^2 =
+    sigma^2 - c_t^T K^-1 c_t for the simple-kriging predictor.  With many replicates the
+    bootstrap MSE is within a few standard errors (relative SE sqrt(2 / B)) of it."""
+    n1, n2 = 12, 10
+    cov = I.Cov(1.0, 0.2, 1.5, 0.1)
+    mask = I.mask_uniform(n1, n2, 0.3, 4)
+    targets = np.flatnonzero(~mask.ravel())
+    M1, M2 = O.sample_embed_size(n1, n2, cov)
+    B = 4000
+    rng = np.random.default_rng(11)
+    xis = rng.standard_normal((B, 2, M1, M2))
+    epss = rng.standard_normal((B, int(mask.sum())))
+    boot = O.bootstrap_kriging_variance(n1, n2, mask, cov, targets, xis, epss)
+    S1, S2 = O.coords(n1, n2)
+    t_sites = np.stack([S1.ravel()[targets], S2.ravel()[targets]], axis=1)
+    y = np.zeros(int(mask.sum()))
+    X = np.ones((y.size, 1))
+    _, exact = O.krige_dense(n1, n2, mask, cov, y, X, t_sites, np.ones((len(targets), 1)), beta=np.zeros(1))
+    assert np.all(np.abs(boot - exact) <= 4.5 * math.sqrt(2.0 / B) * exact)
+    assert abs(np.mean(boot / exact) - 1.0) <= 4.5 * math.sqrt(2.0 / B / len(targets)) + 0.01
