@@ -235,6 +235,26 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
 kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
                       const double* xi_dev, double* out_dev);
 
+/* Parametric-bootstrap MSE of the kriging prediction of the latent field at
+ * grid cells (Sec. 3.5, Eq. bootstrap_uq), theta and beta known: replicate b
+ * draws x_b on the n1 x n2 grid of the last kry_set_mask with the
+ * circulant-embedding sampler (as kry_sample, white noise
+ * xi_dev + b * 2 * M1 * M2), forms r_b = A x_b + tau eps_b (eps_dev + b * p:
+ * p standard normals), predicts x_hat_b = sigma^2 Sigma A^T K^-1 r_b at every
+ * cell (CG on the nrep right-hand sides together, opts->prec / rtol / maxit;
+ * FP64 covariance map) and writes var_dev[t] = (1/nrep) sum_b
+ * (x_b(c_t) - x_hat_b(c_t))^2 for the flat row-major cells c_t of
+ * cells_dev[ncell] (int64).  It estimates the simple-kriging variance; the MSE
+ * of y at a cell adds tau^2.  M1, M2 as for kry_sample (kry_sample_size gives
+ * the smallest usable torus).  The caller owns every buffer (device); the
+ * library keeps 2 nrep (n1 n2 + p) doubles of scratch in the context.
+ * Errors: KRY_EINVAL for bad arguments or a target cell outside the grid (its
+ * variance is NaN); KRY_ENOCONV when some replicate's CG missed rtol (the
+ * variances are still written).  Synchronises the stream. */
+kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, int32_t nrep, int32_t M1,
+                             int32_t M2, const double* xi_dev, const double* eps_dev, const int64_t* cells_dev,
+                             int64_t ncell, double* var_dev);
+
 /* BCCB approximation of the log-determinant of the latent covariance
  * Sigma(theta) on the n1 x n2 grid of the last kry_set_mask (Sec. 3.3,
  * "Log-determinant approximation"), and of its derivative with respect to the

@@ -100,7 +100,7 @@ void ctx_trim(kry_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
 }
@@ -334,7 +334,7 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         // pool memory cached in this process instead of returning it at each sync
         DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                           &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
         for (DevBuf* b : bufs) b->stream = ctx->stream;
         for (auto& b : ctx->work) b.stream = ctx->stream;
         cudaMemPool_t pool;
@@ -364,7 +364,7 @@ void kry_destroy(kry_ctx* ctx) {
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                       &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
     prof_clear(ctx);
@@ -771,6 +771,51 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2, 
                         (M1 & (M1 - 1)) == 0 && (M2 & (M2 - 1)) == 0,
                     KRY_EINVAL, "M1, M2 must be powers of two with 2 n_d <= M_d <= 8192");
         kry::sample_field(ctx, *cov, M1, M2, xi_dev, out_dev);
+        return KRY_OK;
+    });
+}
+
+kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, int32_t nrep, int32_t M1,
+                             int32_t M2, const double* xi_dev, const double* eps_dev, const int64_t* cells_dev,
+                             int64_t ncell, double* var_dev) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_cov(cov);
+        check_opts(opts);
+        require_mask(ctx);
+        KRY_REQUIRE(nrep >= 1, KRY_EINVAL, "nrep must be >= 1");
+        KRY_REQUIRE(xi_dev && eps_dev, KRY_EINVAL, "xi_dev and eps_dev must not be NULL");
+        KRY_REQUIRE(ncell >= 0 && (ncell == 0 || (cells_dev && var_dev)), KRY_EINVAL,
+                    "cells_dev and var_dev are required when ncell > 0");
+        KRY_REQUIRE(M1 >= 2 * ctx->n1 && M2 >= 2 * ctx->n2 && M1 <= KRY_MAX_M && M2 <= KRY_MAX_M &&
+                        (M1 & (M1 - 1)) == 0 && (M2 & (M2 - 1)) == 0,
+                    KRY_EINVAL, "M1, M2 must be powers of two with 2 n_d <= M_d <= 8192");
+        const int64_t N = (int64_t)ctx->n1 * ctx->n2, p = ctx->p;
+        ctx->boot.ensure(((size_t)2 * nrep * N + (size_t)2 * nrep * p) * sizeof(double) + 16);
+        double* G = ctx->boot.as<double>();       // sampled fields x_b on the grid
+        double* H = G + (size_t)nrep * N;         // predictions sigma^2 Sigma A^T K^-1 r_b on the grid
+        double* R = H + (size_t)nrep * N;         // r_b = A x_b + tau eps_b
+        double* Wd = R + (size_t)nrep * p;        // K^-1 r_b
+        int* bad = reinterpret_cast<int*>(Wd + (size_t)nrep * p);
+        KRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+        for (int b = 0; b < nrep; ++b)
+            kry::sample_field(ctx, *cov, M1, M2, xi_dev + (size_t)b * 2 * M1 * M2, G + (size_t)b * N);
+        kry::boot_rhs(ctx, G, N, eps_dev, sqrt(cov->tau2), R, nrep);
+        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry::SolveInfo si;
+        try {
+            si = kry::solve(ctx, e, R, p, Wd, p, nrep, opts->rtol, opts->maxit);
+            kry::sigma_to_grid64(ctx, e, Wd, H, nrep, p);
+        } catch (...) {
+            free_embed(e);
+            throw;
+        }
+        free_embed(e);
+        kry::boot_mse(ctx, G, H, N, nrep, cells_dev, ncell, var_dev, bad);
+        int* hbad = reinterpret_cast<int*>(ctx->host_pinned);
+        KRY_CUDA(cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (*hbad) return fail(ctx, KRY_EINVAL, "a target cell index lies outside the grid (its variance is NaN)");
+        if (!si.converged) return fail(ctx, KRY_ENOCONV, "CG did not reach rtol for some replicate");
         return KRY_OK;
     });
 }

@@ -115,6 +115,7 @@ struct kry_ctx {
     DevBuf tolbuf, kxbuf;         // CG tolerances, FP64 residual matvec output
     DevBuf cbuf, sbuf;            // kriging-variance right-hand sides and solutions
     DevBuf zbuf, gbuf;            // [y, X] and its solve; kriging grid and weights
+    DevBuf boot;                  // bootstrap replicates: fields, predictions, right-hand sides, solves
     double* host_pinned = nullptr;   // pinned host scratch (4096 doubles)
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -190,6 +191,12 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
                      int64_t ld, int vpt = 0);
 
 void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out);
+
+// Bootstrap helpers (Sec. 3.5): R[b][q] = G[b][cell of q] + tau * eps[b][q];
+// var[t] = mean_b (G[b][cells[t]] - H[b][cells[t]])^2 (bad index -> NaN, *bad).
+void boot_rhs(kry_ctx* ctx, const double* G, int64_t N, const double* eps, double tau, double* R, int nrep);
+void boot_mse(kry_ctx* ctx, const double* G, const double* H, int64_t N, int nrep, const int64_t* cells,
+              int64_t ncell, double* var, int* bad);
 
 // BCCB approximation of log det Sigma (no nugget) on the mask's grid and, if
 // deriv, of its range derivative (Sec. 3.3, Appendix A).

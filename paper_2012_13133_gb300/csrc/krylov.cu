@@ -1362,6 +1362,49 @@ __global__ void k_resid_weights(const double* __restrict__ Z, int64_t p, int nco
     }
 }
 
+// ------------------------------------------------------------------ parametric bootstrap (Sec. 3.5)
+
+__global__ void k_boot_rhs(const double* __restrict__ G, int64_t N, const int* __restrict__ cellidx, int64_t p,
+                           const double* __restrict__ eps, double tau, double* __restrict__ R) {
+    const int b = blockIdx.y;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x)
+        R[(int64_t)b * p + q] = G[(int64_t)b * N + cellidx[q]] + tau * eps[(int64_t)b * p + q];
+}
+
+void boot_rhs(kry_ctx* ctx, const double* G, int64_t N, const double* eps, double tau, double* R, int nrep) {
+    const int64_t p = ctx->p;
+    dim3 g((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nrep);
+    k_boot_rhs<<<g, 256, 0, ctx->stream>>>(G, N, ctx->cellidx.as<int>(), p, eps, tau, R);
+    KRY_CHECK_LAUNCH();
+}
+
+__global__ void k_boot_mse(const double* __restrict__ G, const double* __restrict__ H, int64_t N, int nrep,
+                           const int64_t* __restrict__ cells, int64_t ncell, double* __restrict__ var,
+                           int* __restrict__ bad) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ncell; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = cells[t];
+        if (cell < 0 || cell >= N) {
+            var[t] = __longlong_as_double(0x7ff8000000000000ll);
+            *bad = 1;
+            continue;
+        }
+        double s = 0.0;
+        for (int b = 0; b < nrep; ++b) {
+            const double d = G[(int64_t)b * N + cell] - H[(int64_t)b * N + cell];
+            s += d * d;
+        }
+        var[t] = s / nrep;
+    }
+}
+
+void boot_mse(kry_ctx* ctx, const double* G, const double* H, int64_t N, int nrep, const int64_t* cells,
+              int64_t ncell, double* var, int* bad) {
+    if (ncell <= 0) return;
+    k_boot_mse<<<(unsigned)std::min<int64_t>((ncell + 255) / 256, 4096), 256, 0, ctx->stream>>>(G, H, N, nrep, cells,
+                                                                                              ncell, var, bad);
+    KRY_CHECK_LAUNCH();
+}
+
 // mean[t] = X_t beta + grid[cells[t]]; a cell index outside [0, N) gives NaN
 // and raises *bad.
 __global__ void k_krige_cells(const double* __restrict__ grid, int64_t N, const int64_t* __restrict__ cells,

@@ -90,6 +90,8 @@ SIGNATURES = {
     "kry_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _DP]),
     "kry_launch_count": (C.c_uint64, []),
     "kry_bccb_logdet": (C.c_int, [_P, C.POINTER(kry_cov), _DP, _DP]),
+    "kry_bootstrap_var": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), C.c_int32, C.c_int32, C.c_int32,
+                                    _P, _P, _P, C.c_int64, _P]),
 }
 
 
@@ -340,6 +342,17 @@ class Context:
         out = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=xi.device)
         self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, _ptr(xi.contiguous()), _ptr(out)))
         return out
+
+    def bootstrap_var(self, cov, opts: Opts, xi, eps, cells):
+        """Parametric-bootstrap kriging MSE at grid cells.  xi: (nrep, 2, M1, M2) float64 CUDA white
+        noise, eps: (nrep, p) float64 CUDA, cells: (ncell,) int64 CUDA.  Returns (var, status)."""
+        xi, eps, cells = xi.contiguous(), eps.contiguous(), cells.contiguous()
+        nrep, _, M1, M2 = xi.shape
+        var = self.torch.empty(cells.shape[0], dtype=self.torch.float64, device=xi.device)
+        st = self._check(_lib.kry_bootstrap_var(self.h, C.byref(make_cov(cov)), C.byref(opts.c()), nrep, M1, M2,
+                                                _ptr(xi), _ptr(eps), _ptr(cells), cells.shape[0], _ptr(var)),
+                         allow=(KRY_ENOCONV,))
+        return var, st
 
     def bccb_logdet(self, cov, derivative=True):
         """BCCB approximation of log det Sigma (no nugget) on the mask's grid and its range

@@ -4,6 +4,7 @@
   python -m paper_2012_13133_gb300.measure --workload large4096   # log-likelihood + kriging means, wall time
   python -m paper_2012_13133_gb300.measure --workload tiny32      # FP64 evaluations per second
   python -m paper_2012_13133_gb300.measure --workload grid1024 --bccb   # BCCB log-det + derivative
+  python -m paper_2012_13133_gb300.measure --workload grid1024 --bootstrap 20   # bootstrap kriging MSE
 
 Inputs are the seeded synthetic workloads of ``inputs.WORKLOADS``, resident on
 the device before timing; each timed call is bracketed by device
@@ -57,13 +58,27 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32", "grid1024"])
     ap.add_argument("--bccb", action="store_true", help="time the BCCB log-det and its range derivative")
+    ap.add_argument("--bootstrap", type=int, default=0,
+                    help="time the parametric-bootstrap kriging MSE with this many replicates at all missing cells")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
     ctx = kry.Context(0)
     mask, p, y, X, S1, S2 = problem(ctx, w, dev)
     out = {"workload": args.workload, "grid": [w.n1, w.n2], "p": p}
-    if args.bccb:
+    if args.bootstrap:
+        nrep = args.bootstrap
+        M1, M2, _ = ctx.sample_size(w.cov)
+        rng = np.random.default_rng(w.data_seed + 101)
+        xi = torch.tensor(rng.standard_normal((nrep, 2, M1, M2)), device=dev)
+        eps = torch.tensor(rng.standard_normal((nrep, p)), device=dev)
+        cells = torch.tensor(np.flatnonzero(~mask.ravel()).astype(np.int64), device=dev)
+        opts = kry.Opts(prec=kry.KRY_F32, rtol=w.cg_tol, maxit=30000)
+        (var, st), t = timed(lambda: ctx.bootstrap_var(w.cov, opts, xi, eps, cells))
+        v = var.cpu().numpy()
+        out.update({"replicates": nrep, "cells": int(cells.numel()), "bootstrap_s": t, "status": int(st),
+                    "mean_var": float(v.mean()), "min_var": float(v.min()), "max_var": float(v.max())})
+    elif args.bccb:
         ctx.bccb_logdet(w.cov)
         reps = 5
         (ld, dl), t = timed(lambda: [ctx.bccb_logdet(w.cov) for _ in range(reps)][-1])

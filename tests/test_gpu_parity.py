@@ -479,3 +479,33 @@ def test_bccb_logdet_matches_oracle(ctx, n1, n2, cov):
     assert dl == pytest.approx(ref_dl, rel=1e-7)
     ld2, none = ctx.bccb_logdet(cov, derivative=False)
     assert ld2 == ld and none is None
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-6), ("f32", 1e-4)])
+def test_bootstrap_variance_matches_oracle(ctx, prec, tol):
+    """Parametric-bootstrap kriging MSE (Sec. 3.5, Eq. bootstrap_uq) with the same white noise as
+    the oracle: sampler, data, batched CG over the replicates, covariance map, MSE."""
+    n1, n2 = 40, 36
+    cov = I.Cov(1.0, 0.15, 1.5, 0.1)
+    mask = I.mask_circles(n1, n2, 0.3, 6)
+    p = set_mask(ctx, mask)
+    M1, M2, _ = ctx.sample_size(cov)
+    nrep = 20
+    rng = np.random.default_rng(21)
+    xis = rng.standard_normal((nrep, 2, M1, M2))
+    epss = rng.standard_normal((nrep, p))
+    cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+    # the replicates' predictions come from CG (the oracle's from Cholesky): solution errors are
+    # ~cond(K) x rtol, so the comparison allows for them
+    opts = kry.Opts(prec=kry.KRY_F32 if prec == "f32" else kry.KRY_F64, rtol=1e-12 if prec == "f64" else 1e-7,
+                    maxit=20000)
+    var, st = ctx.bootstrap_var(cov, opts, torch.tensor(xis, device=DEV), torch.tensor(epss, device=DEV),
+                                torch.tensor(cells, device=DEV))
+    assert st == kry.KRY_OK
+    ref = O.bootstrap_kriging_variance(n1, n2, mask, cov, cells, xis, epss)
+    assert relerr(var.cpu().numpy(), ref) <= tol
+    # a cell outside the grid is an argument error
+    with pytest.raises(kry.KryError) as ei:
+        ctx.bootstrap_var(cov, opts, torch.tensor(xis[:1], device=DEV), torch.tensor(epss[:1], device=DEV),
+                          torch.tensor([n1 * n2], dtype=torch.int64, device=DEV))
+    assert ei.value.status == kry.KRY_EINVAL
