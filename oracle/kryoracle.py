@@ -529,6 +529,95 @@ def sample_field(n1, n2, M1, M2, cov, xi):
     return scipy.fft.fft2(z, workers=_WORKERS).real[:n1, :n2]
 
 
+def gengk(n1, n2, mask, cov, b, k, reorth=False):
+    """Generalized Golub-Kahan bidiagonalization (Alg. 1) for the genHyBR problem of Sec. 3.2:
+    A = selection of the observed cells of the n1 x n2 grid, Sigma = the correlation matrix
+    (sigma^2 = 1) applied on the whole grid by the FP64 circulant-embedding matvec, b = y - X beta,
+    R = tau^2 I.  Reading of a garble in the algorithm's step for beta_{i+1}: beta_{i+1} =
+    ||A Sigma v_i - alpha_i u_i||_2 / tau (as beta_1 = ||b||_2 / tau), which is what makes
+    U^T U = tau^2 I hold (Eq. exact_arith).  reorth: re-orthogonalise each new u against U
+    (Euclidean) and each new v against V (Sigma inner product), twice.
+    Returns (beta1, U[p, k+1], V[N, k+1], alphas[k+1], betas[k+1] with betas[0] = beta1)."""
+    mask = np.asarray(mask, bool)
+    full = np.ones((n1, n2), bool)
+    corr = type(cov)(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
+    M1, M2 = embed_size(n1), embed_size(n2)
+    lam, _ = embedding_eigs(lag_covariance(n1, n2, M1, M2, corr))
+
+    def sig(v):                                   # Sigma v on the whole grid
+        return bttb_matvec_fft(n1, n2, M1, M2, lam, full, v, 0.0)
+
+    def At(u):                                    # A^T u: observed values into a zero grid
+        g = np.zeros(n1 * n2)
+        g[mask.ravel()] = u
+        return g
+
+    tau2 = cov.tau2
+    tau = math.sqrt(tau2)
+    N, p = n1 * n2, int(mask.sum())
+    U = np.zeros((p, k + 1))
+    V = np.zeros((N, k + 1))
+    SV = np.zeros((N, k + 1))
+    alphas, betas = np.zeros(k + 1), np.zeros(k + 1)
+    beta1 = float(np.linalg.norm(b)) / tau
+    U[:, 0] = b / beta1
+    betas[0] = beta1
+    w = At(U[:, 0]) / tau2
+    sw = sig(w)
+    alphas[0] = math.sqrt(float(w @ sw))
+    V[:, 0], SV[:, 0] = w / alphas[0], sw / alphas[0]
+    for i in range(k):
+        t = SV[mask.ravel(), i] - alphas[i] * U[:, i]
+        if reorth:
+            for _ in range(2):
+                t -= U[:, : i + 1] @ (U[:, : i + 1].T @ t) / tau2
+        betas[i + 1] = float(np.linalg.norm(t)) / tau
+        U[:, i + 1] = t / betas[i + 1]
+        w = At(U[:, i + 1]) / tau2 - betas[i + 1] * V[:, i]
+        if reorth:
+            for _ in range(2):
+                w -= V[:, : i + 1] @ (SV[:, : i + 1].T @ w)
+        sw = sig(w)
+        alphas[i + 1] = math.sqrt(float(w @ sw))
+        V[:, i + 1], SV[:, i + 1] = w / alphas[i + 1], sw / alphas[i + 1]
+    return beta1, U, V, alphas, betas
+
+
+def genhybr(n1, n2, mask, cov, b, k, reorth=False):
+    """genHyBR estimate of x_hat (Sec. 3.2): with B_k the (k+1) x k lower bidiagonal of alphas
+    and betas from Alg. 1, z_k = (B_k^T B_k + I / sigma^2)^-1 B_k^T beta1 e_1 and
+    x_k* = Sigma V_k z_k (Eq. xhat_est), Sigma the correlation; x_hat^T Sigma^-1 x_hat ~ ||z_k||^2.
+    Returns dict(x, z, psi2 = ||b - A x_k*||^2, z2 = ||z_k||^2)."""
+    mask = np.asarray(mask, bool)
+    beta1, U, V, al, be = gengk(n1, n2, mask, cov, b, k, reorth)
+    Bk = np.zeros((k + 1, k))
+    for i in range(k):
+        Bk[i, i] = al[i]
+        Bk[i + 1, i] = be[i + 1]
+    rhs = Bk.T @ (beta1 * np.eye(k + 1)[:, 0])
+    z = np.linalg.solve(Bk.T @ Bk + np.eye(k) / cov.sigma2, rhs)
+    corr = type(cov)(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
+    M1, M2 = embed_size(n1), embed_size(n2)
+    lam, _ = embedding_eigs(lag_covariance(n1, n2, M1, M2, corr))
+    x = bttb_matvec_fft(n1, n2, M1, M2, lam, np.ones((n1, n2), bool), V[:, :k] @ z, 0.0)
+    psi = b - x[mask.ravel()]
+    return dict(x=x, z=z, psi2=float(psi @ psi), z2=float(z @ z))
+
+
+def approx_profile_loglik(n1, n2, mask, cov, b, k, reading="scaled", reorth=False):
+    """The paper's approximate profile log-likelihood (Eq. prof_lik), constants dropped as there:
+    -p/2 log tau^2 - ||psi_k*||^2 / (2 tau^2) - n/2 log sigma^2 - 1/2 logdet~ Sigma - ||z_k||^2 / (2 sigma^2),
+    Sigma the correlation, logdet~ its BCCB approximation (Sec. 3.3, reading as bccb_logdet)."""
+    mask = np.asarray(mask, bool)
+    g = genhybr(n1, n2, mask, cov, b, k, reorth)
+    corr = type(cov)(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
+    ld, _ = bccb_logdet(n1, n2, corr, reading)
+    p, N = int(mask.sum()), n1 * n2
+    pl = (-0.5 * p * math.log(cov.tau2) - g["psi2"] / (2 * cov.tau2) - 0.5 * N * math.log(cov.sigma2) - 0.5 * ld -
+          g["z2"] / (2 * cov.sigma2))
+    return dict(pl=pl, logdet=ld, **g)
+
+
 def bootstrap_kriging_variance(n1, n2, mask, cov, targets, xis, epss):
     """Parametric-bootstrap MSE of the kriging prediction of x at grid cells ``targets`` (flat
     row-major indices), theta and beta known (Sec. 3.5, Eq. bootstrap_uq): replicate b draws

@@ -496,3 +496,52 @@ def test_bootstrap_variance_converges_to_the_kriging_variance():
     _, exact = O.krige_dense(n1, n2, mask, cov, y, X, t_sites, np.ones((len(targets), 1)), beta=np.zeros(1))
     assert np.all(np.abs(boot - exact) <= 4.5 * math.sqrt(2.0 / B) * exact)
     assert abs(np.mean(boot / exact) - 1.0) <= 4.5 * math.sqrt(2.0 / B / len(targets)) + 0.01
+
+
+# ---------------------------------------------------------------- genGK / genHyBR (Alg. 1, Sec. 3.2)
+
+def _gk_problem():
+    n1, n2 = 12, 10
+    cov = I.Cov(1.3, 0.2, 1.5, 0.2, angle=0.3, ratio=1.4)
+    mask = I.mask_uniform(n1, n2, 0.3, 4)
+    b = np.random.default_rng(1).standard_normal(int(mask.sum()))
+    full = np.ones((n1, n2), bool)
+    sites = O.observed_sites(n1, n2, full)
+    S = O.dense_sigma(sites, sites, I.Cov(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio))
+    A = np.eye(n1 * n2)[mask.ravel()]
+    return n1, n2, cov, mask, b, S, A
+
+
+@pytest.mark.parametrize("reorth", [True, False])
+def test_gengk_satisfies_its_exact_arithmetic_relations(reorth):
+    """Eq. exact_arith: A Sigma V_k = U_{k+1} B_k, U^T U = tau^2 I, V^T Sigma V = I, against the
+    dense correlation matrix (without reorthogonalisation the recurrence relation still holds to
+    rounding and the bases stay orthogonal for a few steps)."""
+    n1, n2, cov, mask, b, S, A = _gk_problem()
+    k = 12 if reorth else 5
+    beta1, U, V, al, be = O.gengk(n1, n2, mask, cov, b, k, reorth=reorth)
+    Bk = np.zeros((k + 1, k))
+    for i in range(k):
+        Bk[i, i], Bk[i + 1, i] = al[i], be[i + 1]
+    assert np.abs(A @ S @ V[:, :k] - U @ Bk).max() <= 1e-12
+    assert np.abs(U.T @ U - cov.tau2 * np.eye(k + 1)).max() <= 1e-10
+    assert np.abs(V.T @ S @ V - np.eye(k + 1)).max() <= 1e-10
+    assert beta1 == pytest.approx(np.linalg.norm(b) / math.sqrt(cov.tau2), rel=1e-14)
+
+
+def test_genhybr_on_the_full_krylov_space_is_the_exact_estimate():
+    """With k = p the Krylov space holds the solution: x_k* equals x_hat of Eq. act_xhat, ||z_k||^2
+    equals x_hat^T Sigma^-1 x_hat and psi the exact residual, so Eq. prof_lik's terms equal those of
+    the exact profile likelihood (Eq. exact_plik)."""
+    n1, n2, cov, mask, b, S, A = _gk_problem()
+    p = int(mask.sum())
+    g = O.genhybr(n1, n2, mask, cov, b, p, reorth=True)
+    Gi = np.linalg.inv(S) / cov.sigma2 + A.T @ A / cov.tau2
+    xhat = np.linalg.solve(Gi, A.T @ b / cov.tau2)
+    assert np.abs(g["x"] - xhat).max() <= 1e-10 * np.abs(xhat).max()
+    assert g["z2"] == pytest.approx(float(xhat @ np.linalg.solve(S, xhat)), rel=1e-9)
+    psi = b - A @ xhat
+    assert g["psi2"] == pytest.approx(float(psi @ psi), rel=1e-9)
+    ex = O.approx_profile_loglik(n1, n2, mask, cov, b, p, reorth=True)
+    corr = I.Cov(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
+    assert ex["logdet"] == pytest.approx(O.bccb_logdet(n1, n2, corr, "scaled")[0], rel=1e-14)
