@@ -235,6 +235,28 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
 kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
                       const double* xi_dev, double* out_dev);
 
+/* genHyBR estimate of the latent field and the paper's approximate profile
+ * log-likelihood (Sec. 3.2, Alg. 1, Eq. xhat_est, Eq. prof_lik), for the
+ * mask's grid, cov's sigma2, range, nu, anisotropy and nugget tau2 (> 0), and
+ * b_dev = y - X beta on the p observed cells (device, FP64; the caller chooses
+ * beta).  k steps of the generalized Golub-Kahan bidiagonalization (Alg. 1)
+ * with A the observed-cell selection, Sigma the correlation matrix applied on
+ * the whole grid by the FP64 embedding matvec and R = tau2 I, then
+ * z_k = (B_k^T B_k + I / sigma2)^-1 B_k^T beta1 e1, x_k* = Sigma V_k z_k and
+ *   *pl = -p/2 log tau2 - ||b - A x_k*||^2 / (2 tau2) - n/2 log sigma2
+ *         - 1/2 logdet~ Sigma - ||z_k||^2 / (2 sigma2)
+ * (constants dropped as in the paper; n = n1 n2; logdet~ the BCCB
+ * approximation of kry_bccb_logdet).  beta_{i+1} of Alg. 1 is read as
+ * ||A Sigma v_i - alpha_i u_i||_2 / tau (as beta_1 = ||b||_2 / tau), which
+ * U^T U = tau2 I requires; no reorthogonalisation (as the paper runs it).
+ * Outputs (each may be NULL): x_dev[n1 n2] (device) = x_k*; alphas[k+1],
+ * betas[k+1] (host) the bidiagonal entries (betas[0] = beta1); *z2 =
+ * ||z_k||^2, *psi2 = ||b - A x_k*||^2, *pl.  Library scratch: (2k + 6) n1 n2
+ * doubles.  Errors: KRY_EINVAL (bad arguments, tau2 or sigma2 not positive,
+ * b zero), KRY_ENAN on a breakdown (a zero alpha or beta).  Synchronises. */
+kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, int32_t k, double* x_dev,
+                       double* alphas, double* betas, double* z2, double* psi2, double* pl);
+
 /* Parametric-bootstrap MSE of the kriging prediction of the latent field at
  * grid cells (Sec. 3.5, Eq. bootstrap_uq), theta and beta known: replicate b
  * draws x_b on the n1 x n2 grid of the last kry_set_mask with the

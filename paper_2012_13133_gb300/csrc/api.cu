@@ -100,7 +100,7 @@ void ctx_trim(kry_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
 }
@@ -255,6 +255,10 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     return e;
 }
 
+namespace kry {
+kry_embed* make_embed_internal(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) { return make_embed(ctx, cov, prec); }
+}  // namespace kry
+
 // Stream-ordered release on stream s (the creating context's stream while it
 // lives; the legacy stream from kry_embed_free, whose context may be gone).
 static void free_embed(kry_embed* e, cudaStream_t s) {
@@ -268,6 +272,10 @@ static void free_embed(kry_embed* e, cudaStream_t s) {
 static void free_embed(kry_embed* e) {
     if (e) free_embed(e, e->stream);
 }
+
+namespace kry {
+void free_embed_internal(kry_embed* e) { free_embed(e); }
+}  // namespace kry
 
 // Several covariance settings on the grid of the mask in one embedding:
 // eigenvalue blocks back to back, per-setting nuggets on the device.
@@ -334,7 +342,7 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         // pool memory cached in this process instead of returning it at each sync
         DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                           &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
+                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
         for (DevBuf* b : bufs) b->stream = ctx->stream;
         for (auto& b : ctx->work) b.stream = ctx->stream;
         cudaMemPool_t pool;
@@ -364,7 +372,7 @@ void kry_destroy(kry_ctx* ctx) {
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                       &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
     prof_clear(ctx);
@@ -816,6 +824,18 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
         KRY_CUDA(cudaStreamSynchronize(ctx->stream));
         if (*hbad) return fail(ctx, KRY_EINVAL, "a target cell index lies outside the grid (its variance is NaN)");
         if (!si.converged) return fail(ctx, KRY_ENOCONV, "CG did not reach rtol for some replicate");
+        return KRY_OK;
+    });
+}
+
+kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, int32_t k, double* x_dev,
+                       double* alphas, double* betas, double* z2, double* psi2, double* pl) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_cov(cov);
+        require_mask(ctx);
+        KRY_REQUIRE(b_dev != nullptr, KRY_EINVAL, "b_dev must not be NULL");
+        KRY_REQUIRE(k >= 1 && k <= 4096, KRY_EINVAL, "k must be in [1, 4096]");
+        kry::genhybr(ctx, *cov, b_dev, k, x_dev, alphas, betas, z2, psi2, pl);
         return KRY_OK;
     });
 }

@@ -1,0 +1,260 @@
+// genHyBR for the latent field (Sec. 3.2): generalized Golub-Kahan
+// bidiagonalization (Alg. 1) with A = the observed-cell selection, Sigma =
+// the correlation matrix (sigma^2 = 1) applied on the whole grid by the FP64
+// circulant-embedding matvec, R = tau^2 I; the projected Tikhonov problem
+// (B_k^T B_k + I / sigma^2) z = B_k^T beta1 e1; x_k* = Sigma V_k z_k (Eq.
+// xhat_est); and the approximate profile log-likelihood of Eq. prof_lik with
+// the BCCB log-det of Sec. 3.3.
+//
+// Reading of the garbled beta_{i+1} step of Alg. 1: beta_{i+1} =
+// ||A Sigma v_i - alpha_i u_i||_2 / tau, as beta_1 = ||b||_2 / tau, which is
+// what U^T U = tau^2 I (Eq. exact_arith) requires.  No reorthogonalisation
+// (the paper runs without it).
+//
+// The whole-grid matvec reuses the FP64 passes of the observed-cell matvec
+// with the row/column index lists of a full mask swapped in for the duration
+// of each call; pass C's fused dot product gives w^T Sigma w, the squared
+// Sigma-norm of Alg. 1.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kry_internal.cuh"
+
+namespace kry {
+
+template <typename T>
+void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+               int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
+int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
+
+namespace {
+
+__global__ void k_full_index(int* __restrict__ rowptr, int* __restrict__ colidx, int n1, int n2) {
+    const int64_t N = (int64_t)n1 * n2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        colidx[i] = (int)(i % n2);
+        if (i % n2 == 0) rowptr[i / n2] = (int)i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rowptr[n1] = (int)N;
+}
+
+// Swaps the full-grid index lists into the context for one scope.
+struct FullGrid {
+    kry_ctx* ctx;
+    int64_t p_saved;
+    explicit FullGrid(kry_ctx* c) : ctx(c), p_saved(c->p) {
+        std::swap(ctx->rowptr, ctx->rowptr_full);
+        std::swap(ctx->colidx, ctx->colidx_full);
+        ctx->p = (int64_t)ctx->n1 * ctx->n2;
+    }
+    ~FullGrid() {
+        std::swap(ctx->rowptr, ctx->rowptr_full);
+        std::swap(ctx->colidx, ctx->colidx_full);
+        ctx->p = p_saved;
+    }
+};
+
+// Per-block partial sums of x[i]^2 (fixed order within a block).
+__global__ void k_sq_partials(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += x[i] * x[i];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// t[q] = sv[cell q] - alpha u[q]
+__global__ void k_gk_gather(const double* __restrict__ sv, const int* __restrict__ cellidx, const double* __restrict__ u,
+                            double alpha, double* __restrict__ t, int64_t p) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x)
+        t[q] = sv[cellidx[q]] - alpha * u[q];
+}
+
+__global__ void k_scale_copy(const double* __restrict__ x, double s, double* __restrict__ y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = s * x[i];
+}
+
+// w = -beta v (whole grid), then w[cell q] += u[q] / tau^2 (cells are distinct)
+__global__ void k_gk_fill(const double* __restrict__ v, double beta, double* __restrict__ w, int64_t N) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = -beta * v[i];
+}
+__global__ void k_gk_scatter_add(const double* __restrict__ u, const int* __restrict__ cellidx, double inv_tau2,
+                                 double* __restrict__ w, int64_t p) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x)
+        w[cellidx[q]] += inv_tau2 * u[q];
+}
+
+// out[i] = sum_j z[j] V[j][i]  (j < k, fixed order)
+__global__ void k_gk_combine(const double* __restrict__ V, const double* __restrict__ z, int k, int64_t N,
+                             double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) s += z[j] * V[(int64_t)j * N + i];
+        out[i] = s;
+    }
+}
+
+const int NB = 256;
+
+unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
+
+double sum_sq(kry_ctx* ctx, const double* x, int64_t n, double* part) {
+    k_sq_partials<<<NB, 256, 0, ctx->stream>>>(x, n, part);
+    KRY_CHECK_LAUNCH();
+    KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, part, NB * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    double s = 0.0;
+    for (int b = 0; b < NB; ++b) s += ctx->host_pinned[b];
+    return s;
+}
+
+// sw = Sigma w on the whole grid; returns w^T Sigma w.
+double sigma_full(kry_ctx* ctx, const kry_embed* e, const double* w, double* sw, double* dots, int nds) {
+    {
+        FullGrid fg(ctx);
+        const int64_t N = ctx->p;
+        matvec_ex<double>(ctx, e, w, N, nullptr, sw, N, 1, dots, nds);
+    }
+    KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, dots, nds * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    double s = 0.0;
+    for (int b = 0; b < nds; ++b) s += ctx->host_pinned[b];
+    return s;
+}
+
+}  // namespace
+
+void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
+             double* z2_out, double* psi2_out, double* pl_out) {
+    const int n1 = ctx->n1, n2 = ctx->n2;
+    const int64_t N = (int64_t)n1 * n2, p = ctx->p;
+    KRY_REQUIRE(cov.tau2 > 0.0 && cov.sigma2 > 0.0, KRY_EINVAL, "genHyBR needs tau2 > 0 and sigma2 > 0");
+    KRY_REQUIRE(N <= 4096 * 4096, KRY_EUNSUPPORTED, "grid too large for the whole-grid matvec");
+    // whole-grid index lists (built once per mask)
+    KRY_REQUIRE(k >= 1, KRY_EINVAL, "k must be >= 1");
+    if (ctx->rowptr_full.p == nullptr || ctx->full_n1 != n1 || ctx->full_n2 != n2) {
+        ctx->rowptr_full.ensure((size_t)(n1 + 1) * sizeof(int));
+        ctx->colidx_full.ensure((size_t)N * sizeof(int));
+        k_full_index<<<grid_for(N), 256, 0, ctx->stream>>>(ctx->rowptr_full.as<int>(), ctx->colidx_full.as<int>(), n1,
+                                                           n2);
+        KRY_CHECK_LAUNCH();
+        ctx->full_n1 = n1;
+        ctx->full_n2 = n2;
+    }
+    kry_cov corr = cov;
+    corr.sigma2 = 1.0;
+    corr.tau2 = 0.0;
+    const double tau2 = cov.tau2, tau = sqrt(tau2);
+    // scratch: V [k+1][N], SV, W, X (whole grid); U [k+1][p], T (observed); partials; z
+    int nds = 0;
+    ctx->gk.ensure(((size_t)(k + 4) * N + (size_t)(k + 2) * p + 2 * NB + 8192 + (size_t)k + 1) * sizeof(double));
+    double* V = ctx->gk.as<double>();
+    double* SV = V + (size_t)(k + 1) * N;
+    double* W = SV + N;
+    double* X = W + N;
+    double* U = X + N;
+    double* T = U + (size_t)(k + 1) * p;
+    double* part = T + p;
+    double* dots = part + 2 * NB;   // pass C partials (at most 8192)
+    double* zdev = dots + 8192;     // k coefficients
+
+    kry_embed* e = make_embed_internal(ctx, &corr, KRY_F64);
+    try {
+        nds = matvec_num_partials(ctx, e, true, 1);
+        KRY_REQUIRE(nds <= 4096, KRY_EUNSUPPORTED, "too many matvec partials");   // the pinned host buffer
+        std::vector<double> al(k + 1, 0.0), be(k + 1, 0.0);
+        // u_1 = b / beta_1, beta_1 = ||b|| / tau
+        const double beta1 = sqrt(sum_sq(ctx, b, p, part)) / tau;
+        KRY_REQUIRE(beta1 > 0.0 && isfinite(beta1), KRY_EINVAL, "b must be finite and nonzero");
+        be[0] = beta1;
+        k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(b, 1.0 / beta1, U, p);
+        KRY_CHECK_LAUNCH();
+        // w = A^T u_1 / tau^2, alpha_1 = ||w||_Sigma, v_1 = w / alpha_1
+        KRY_CUDA(cudaMemsetAsync(W, 0, N * sizeof(double), ctx->stream));
+        k_gk_scatter_add<<<grid_for(p), 256, 0, ctx->stream>>>(U, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
+        KRY_CHECK_LAUNCH();
+        double a2 = sigma_full(ctx, e, W, SV, dots, nds);
+        KRY_REQUIRE(a2 > 0.0 && isfinite(a2), KRY_ENAN, "alpha_1 is not positive");
+        al[0] = sqrt(a2);
+        k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[0], V, N);
+        KRY_CHECK_LAUNCH();
+        k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[0], SV, N);
+        KRY_CHECK_LAUNCH();
+        for (int i = 0; i < k; ++i) {
+            double* ui = U + (size_t)i * p;
+            double* un = U + (size_t)(i + 1) * p;
+            double* vi = V + (size_t)i * N;
+            double* vn = V + (size_t)(i + 1) * N;
+            // t = A Sigma v_i - alpha_i u_i, beta_{i+1} = ||t|| / tau, u_{i+1} = t / beta_{i+1}
+            k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(SV, ctx->cellidx.as<int>(), ui, al[i], T, p);
+            KRY_CHECK_LAUNCH();
+            be[i + 1] = sqrt(sum_sq(ctx, T, p, part)) / tau;
+            KRY_REQUIRE(be[i + 1] > 0.0 && isfinite(be[i + 1]), KRY_ENAN, "genGK breakdown (beta = 0)");
+            k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(T, 1.0 / be[i + 1], un, p);
+            KRY_CHECK_LAUNCH();
+            // w = A^T u_{i+1} / tau^2 - beta_{i+1} v_i, alpha_{i+1} = ||w||_Sigma
+            k_gk_fill<<<grid_for(N), 256, 0, ctx->stream>>>(vi, be[i + 1], W, N);
+            KRY_CHECK_LAUNCH();
+            k_gk_scatter_add<<<grid_for(p), 256, 0, ctx->stream>>>(un, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
+            KRY_CHECK_LAUNCH();
+            a2 = sigma_full(ctx, e, W, SV, dots, nds);
+            KRY_REQUIRE(a2 > 0.0 && isfinite(a2), KRY_ENAN, "genGK breakdown (alpha = 0)");
+            al[i + 1] = sqrt(a2);
+            k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[i + 1], vn, N);
+            KRY_CHECK_LAUNCH();
+            k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[i + 1], SV, N);
+            KRY_CHECK_LAUNCH();
+        }
+        // projected Tikhonov problem: (B^T B + I / sigma^2) z = B^T beta1 e1, B (k+1) x k lower
+        // bidiagonal; B^T B is tridiagonal: diag a_j^2 + b_{j+1}^2, off-diagonal a_{j+1} b_{j+1}
+        std::vector<double> d(k), o(k > 0 ? k - 1 : 0), z(k, 0.0);
+        for (int j = 0; j < k; ++j) d[j] = al[j] * al[j] + be[j + 1] * be[j + 1] + 1.0 / cov.sigma2;
+        for (int j = 0; j + 1 < k; ++j) o[j] = al[j + 1] * be[j + 1];
+        z[0] = al[0] * beta1;
+        // symmetric tridiagonal solve (LDL^T without pivoting: the matrix is positive definite)
+        std::vector<double> dd(d), zz(z);
+        for (int j = 1; j < k; ++j) {
+            const double m = o[j - 1] / dd[j - 1];
+            dd[j] -= m * o[j - 1];
+            zz[j] -= m * zz[j - 1];
+        }
+        for (int j = k - 1; j >= 0; --j) zz[j] = (zz[j] - (j + 1 < k ? o[j] * zz[j + 1] : 0.0)) / dd[j];
+        double z2 = 0.0;
+        for (int j = 0; j < k; ++j) z2 += zz[j] * zz[j];
+        // x* = Sigma V_k z, psi = b - A x*
+        KRY_CUDA(cudaMemcpyAsync(zdev, zz.data(), k * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        k_gk_combine<<<grid_for(N), 256, 0, ctx->stream>>>(V, zdev, k, N, W);
+        KRY_CHECK_LAUNCH();
+        sigma_full(ctx, e, W, X, dots, nds);
+        k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(X, ctx->cellidx.as<int>(), b, 1.0, T, p);   // x*[c] - b
+        KRY_CHECK_LAUNCH();
+        const double psi2 = sum_sq(ctx, T, p, part);
+        if (x_out) KRY_CUDA(cudaMemcpyAsync(x_out, X, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        double ld = 0.0;
+        bccb_logdet(ctx, corr, false, &ld, nullptr);
+        const double pl = -0.5 * (double)p * log(tau2) - psi2 / (2.0 * tau2) - 0.5 * (double)N * log(cov.sigma2) -
+                          0.5 * ld - z2 / (2.0 * cov.sigma2);
+        if (alphas) std::copy(al.begin(), al.end(), alphas);
+        if (betas) std::copy(be.begin(), be.end(), betas);
+        if (z2_out) *z2_out = z2;
+        if (psi2_out) *psi2_out = psi2;
+        if (pl_out) *pl_out = pl;
+        KRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+        free_embed_internal(e);
+        throw;
+    }
+    free_embed_internal(e);
+}
+
+}  // namespace kry

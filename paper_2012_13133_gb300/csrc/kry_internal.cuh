@@ -116,6 +116,9 @@ struct kry_ctx {
     DevBuf cbuf, sbuf;            // kriging-variance right-hand sides and solutions
     DevBuf zbuf, gbuf;            // [y, X] and its solve; kriging grid and weights
     DevBuf boot;                  // bootstrap replicates: fields, predictions, right-hand sides, solves
+    DevBuf gk;                    // genGK bases and work vectors
+    DevBuf rowptr_full, colidx_full;   // index lists of the whole grid (genGK's Sigma matvec)
+    int full_n1 = 0, full_n2 = 0;
     double* host_pinned = nullptr;   // pinned host scratch (4096 doubles)
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -197,6 +200,15 @@ void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double
 void boot_rhs(kry_ctx* ctx, const double* G, int64_t N, const double* eps, double tau, double* R, int nrep);
 void boot_mse(kry_ctx* ctx, const double* G, const double* H, int64_t N, int nrep, const int64_t* cells,
               int64_t ncell, double* var, int* bad);
+
+// Embedding of one covariance setting on the mask's grid (library-owned).
+kry_embed* make_embed_internal(kry_ctx* ctx, const kry_cov* cov, kry_prec prec);
+void free_embed_internal(kry_embed* e);
+
+// genHyBR with k genGK steps (Sec. 3.2, Alg. 1; Eq. prof_lik): b = y - X beta on the
+// observed cells; x_out (whole grid, may be NULL), alphas/betas[k+1] (host, may be NULL).
+void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
+             double* z2, double* psi2, double* pl);
 
 // BCCB approximation of log det Sigma (no nugget) on the mask's grid and, if
 // deriv, of its range derivative (Sec. 3.3, Appendix A).

@@ -5,6 +5,7 @@
   python -m paper_2012_13133_gb300.measure --workload tiny32      # FP64 evaluations per second
   python -m paper_2012_13133_gb300.measure --workload grid1024 --bccb   # BCCB log-det + derivative
   python -m paper_2012_13133_gb300.measure --workload grid1024 --bootstrap 20   # bootstrap kriging MSE
+  python -m paper_2012_13133_gb300.measure --workload grid1024 --genhybr 50     # genHyBR, k = 50
 
 Inputs are the seeded synthetic workloads of ``inputs.WORKLOADS``, resident on
 the device before timing; each timed call is bracketed by device
@@ -58,6 +59,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32", "grid1024"])
     ap.add_argument("--bccb", action="store_true", help="time the BCCB log-det and its range derivative")
+    ap.add_argument("--genhybr", type=int, default=0, help="time genHyBR (Alg. 1 + Eq. prof_lik) with k steps")
     ap.add_argument("--bootstrap", type=int, default=0,
                     help="time the parametric-bootstrap kriging MSE with this many replicates at all missing cells")
     args = ap.parse_args()
@@ -66,7 +68,12 @@ def main():
     ctx = kry.Context(0)
     mask, p, y, X, S1, S2 = problem(ctx, w, dev)
     out = {"workload": args.workload, "grid": [w.n1, w.n2], "p": p}
-    if args.bootstrap:
+    if args.genhybr:
+        b = (y - X.T @ torch.tensor(w.beta, device=dev, dtype=torch.float64)).contiguous()
+        ctx.genhybr(w.cov, b, 2)
+        g, t = timed(lambda: ctx.genhybr(w.cov, b, args.genhybr))
+        out.update({"k": args.genhybr, "genhybr_s": t, "pl": g["pl"], "z2": g["z2"], "psi2": g["psi2"]})
+    elif args.bootstrap:
         nrep = args.bootstrap
         M1, M2, _ = ctx.sample_size(w.cov)
         rng = np.random.default_rng(w.data_seed + 101)

@@ -509,3 +509,26 @@ def test_bootstrap_variance_matches_oracle(ctx, prec, tol):
         ctx.bootstrap_var(cov, opts, torch.tensor(xis[:1], device=DEV), torch.tensor(epss[:1], device=DEV),
                           torch.tensor([n1 * n2], dtype=torch.int64, device=DEV))
     assert ei.value.status == kry.KRY_EINVAL
+
+
+@pytest.mark.parametrize("n1,n2,cov,k", [
+    (24, 20, I.Cov(1.3, 0.2, 1.5, 0.2, angle=0.3, ratio=1.4), 8),
+    (40, 36, I.Cov(1.0, 0.1, 0.5, 0.1), 15),
+    (33, 47, I.Cov(2.0, 0.15, 1.0, 0.3), 10),
+])
+def test_genhybr_matches_oracle(ctx, n1, n2, cov, k):
+    """genGK (Alg. 1) bidiagonal, genHyBR estimate (Eq. xhat_est) and the approximate profile
+    log-likelihood (Eq. prof_lik) against the FP64 oracle (both without reorthogonalisation)."""
+    mask = make_mask(n1, n2, 0.3, "circles")
+    p = set_mask(ctx, mask)
+    b = I.normals(p, 31)
+    g = ctx.genhybr(cov, torch.tensor(b, device=DEV), k)
+    ref = O.approx_profile_loglik(n1, n2, mask, cov, b, k)
+    _, _, _, al, be = O.gengk(n1, n2, mask, cov, b, k)
+    assert np.allclose(g["alphas"], al, rtol=1e-9) and np.allclose(g["betas"], be, rtol=1e-9)
+    assert g["z2"] == pytest.approx(ref["z2"], rel=1e-8)
+    assert g["psi2"] == pytest.approx(ref["psi2"], rel=1e-8)
+    assert relerr(g["x"].cpu().numpy().ravel(), ref["x"]) <= 1e-8
+    assert g["pl"] == pytest.approx(ref["pl"], rel=1e-10)
+    with pytest.raises(kry.KryError):
+        ctx.genhybr(I.Cov(1.0, 0.1, 0.5, 0.0), torch.tensor(b, device=DEV), k)   # tau2 = 0
