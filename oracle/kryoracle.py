@@ -599,9 +599,10 @@ def genhybr(n1, n2, mask, cov, b, k, reorth=False):
     corr = type(cov)(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
     M1, M2 = embed_size(n1), embed_size(n2)
     lam, _ = embedding_eigs(lag_covariance(n1, n2, M1, M2, corr))
-    x = bttb_matvec_fft(n1, n2, M1, M2, lam, np.ones((n1, n2), bool), V[:, :k] @ z, 0.0)
+    q = V[:, :k] @ z
+    x = bttb_matvec_fft(n1, n2, M1, M2, lam, np.ones((n1, n2), bool), q, 0.0)
     psi = b - x[mask.ravel()]
-    return dict(x=x, z=z, psi2=float(psi @ psi), z2=float(z @ z))
+    return dict(x=x, z=z, q=q, psi=psi, psi2=float(psi @ psi), z2=float(z @ z))
 
 
 def approx_profile_loglik(n1, n2, mask, cov, b, k, reading="scaled", reorth=False):
@@ -616,6 +617,30 @@ def approx_profile_loglik(n1, n2, mask, cov, b, k, reading="scaled", reorth=Fals
     pl = (-0.5 * p * math.log(cov.tau2) - g["psi2"] / (2 * cov.tau2) - 0.5 * N * math.log(cov.sigma2) - 0.5 * ld -
           g["z2"] / (2 * cov.sigma2))
     return dict(pl=pl, logdet=ld, **g)
+
+
+def approx_gradient(n1, n2, mask, cov, b, k, reading="scaled", reorth=False):
+    """The paper's approximate gradient of the profile log-likelihood (Appendix A, Eq. approx_grad),
+    in its parametrisation lambda^2 = 1/sigma^2, lambda_e^2 = 1/tau^2:
+      d pl / d lambda^2   ~ n / (2 lambda^2) - ||z_k||^2 / 2,
+      d pl / d rho        ~ -dL~ / 2 + lambda^2 / 2 (V_k z_k)^T dSigma (V_k z_k),
+      d pl / d lambda_e^2 ~ p / (2 lambda_e^2) - ||psi_k*||^2 / 2,
+    (d pl / d beta ~ lambda_e^2 X^T psi_k*, formed by the caller from the returned psi), with
+    dSigma the range derivative of the correlation applied by its circulant extension on the whole
+    grid and dL~ the BCCB derivative of Sec. 3.3 (reading as bccb_logdet).
+    Returns dict(grad = [d/d lambda^2, d/d rho, d/d lambda_e^2], psi)."""
+    mask = np.asarray(mask, bool)
+    g = genhybr(n1, n2, mask, cov, b, k, reorth)
+    corr = type(cov)(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
+    M1, M2 = embed_size(n1), embed_size(n2)
+    lam_d = scipy.fft.fft2(_torus_first_row(n1, n2, M1, M2, corr, covariance_drange), workers=_WORKERS).real
+    dq = bttb_matvec_fft(n1, n2, M1, M2, lam_d, np.ones((n1, n2), bool), g["q"], 0.0)
+    _, dl = bccb_logdet(n1, n2, corr, reading)
+    lam2, lame2 = 1.0 / cov.sigma2, 1.0 / cov.tau2
+    N, p = n1 * n2, int(mask.sum())
+    grad = [N / (2 * lam2) - 0.5 * g["z2"], -0.5 * dl + 0.5 * lam2 * float(g["q"] @ dq),
+            p / (2 * lame2) - 0.5 * g["psi2"]]
+    return dict(grad=np.array(grad), psi=g["psi"])
 
 
 def bootstrap_kriging_variance(n1, n2, mask, cov, targets, xis, epss):

@@ -545,3 +545,38 @@ def test_genhybr_on_the_full_krylov_space_is_the_exact_estimate():
     ex = O.approx_profile_loglik(n1, n2, mask, cov, b, p, reorth=True)
     corr = I.Cov(1.0, cov.range, cov.nu, 0.0, cov.angle, cov.ratio)
     assert ex["logdet"] == pytest.approx(O.bccb_logdet(n1, n2, corr, "scaled")[0], rel=1e-14)
+
+
+def test_approximate_gradient_is_exact_on_the_full_krylov_space():
+    """Eq. approx_grad with k = p (x_k* = x_hat) is the gradient of Eq. prof_lik (the envelope
+    argument behind Eq. anal_grad: x_hat maximises the joint objective): checked against
+    difference quotients of approx_profile_loglik in lambda^2, rho, lambda_e^2 and beta."""
+    n1, n2 = 10, 9
+    mask = I.mask_uniform(n1, n2, 0.25, 2)
+    p = int(mask.sum())
+    S1, S2 = I.cell_centres(n1, n2)
+    X = I.covariates(S1[mask], S2[mask])
+    y = np.random.default_rng(5).standard_normal(p)
+    beta = np.array([0.3, -0.2, 0.1])
+    base = dict(nu=1.5, angle=0.2, ratio=1.3)
+
+    def pl(lam2, rho, lame2, bt):
+        cov = I.Cov(1.0 / lam2, rho, tau2=1.0 / lame2, **base)
+        return O.approx_profile_loglik(n1, n2, mask, cov, y - X @ bt, p, reorth=True)["pl"]
+
+    lam2, rho, lame2 = 1.0 / 1.4, 0.18, 1.0 / 0.25
+    cov = I.Cov(1.0 / lam2, rho, tau2=1.0 / lame2, **base)
+    ag = O.approx_gradient(n1, n2, mask, cov, y - X @ beta, p, reorth=True)
+    for j, (name, h) in enumerate([("lam2", 1e-6), ("rho", 1e-7), ("lame2", 1e-6)]):
+        args = [lam2, rho, lame2]
+        up, dn = list(args), list(args)
+        up[j] += h
+        dn[j] -= h
+        fd = (pl(*up, beta) - pl(*dn, beta)) / (2 * h)
+        assert ag["grad"][j] == pytest.approx(fd, rel=1e-5, abs=1e-6), name
+    gb = (1.0 / cov.tau2) * X.T @ ag["psi"]
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = 1e-6
+        fd = (pl(lam2, rho, lame2, beta + e) - pl(lam2, rho, lame2, beta - e)) / 2e-6
+        assert gb[c] == pytest.approx(fd, rel=1e-5, abs=1e-6)
