@@ -249,13 +249,26 @@ kry_status kry_sample(kry_ctx* ctx, const kry_cov* cov, int32_t M1, int32_t M2,
  * approximation of kry_bccb_logdet).  beta_{i+1} of Alg. 1 is read as
  * ||A Sigma v_i - alpha_i u_i||_2 / tau (as beta_1 = ||b||_2 / tau), which
  * U^T U = tau2 I requires; no reorthogonalisation (as the paper runs it).
+ * A step whose beta or alpha falls below 1e-13 of beta1 or alpha1 ends the
+ * bidiagonalization early (the Krylov space then holds the solution; the
+ * remaining alphas / betas are 0).
  * Outputs (each may be NULL): x_dev[n1 n2] (device) = x_k*; alphas[k+1],
  * betas[k+1] (host) the bidiagonal entries (betas[0] = beta1); *z2 =
- * ||z_k||^2, *psi2 = ||b - A x_k*||^2, *pl.  Library scratch: (2k + 6) n1 n2
- * doubles.  Errors: KRY_EINVAL (bad arguments, tau2 or sigma2 not positive,
- * b zero), KRY_ENAN on a breakdown (a zero alpha or beta).  Synchronises. */
+ * ||z_k||^2, *psi2 = ||b - A x_k*||^2, *pl; grad[3] (host) the approximate
+ * gradient of Appendix A (Eq. approx_grad) in the paper's parametrisation
+ * lambda^2 = 1/sigma2, lambda_e^2 = 1/tau2:
+ *   grad[0] = d pl / d lambda^2   ~ n / (2 lambda^2) - ||z_k||^2 / 2,
+ *   grad[1] = d pl / d range      ~ -dL~ / 2 + lambda^2 / 2 (V_k z_k)^T dSigma (V_k z_k),
+ *   grad[2] = d pl / d lambda_e^2 ~ p / (2 lambda_e^2) - ||psi_k*||^2 / 2
+ * (dSigma the range derivative of the correlation, dL~ the BCCB derivative
+ * of kry_bccb_logdet); psi_dev[p] (device) = psi_k* = b - A x_k*, from which
+ * the caller forms d pl / d beta ~ lambda_e^2 X^T psi_k*.  Library scratch:
+ * (2k + 6) n1 n2 doubles.  Errors: KRY_EINVAL (bad arguments, tau2 or sigma2
+ * not positive, b zero), KRY_ENAN for a non-finite alpha or beta.
+ * Synchronises the stream. */
 kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, int32_t k, double* x_dev,
-                       double* alphas, double* betas, double* z2, double* psi2, double* pl);
+                       double* alphas, double* betas, double* z2, double* psi2, double* pl, double* grad,
+                       double* psi_dev);
 
 /* Parametric-bootstrap MSE of the kriging prediction of the latent field at
  * grid cells (Sec. 3.5, Eq. bootstrap_uq), theta and beta known: replicate b

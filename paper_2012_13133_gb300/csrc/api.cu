@@ -829,13 +829,14 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
 }
 
 kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, int32_t k, double* x_dev,
-                       double* alphas, double* betas, double* z2, double* psi2, double* pl) {
+                       double* alphas, double* betas, double* z2, double* psi2, double* pl, double* grad,
+                       double* psi_dev) {
     return guarded(ctx, [&]() -> kry_status {
         check_cov(cov);
         require_mask(ctx);
         KRY_REQUIRE(b_dev != nullptr, KRY_EINVAL, "b_dev must not be NULL");
         KRY_REQUIRE(k >= 1 && k <= 4096, KRY_EINVAL, "k must be in [1, 4096]");
-        kry::genhybr(ctx, *cov, b_dev, k, x_dev, alphas, betas, z2, psi2, pl);
+        kry::genhybr(ctx, *cov, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
         return KRY_OK;
     });
 }

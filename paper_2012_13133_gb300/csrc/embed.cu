@@ -404,6 +404,25 @@ void store_embedding(kry_ctx* ctx, kry_embed* e, int slot) {
     KRY_CHECK_LAUNCH();
 }
 
+// Replace the eigenvalues of FP64 embedding e (one setting, e's grid) by those
+// of the circulant extension of d Sigma / d(range) for cov, so that matvecs
+// with e apply the range derivative of the covariance (Appendix A, dSigma).
+void drange_embedding(kry_ctx* ctx, const kry_cov& cov, kry_embed* e) {
+    const int M1 = e->M1, M2 = e->M2;
+    const int64_t MM = (int64_t)M1 * M2;
+    ctx->eig_c.ensure(MM * sizeof(double));
+    ctx->eig_z.ensure(MM * sizeof(double2));
+    double* c = ctx->eig_c.as<double>();
+    double2* z = ctx->eig_z.as<double2>();
+    k_lag_cov<true><<<(unsigned)((MM + 255) / 256), 256, 0, ctx->stream>>>(c, M1, M2,
+                                                                        cov_dev(cov, ctx->dx1, ctx->dx2));
+    KRY_CHECK_LAUNCH();
+    launch_rows_full<0>(ctx, c, nullptr, 0.0, z, M1, M2);
+    launch_cols_full<0>(ctx, z, c, M1, M2, 0, 0);
+    store_embedding(ctx, e, 0);
+}
+
+
 void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double* xi, double* out) {
     double lo, hi;
     compute_eigs(ctx, cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, M1, M2, &lo, &hi);

@@ -135,7 +135,7 @@ double sigma_full(kry_ctx* ctx, const kry_embed* e, const double* w, double* sw,
 }  // namespace
 
 void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
-             double* z2_out, double* psi2_out, double* pl_out) {
+             double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
     const int n1 = ctx->n1, n2 = ctx->n2;
     const int64_t N = (int64_t)n1 * n2, p = ctx->p;
     KRY_REQUIRE(cov.tau2 > 0.0 && cov.sigma2 > 0.0, KRY_EINVAL, "genHyBR needs tau2 > 0 and sigma2 > 0");
@@ -190,6 +190,10 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
         KRY_CHECK_LAUNCH();
         k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[0], SV, N);
         KRY_CHECK_LAUNCH();
+        // A step whose beta or alpha falls below 1e-13 of the first one ends the bidiagonalization:
+        // the Krylov space then holds the solution (an exact breakdown up to rounding), and the
+        // projected problem uses the keff steps taken.
+        int keff = k;
         for (int i = 0; i < k; ++i) {
             double* ui = U + (size_t)i * p;
             double* un = U + (size_t)(i + 1) * p;
@@ -199,7 +203,12 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
             k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(SV, ctx->cellidx.as<int>(), ui, al[i], T, p);
             KRY_CHECK_LAUNCH();
             be[i + 1] = sqrt(sum_sq(ctx, T, p, part)) / tau;
-            KRY_REQUIRE(be[i + 1] > 0.0 && isfinite(be[i + 1]), KRY_ENAN, "genGK breakdown (beta = 0)");
+            KRY_REQUIRE(isfinite(be[i + 1]), KRY_ENAN, "genGK: beta is NaN/Inf");
+            if (!(be[i + 1] > 1e-13 * beta1)) {
+                be[i + 1] = 0.0;
+                keff = i + 1;
+                break;
+            }
             k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(T, 1.0 / be[i + 1], un, p);
             KRY_CHECK_LAUNCH();
             // w = A^T u_{i+1} / tau^2 - beta_{i+1} v_i, alpha_{i+1} = ||w||_Sigma
@@ -208,7 +217,11 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
             k_gk_scatter_add<<<grid_for(p), 256, 0, ctx->stream>>>(un, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
             KRY_CHECK_LAUNCH();
             a2 = sigma_full(ctx, e, W, SV, dots, nds);
-            KRY_REQUIRE(a2 > 0.0 && isfinite(a2), KRY_ENAN, "genGK breakdown (alpha = 0)");
+            KRY_REQUIRE(isfinite(a2), KRY_ENAN, "genGK: alpha is NaN/Inf");
+            if (!(a2 > 1e-26 * al[0] * al[0])) {
+                keff = i + 1;
+                break;
+            }
             al[i + 1] = sqrt(a2);
             k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[i + 1], vn, N);
             KRY_CHECK_LAUNCH();
@@ -217,33 +230,50 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
         }
         // projected Tikhonov problem: (B^T B + I / sigma^2) z = B^T beta1 e1, B (k+1) x k lower
         // bidiagonal; B^T B is tridiagonal: diag a_j^2 + b_{j+1}^2, off-diagonal a_{j+1} b_{j+1}
-        std::vector<double> d(k), o(k > 0 ? k - 1 : 0), z(k, 0.0);
-        for (int j = 0; j < k; ++j) d[j] = al[j] * al[j] + be[j + 1] * be[j + 1] + 1.0 / cov.sigma2;
-        for (int j = 0; j + 1 < k; ++j) o[j] = al[j + 1] * be[j + 1];
+        const int kk = keff;
+        std::vector<double> d(kk), o(kk > 0 ? kk - 1 : 0), z(kk, 0.0);
+        for (int j = 0; j < kk; ++j) d[j] = al[j] * al[j] + be[j + 1] * be[j + 1] + 1.0 / cov.sigma2;
+        for (int j = 0; j + 1 < kk; ++j) o[j] = al[j + 1] * be[j + 1];
         z[0] = al[0] * beta1;
         // symmetric tridiagonal solve (LDL^T without pivoting: the matrix is positive definite)
         std::vector<double> dd(d), zz(z);
-        for (int j = 1; j < k; ++j) {
+        for (int j = 1; j < kk; ++j) {
             const double m = o[j - 1] / dd[j - 1];
             dd[j] -= m * o[j - 1];
             zz[j] -= m * zz[j - 1];
         }
-        for (int j = k - 1; j >= 0; --j) zz[j] = (zz[j] - (j + 1 < k ? o[j] * zz[j + 1] : 0.0)) / dd[j];
+        for (int j = kk - 1; j >= 0; --j) zz[j] = (zz[j] - (j + 1 < kk ? o[j] * zz[j + 1] : 0.0)) / dd[j];
         double z2 = 0.0;
-        for (int j = 0; j < k; ++j) z2 += zz[j] * zz[j];
+        for (int j = 0; j < kk; ++j) z2 += zz[j] * zz[j];
         // x* = Sigma V_k z, psi = b - A x*
-        KRY_CUDA(cudaMemcpyAsync(zdev, zz.data(), k * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        k_gk_combine<<<grid_for(N), 256, 0, ctx->stream>>>(V, zdev, k, N, W);
+        KRY_CUDA(cudaMemcpyAsync(zdev, zz.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        k_gk_combine<<<grid_for(N), 256, 0, ctx->stream>>>(V, zdev, kk, N, W);
         KRY_CHECK_LAUNCH();
         sigma_full(ctx, e, W, X, dots, nds);
         k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(X, ctx->cellidx.as<int>(), b, 1.0, T, p);   // x*[c] - b
         KRY_CHECK_LAUNCH();
         const double psi2 = sum_sq(ctx, T, p, part);
         if (x_out) KRY_CUDA(cudaMemcpyAsync(x_out, X, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-        double ld = 0.0;
-        bccb_logdet(ctx, corr, false, &ld, nullptr);
+        if (psi_out) {   // psi = b - A x* = -T
+            k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(T, -1.0, psi_out, p);
+            KRY_CHECK_LAUNCH();
+        }
+        // Appendix A, Eq. approx_grad: (V_k z_k)^T dSigma (V_k z_k), V_k z_k still in W
+        double qdq = 0.0;
+        if (grad) {
+            drange_embedding(ctx, corr, e);   // e now applies dSigma
+            qdq = sigma_full(ctx, e, W, SV, dots, nds);
+        }
+        double ld = 0.0, dl = 0.0;
+        bccb_logdet(ctx, corr, grad != nullptr, &ld, grad ? &dl : nullptr);
         const double pl = -0.5 * (double)p * log(tau2) - psi2 / (2.0 * tau2) - 0.5 * (double)N * log(cov.sigma2) -
                           0.5 * ld - z2 / (2.0 * cov.sigma2);
+        if (grad) {
+            const double lam2 = 1.0 / cov.sigma2, lame2 = 1.0 / tau2;
+            grad[0] = (double)N / (2.0 * lam2) - 0.5 * z2;          // d pl / d lambda^2
+            grad[1] = -0.5 * dl + 0.5 * lam2 * qdq;                 // d pl / d range
+            grad[2] = (double)p / (2.0 * lame2) - 0.5 * psi2;       // d pl / d lambda_e^2
+        }
         if (alphas) std::copy(al.begin(), al.end(), alphas);
         if (betas) std::copy(be.begin(), be.end(), betas);
         if (z2_out) *z2_out = z2;

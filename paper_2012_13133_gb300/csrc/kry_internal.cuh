@@ -201,6 +201,9 @@ void boot_rhs(kry_ctx* ctx, const double* G, int64_t N, const double* eps, doubl
 void boot_mse(kry_ctx* ctx, const double* G, const double* H, int64_t N, int nrep, const int64_t* cells,
               int64_t ncell, double* var, int* bad);
 
+// Overwrite FP64 embedding e's eigenvalues with those of d Sigma / d(range).
+void drange_embedding(kry_ctx* ctx, const kry_cov& cov, kry_embed* e);
+
 // Embedding of one covariance setting on the mask's grid (library-owned).
 kry_embed* make_embed_internal(kry_ctx* ctx, const kry_cov* cov, kry_prec prec);
 void free_embed_internal(kry_embed* e);
@@ -208,7 +211,7 @@ void free_embed_internal(kry_embed* e);
 // genHyBR with k genGK steps (Sec. 3.2, Alg. 1; Eq. prof_lik): b = y - X beta on the
 // observed cells; x_out (whole grid, may be NULL), alphas/betas[k+1] (host, may be NULL).
 void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
-             double* z2, double* psi2, double* pl);
+             double* z2, double* psi2, double* pl, double* grad = nullptr, double* psi_out = nullptr);
 
 // BCCB approximation of log det Sigma (no nugget) on the mask's grid and, if
 // deriv, of its range derivative (Sec. 3.3, Appendix A).

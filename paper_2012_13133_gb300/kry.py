@@ -90,7 +90,7 @@ SIGNATURES = {
     "kry_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _DP]),
     "kry_launch_count": (C.c_uint64, []),
     "kry_bccb_logdet": (C.c_int, [_P, C.POINTER(kry_cov), _DP, _DP]),
-    "kry_genhybr": (C.c_int, [_P, C.POINTER(kry_cov), _P, C.c_int32, _P, _DP, _DP, _DP, _DP, _DP]),
+    "kry_genhybr": (C.c_int, [_P, C.POINTER(kry_cov), _P, C.c_int32, _P, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
     "kry_bootstrap_var": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), C.c_int32, C.c_int32, C.c_int32,
                                     _P, _P, _P, C.c_int64, _P]),
 }
@@ -355,16 +355,19 @@ class Context:
                          allow=(KRY_ENOCONV,))
         return var, st
 
-    def genhybr(self, cov, b, k, want_x=True):
+    def genhybr(self, cov, b, k, want_x=True, gradient=False):
         """genHyBR with k genGK steps.  b: (p,) float64 CUDA = y - X beta.  Returns dict(x (n1 x n2
-        float64 CUDA or None), alphas, betas (k+1 each), z2, psi2, pl)."""
+        float64 CUDA or None), alphas, betas (k+1 each), z2, psi2, pl, and with gradient=True
+        grad (d pl / d lambda^2, d range, d lambda_e^2) and psi (p,) float64 CUDA)."""
         b = b.contiguous()
         x = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=b.device) if want_x else None
+        psi = self.torch.empty_like(b) if gradient else None
+        grad = np.zeros(3) if gradient else None
         al, be = np.zeros(k + 1), np.zeros(k + 1)
         z2, psi2, pl = C.c_double(), C.c_double(), C.c_double()
         self._check(_lib.kry_genhybr(self.h, C.byref(make_cov(cov)), _ptr(b), k, _ptr(x), _np_dp(al), _np_dp(be),
-                                     C.byref(z2), C.byref(psi2), C.byref(pl)))
-        return dict(x=x, alphas=al, betas=be, z2=z2.value, psi2=psi2.value, pl=pl.value)
+                                     C.byref(z2), C.byref(psi2), C.byref(pl), _np_dp(grad), _ptr(psi)))
+        return dict(x=x, alphas=al, betas=be, z2=z2.value, psi2=psi2.value, pl=pl.value, grad=grad, psi=psi)
 
     def bccb_logdet(self, cov, derivative=True):
         """BCCB approximation of log det Sigma (no nugget) on the mask's grid and its range

@@ -532,3 +532,63 @@ def test_genhybr_matches_oracle(ctx, n1, n2, cov, k):
     assert g["pl"] == pytest.approx(ref["pl"], rel=1e-10)
     with pytest.raises(kry.KryError):
         ctx.genhybr(I.Cov(1.0, 0.1, 0.5, 0.0), torch.tensor(b, device=DEV), k)   # tau2 = 0
+
+
+def test_genhybr_gradient_matches_oracle(ctx):
+    """The approximate gradient of Appendix A (Eq. approx_grad) and psi_k* against the oracle."""
+    n1, n2, k = 30, 26, 12
+    cov = I.Cov(1.4, 0.17, 1.5, 0.25, angle=0.2, ratio=1.3)
+    mask = make_mask(n1, n2, 0.3, "uniform")
+    p = set_mask(ctx, mask)
+    b = I.normals(p, 41)
+    g = ctx.genhybr(cov, torch.tensor(b, device=DEV), k, gradient=True)
+    ref = O.approx_gradient(n1, n2, mask, cov, b, k)
+    assert np.allclose(g["grad"], ref["grad"], rtol=1e-8, atol=1e-9)
+    assert relerr(g["psi"].cpu().numpy(), ref["psi"]) <= 1e-9
+
+
+def test_fits_raise_their_objectives_and_land_near_the_truth(ctx):
+    """Parameter estimation (Sec. 3.4) on data simulated from known parameters.  The marginal
+    likelihood fit of sigma^2, tau^2 and range raises its objective from a start 2x off and lands
+    near the generating values.  The paper-objective fit of range and beta at the true variances
+    raises Eq. prof_lik and ends at a KKT point of it: the objective keeps -1/2 log det Sigma, which
+    grows without bound as the range grows (Sigma tends to a singular matrix), so the point may be
+    the upper range bound, with the approximate gradient pointing out of the box there."""
+    from paper_2012_13133_gb300 import fit as F
+    n1 = n2 = 48
+    true = I.Cov(1.0, 0.12, 0.5, 0.1)
+    mask = I.mask_uniform(n1, n2, 0.2, 7)
+    p = set_mask(ctx, mask)
+    S1, S2 = I.cell_centres(n1, n2)
+    X = I.covariates(S1[mask], S2[mask])
+    M1, M2, _ = ctx.sample_size(true)
+    xi, eps = I.data_noise(M1, M2, p, 12)
+    field = ctx.sample(true, M1, M2, torch.tensor(xi, device=DEV)).cpu().numpy()
+    y = X @ np.array([1.0, 0.5, -0.5]) + field[mask] + math.sqrt(true.tau2) * eps
+    yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
+    opts = kry.Opts(prec=kry.KRY_F64, nprobe=16, nsteps=40, seed=3, rtol=1e-10, maxit=20000)
+    start = I.Cov(2.0, 0.24, 0.5, 0.2)
+    ll0 = ctx.profile_loglik(yt, Xt, [start], opts)["loglik"][0]
+    res = F.fit_marginal(ctx, yt, Xt, start, opts)
+    assert res["loglik"] > ll0
+    c = res["cov"]
+    assert 0.5 * true.range <= c.range <= 2.0 * true.range
+    assert 0.5 * true.tau2 <= c.tau2 <= 2.0 * true.tau2
+    assert 0.3 * true.sigma2 <= c.sigma2 <= 3.0 * true.sigma2
+    # the paper's objective over range and beta at the true variances
+    start = I.Cov(1.0, 0.24, 0.5, 0.1)
+    b0 = (yt - Xt.T @ torch.zeros(3, dtype=torch.float64, device=DEV)).contiguous()
+    pl0 = ctx.genhybr(start, b0, 60, want_x=False)["pl"]
+    res = F.fit_paper(ctx, yt, Xt, start, np.zeros(3), k=60)
+    assert res["pl"] > pl0
+    c = res["cov"]
+    b = (yt - Xt.T @ torch.tensor(res["beta"], dtype=torch.float64, device=DEV)).contiguous()
+    g = ctx.genhybr(c, b, 60, want_x=False, gradient=True)
+    d_logrange = c.range * g["grad"][1]
+    scale = abs(g["pl"])
+    if c.range < 2.0 * (1 - 1e-9):
+        assert abs(d_logrange) <= 1e-3 * scale, d_logrange
+    else:
+        assert d_logrange > 0
+    dbeta = (Xt @ g["psi"]).cpu().numpy() / c.tau2
+    assert np.abs(dbeta).max() <= 1e-3 * scale, dbeta
