@@ -55,6 +55,24 @@ def workload_desc(w):
             f"rel. res. {w.cg_tol:g} (FP32 CG, FP64 residual replacement); GLS beta; kriging mean at all unobserved cells")
 
 
+def max_over_ranks(x, device, world):
+    """Largest value of x over the ranks of the default process group (x itself when world == 1):
+    every rank's timed region ends only when the slowest replica's does."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, seconds):
+    """Whole-job evaluations per second of world replicas that each ran steps evaluations, with
+    seconds the slowest rank's time (weak scaling: the work per GPU is fixed)."""
+    return world * steps / seconds
+
+
 def model_bytes_per_vector(n1, n2, M1, M2, p):
     """Algorithmic bytes of the 3-pass FP32 matvec per real vector: the
     n1 x M2 complex slab written and read twice (16 n1 M2), the vector read,
@@ -234,9 +252,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx.profile_enable(False)
     if world > 1:
         dist.barrier()
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(dev_ms, dev, world)
 
     # ---- end to end: host buffers, H2D + D2H inside the timed region
     e2e = None
@@ -266,17 +282,14 @@ def run_gpu(args, rank, world, local_rank):
             d2h = mean_h.numel() * 8 + 8 * (2 + X_d.shape[0])
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+        e2e_s = max_over_ranks(e2e_s, dev, world)
+        e2e = {"value": replica_throughput(world, args.steps, e2e_s), "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
         return None
 
-    value = world * args.steps / (dev_ms / 1000.0)
+    value = replica_throughput(world, args.steps, dev_ms / 1000.0)
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
     peak_src = "measured" if peaks else "fallback"
