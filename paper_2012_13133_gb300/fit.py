@@ -36,30 +36,30 @@ if ROOT not in sys.path:
 from paper_2012_13133_gb300 import inputs as I  # noqa: E402
 
 
-def fit_marginal(ctx, y, X, cov0, opts, maxiter=100, h=None):
-    """Maximise the marginal log-likelihood (kry_profile_loglik) over log sigma^2, log tau^2 and log
-    range (nu and anisotropy fixed; beta profiled by GLS).  y: (p,) float64 CUDA; X: (ncov, p) float64
-    CUDA; opts: kry.Opts (its probes and seed stay fixed).  h: central-difference step in the log
-    parameters (default 1e-4 for FP64 vectors, 1e-2 for FP32, whose rounding noise in the
-    log-likelihood would swamp a smaller step).  Returns dict(cov, beta, loglik, evaluations,
-    converged, message)."""
+def _log_bounds(ctx, variances):
+    """Box on the log parameters: variances in [1e-6, 1e4], range from half a cell to 2."""
+    cell = 1.0 / max(ctx.n1, ctx.n2)
+    var = [(math.log(1e-6), math.log(1e4))] * variances
+    return var + [(math.log(0.5 * cell), math.log(2.0))]
+
+
+def marginal_objective(ctx, y, X, cov0, opts, h=None):
+    """(f, counter) with f(v) = (-loglik, -gradient) at v = [log sigma^2, log tau^2, log range]: the
+    marginal log-likelihood of kry_profile_loglik (beta profiled by GLS; nu and anisotropy from cov0)
+    and its central differences with step h (default 1e-4 for FP64 vectors, 1e-2 for FP32, whose
+    rounding noise in the log-likelihood would swamp a smaller step).  A setting where the solve
+    breaks down (KryError) scores below every value seen so far, so a line search backs off from it."""
     from paper_2012_13133_gb300 import kry
 
     if h is None:
         h = 1e-4 if opts.prec == kry.KRY_F64 else 1e-2
-    import scipy.optimize
-
-    nu, angle, ratio = cov0.nu, cov0.angle, cov0.ratio
     evals = [0]
-
-    def cov_of(v):
-        return I.Cov(math.exp(v[0]), math.exp(v[2]), nu, math.exp(v[1]), angle=angle, ratio=ratio)
-
     worst = [None]
 
+    def cov_of(v):
+        return I.Cov(math.exp(v[0]), math.exp(v[2]), cov0.nu, math.exp(v[1]), angle=cov0.angle, ratio=cov0.ratio)
+
     def ll(v):
-        # a setting where the solve breaks down (status KRY_ENAN / KRY_ENOCONV) scores below every
-        # setting seen so far, so the line search backs off from it
         evals[0] += 1
         try:
             f = float(ctx.profile_loglik(y, X, [cov_of(v)], opts)["loglik"][0])
@@ -68,58 +68,79 @@ def fit_marginal(ctx, y, X, cov0, opts, maxiter=100, h=None):
         worst[0] = f if worst[0] is None else min(worst[0], f)
         return f
 
-    def objective(v):
-        f = ll(v)
+    def f(v):
+        v = np.asarray(v, dtype=np.float64)
+        val = ll(v)
         g = np.empty(3)
         for j in range(3):
             e = np.zeros(3)
             e[j] = h
             g[j] = (ll(v + e) - ll(v - e)) / (2 * h)
-        return -f, -g
+        return -val, -g
 
-    cell = 1.0 / max(ctx.n1, ctx.n2)
+    f.cov_of = cov_of
+    return f, evals
+
+
+def fit_marginal(ctx, y, X, cov0, opts, maxiter=100, h=None):
+    """Maximise the marginal log-likelihood (kry_profile_loglik) over log sigma^2, log tau^2 and log
+    range (nu and anisotropy fixed; beta profiled by GLS).  y: (p,) float64 CUDA; X: (ncov, p) float64
+    CUDA; opts: kry.Opts (its probes and seed stay fixed); h as in marginal_objective.  Returns
+    dict(cov, beta, loglik, evaluations, converged, message)."""
+    import scipy.optimize
+
+    f, evals = marginal_objective(ctx, y, X, cov0, opts, h)
     v0 = np.array([math.log(cov0.sigma2), math.log(cov0.tau2), math.log(cov0.range)])
-    bounds = [(math.log(1e-6), math.log(1e4)), (math.log(1e-6), math.log(1e4)),
-              (math.log(0.5 * cell), math.log(2.0))]
-    res = scipy.optimize.minimize(objective, v0, jac=True, method="L-BFGS-B", bounds=bounds,
+    res = scipy.optimize.minimize(f, v0, jac=True, method="L-BFGS-B", bounds=_log_bounds(ctx, 2),
                                   options=dict(maxiter=maxiter))
-    cov = cov_of(res.x)
+    cov = f.cov_of(res.x)
     final = ctx.profile_loglik(y, X, [cov], opts)
     return dict(cov=cov, beta=np.asarray(final["beta"][0]), loglik=float(final["loglik"][0]),
                 evaluations=evals[0] + 1, converged=bool(res.success), message=str(res.message))
 
 
-def fit_paper(ctx, y, X, cov0, beta0, k=50, maxiter=200):
-    """Maximise the paper's approximate profile log-likelihood (Eq. prof_lik) over log range and beta
-    with sigma^2 and tau^2 held at cov0's values, using the gradient of Eq. approx_grad.  y: (p,)
-    float64 CUDA; X: (ncov, p) float64 CUDA.  Returns dict(cov, beta, pl, evaluations, converged,
-    message)."""
-    import scipy.optimize
-    import torch
-
+def paper_objective(ctx, y, X, cov0, k):
+    """(f, counter) with f(v) = (-pl, -gradient) at v = [log range, beta...]: the paper's approximate
+    profile log-likelihood (Eq. prof_lik) from kry_genhybr with k steps, sigma^2 and tau^2 held at
+    cov0's values.  The gradient is the approximate one of Appendix A (Eq. approx_grad) by the chain
+    rule: d/d log range = range * d/d range, and d/d beta = lambda_e^2 X^T psi_k* (b = y - X beta
+    enters pl only through psi_k* = b - A x_k*)."""
     Xh = X.double()
     evals = [0]
 
-    def unpack(v):
-        return I.Cov(cov0.sigma2, math.exp(v[0]), cov0.nu, cov0.tau2, angle=cov0.angle, ratio=cov0.ratio), v[1:]
+    def cov_of(v):
+        return I.Cov(cov0.sigma2, math.exp(v[0]), cov0.nu, cov0.tau2, angle=cov0.angle, ratio=cov0.ratio)
 
-    def objective(v):
-        cov, beta = unpack(v)
+    def f(v):
+        import torch
+
+        v = np.asarray(v, dtype=np.float64)
+        cov, beta = cov_of(v), v[1:]
         b = (y - Xh.T @ torch.tensor(beta, dtype=torch.float64, device=y.device)).contiguous()
         g = ctx.genhybr(cov, b, k, want_x=False, gradient=True)
         evals[0] += 1
         d = np.empty(v.size)
-        d[0] = cov.range * g["grad"][1]                        # d / d log range
-        d[1:] = (1.0 / cov.tau2) * (Xh @ g["psi"]).cpu().numpy()  # d / d beta = lambda_e^2 X^T psi
+        d[0] = cov.range * g["grad"][1]
+        d[1:] = (1.0 / cov.tau2) * (Xh @ g["psi"]).cpu().numpy()
         return -g["pl"], -d
 
-    cell = 1.0 / max(ctx.n1, ctx.n2)
+    f.cov_of = cov_of
+    return f, evals
+
+
+def fit_paper(ctx, y, X, cov0, beta0, k=50, maxiter=200):
+    """Maximise the paper's approximate profile log-likelihood (Eq. prof_lik) over log range and beta
+    with sigma^2 and tau^2 held at cov0's values, using the gradient of Eq. approx_grad
+    (paper_objective).  y: (p,) float64 CUDA; X: (ncov, p) float64 CUDA.  Returns dict(cov, beta, pl,
+    evaluations, converged, message)."""
+    import scipy.optimize
+
+    f, evals = paper_objective(ctx, y, X, cov0, k)
     v0 = np.concatenate([[math.log(cov0.range)], np.asarray(beta0, dtype=np.float64)])
-    bounds = [(math.log(0.5 * cell), math.log(2.0))] + [(None, None)] * (v0.size - 1)
-    res = scipy.optimize.minimize(objective, v0, jac=True, method="L-BFGS-B", bounds=bounds,
+    bounds = _log_bounds(ctx, 0) + [(None, None)] * (v0.size - 1)
+    res = scipy.optimize.minimize(f, v0, jac=True, method="L-BFGS-B", bounds=bounds,
                                   options=dict(maxiter=maxiter, ftol=1e-13, gtol=1e-7))
-    cov, beta = unpack(res.x)
-    return dict(cov=cov, beta=np.asarray(beta), pl=-float(res.fun), evaluations=evals[0],
+    return dict(cov=f.cov_of(res.x), beta=np.asarray(res.x[1:]), pl=-float(res.fun), evaluations=evals[0],
                 converged=bool(res.success), message=str(res.message))
 
 

@@ -1,0 +1,138 @@
+"""Host logic of the covariance-parameter fit (Sec. 3.4), run on the CPU against the oracle.
+
+The fit only forms derivatives and steps L-BFGS-B; every objective value comes from a context's
+genhybr / profile_loglik.  Here that context is the FP64 oracle (dense Cholesky for the marginal
+likelihood, the oracle's genHyBR and Appendix A gradient for Eq. prof_lik), so the chain rule, the
+bounds and the stopping point of the driver are checked without a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import kryoracle as O  # noqa: E402
+from paper_2012_13133_gb300 import fit as F  # noqa: E402
+from paper_2012_13133_gb300 import inputs as I  # noqa: E402
+
+N1 = N2 = 16
+TRUE = I.Cov(1.0, 0.15, 0.5, 0.1)
+BETA = np.array([1.0, 0.5, -0.5])
+
+
+class OracleContext:
+    """The two context calls the fit makes, answered by the oracle."""
+
+    def __init__(self, n1, n2, mask):
+        self.n1, self.n2, self.mask = n1, n2, mask
+
+    def genhybr(self, cov, b, k, want_x=False, gradient=False):
+        bn = b.cpu().numpy()
+        r = O.approx_profile_loglik(self.n1, self.n2, self.mask, cov, bn, k)
+        out = dict(pl=r["pl"], z2=r["z2"], psi2=r["psi2"], grad=None, psi=None)
+        if gradient:
+            g = O.approx_gradient(self.n1, self.n2, self.mask, cov, bn, k)
+            out.update(grad=g["grad"], psi=torch.tensor(g["psi"], dtype=torch.float64))
+        return out
+
+    def profile_loglik(self, y, X, covs, opts):
+        Xn = X.cpu().numpy().T
+        res = [O.loglik_dense(O.dense_K(self.n1, self.n2, self.mask, c), y.cpu().numpy(), Xn) for c in covs]
+        return dict(loglik=np.array([r["loglik"] for r in res]), beta=np.array([r["beta"] for r in res]))
+
+
+class Opts:
+    prec = 1  # KRY_F64: the oracle's objective is smooth to rounding
+
+
+@pytest.fixture(scope="module")
+def problem():
+    mask = I.mask_uniform(N1, N2, 0.3, 21)
+    M1, M2 = O.sample_embed_size(N1, N2, TRUE)
+    xi, eps = I.data_noise(M1, M2, int(mask.sum()), 22)
+    y, X, _ = O.make_data(N1, N2, mask, TRUE, BETA, xi, eps)
+    return OracleContext(N1, N2, mask), torch.tensor(y), torch.tensor(X.T.copy())
+
+
+def central(f, v, j, h):
+    e = np.zeros(v.size)
+    e[j] = h
+    return (f(v + e)[0] - f(v - e)[0]) / (2 * h)
+
+
+def test_paper_objective_chain_rule_matches_central_differences(problem):
+    """d(-pl)/d log range and d(-pl)/d beta returned by the objective equal central differences of
+    its own value.  The beta part is exact (pl depends on beta only through b, linearly in psi_k*
+    at fixed x_k*; with k = n steps x_k* is the exact minimiser, so the envelope theorem holds); the
+    range part inherits the Appendix A approximation, pinned separately, so it is held to 1e-3."""
+    ctx, y, X = problem
+    k = int(ctx.mask.sum())
+    f, _ = F.paper_objective(ctx, y, X, TRUE, k)
+    v = np.array([math.log(0.2), 0.8, 0.3, -0.2])
+    val, g = f(v)
+    assert math.isfinite(val)
+    for j in range(1, 4):
+        fd = central(f, v, j, 1e-4)
+        assert g[j] == pytest.approx(fd, rel=1e-6, abs=1e-6 * abs(val)), (j, g[j], fd)
+    fd = central(f, v, 0, 1e-4)
+    assert g[0] == pytest.approx(fd, rel=1e-3, abs=1e-6 * abs(val)), (g[0], fd)
+
+
+def test_marginal_objective_gradient_and_bad_settings(problem):
+    ctx, y, X = problem
+    f, evals = F.marginal_objective(ctx, y, X, TRUE, Opts())
+    v = np.array([math.log(1.3), math.log(0.08), math.log(0.2)])
+    val, g = f(v)
+    assert evals[0] == 7
+    ll = lambda u: ctx.profile_loglik(y, X, [f.cov_of(u)], Opts())["loglik"][0]  # noqa: E731
+    assert -val == pytest.approx(ll(v), rel=1e-14)
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = 1e-5
+        fd = (ll(v + e) - ll(v - e)) / 2e-5
+        assert -g[j] == pytest.approx(fd, rel=1e-5, abs=1e-6), (j, g[j], fd)
+
+    # a context whose solve breaks down at one setting: that setting scores below every value seen
+    from paper_2012_13133_gb300 import kry
+
+    class Failing(OracleContext):
+        def profile_loglik(self, y, X, covs, opts):
+            if covs[0].range > 0.5:
+                raise kry.KryError(kry.KRY_ENAN, "solve broke down")
+            return super().profile_loglik(y, X, covs, opts)
+
+    f2, _ = F.marginal_objective(Failing(N1, N2, ctx.mask), y, X, TRUE, Opts())
+    good, _ = f2(v)
+    bad, _ = f2(np.array([math.log(1.3), math.log(0.08), math.log(0.9)]))
+    assert bad > good and math.isfinite(bad)
+
+
+def test_fits_on_the_oracle_raise_their_objectives_and_stop_at_kkt_points(problem):
+    ctx, y, X = problem
+    start = I.Cov(2.0, 0.3, 0.5, 0.2)
+    f, _ = F.marginal_objective(ctx, y, X, start, Opts())
+    v0 = np.array([math.log(2.0), math.log(0.2), math.log(0.3)])
+    res = F.fit_marginal(ctx, y, X, start, Opts())
+    assert res["loglik"] > -f(v0)[0]
+    c = res["cov"]
+    v = np.array([math.log(c.sigma2), math.log(c.tau2), math.log(c.range)])
+    _, g = f(v)
+    lo, hi = zip(*F._log_bounds(ctx, 2))
+    for j in range(3):
+        if lo[j] + 1e-9 < v[j] < hi[j] - 1e-9:
+            assert abs(g[j]) <= 1e-3 * abs(res["loglik"]), (j, g[j])
+
+    k = int(ctx.mask.sum())
+    start = I.Cov(TRUE.sigma2, 0.3, 0.5, TRUE.tau2)
+    fp, _ = F.paper_objective(ctx, y, X, start, k)
+    pl0 = -fp(np.array([math.log(0.3), 0.0, 0.0, 0.0]))[0]
+    res = F.fit_paper(ctx, y, X, start, np.zeros(3), k=k)
+    assert res["pl"] > pl0
+    c = res["cov"]
+    _, g = fp(np.concatenate([[math.log(c.range)], res["beta"]]))
+    assert np.abs(g[1:]).max() <= 1e-3 * abs(res["pl"]), g
+    if c.range < 2.0 * (1 - 1e-9):
+        assert abs(g[0]) <= 1e-3 * abs(res["pl"]), g
+    else:
+        assert g[0] < 0          # -pl still falls outwards: the range bound is active
