@@ -676,3 +676,110 @@ def make_data(n1, n2, mask, cov, beta, xi, eps):
     X = np.stack([np.ones(int(mask.sum())), S1[mask], S2[mask]], axis=1)
     y = X @ np.asarray(beta, dtype=np.float64) + x[mask] + math.sqrt(cov.tau2) * eps
     return y, X, x
+
+
+# --------------------------------------------------------------------------------------
+# Irregular observation sites: the Wendland mapping matrix A of Sec. 2
+# --------------------------------------------------------------------------------------
+
+
+def wendland(d):
+    """Wendland's compactly supported function w(d) = (1 - d)_+^4 (1 + 4 d) (Sec. 2)."""
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(d < 1.0, (1.0 - d) ** 4 * (1.0 + 4.0 * d), 0.0)
+
+
+def wendland_A_dense(n1, n2, sites):
+    """The p x n mapping matrix of Sec. 2, written out over every grid cell: the distance of site
+    i to cell centre j is d_ij = max(|s_i1 - s*_j1| / Delta_1, |s_i2 - s*_j2| / Delta_2) in grid
+    spacings (Delta_d = 1 / n_d), and A_ij = w(d_ij) / sum_k w(d_ik).  Cells are numbered row-major
+    (j = j1 n2 + j2).  O(p n): for small grids."""
+    sites = np.asarray(sites, dtype=np.float64)
+    S1, S2 = coords(n1, n2)
+    d = np.maximum(np.abs(sites[:, None, 0] - S1.ravel()[None, :]) * n1,
+                   np.abs(sites[:, None, 1] - S2.ravel()[None, :]) * n2)
+    w = wendland(d)
+    return w / w.sum(axis=1, keepdims=True)
+
+
+def wendland_A(n1, n2, sites):
+    """The same matrix in sparse triplet form: only the cell centres within one spacing of a site
+    on both axes (at most 2 x 2 of them) have d_ij < 1, so only they are visited.  Returns
+    (rows, cols, vals) with rows sorted, as int64, int64, float64 arrays."""
+    sites = np.asarray(sites, dtype=np.float64)
+    rows, cols, vals = [], [], []
+    for i, (a, b) in enumerate(sites):
+        u1, u2 = a * n1 - 0.5, b * n2 - 0.5          # site in cell-centre index units
+        cand = [(j1, j2) for j1 in (math.floor(u1), math.floor(u1) + 1)
+                for j2 in (math.floor(u2), math.floor(u2) + 1)
+                if 0 <= j1 < n1 and 0 <= j2 < n2]
+        ws = [float(wendland(max(abs(u1 - j1), abs(u2 - j2)))) for j1, j2 in cand]
+        tot = sum(ws)
+        for (j1, j2), wv in zip(cand, ws):
+            if wv > 0.0:
+                rows.append(i)
+                cols.append(j1 * n2 + j2)
+                vals.append(wv / tot)
+    return np.array(rows, np.int64), np.array(cols, np.int64), np.array(vals)
+
+
+def wendland_dense_K(n1, n2, sites, cov):
+    """Marginal covariance of irregular sites, K = sigma^2 A Sigma A^T + tau^2 I (Eq. obs_mod with
+    the Wendland A), from the dense covariance of the whole latent grid."""
+    A = wendland_A_dense(n1, n2, sites)
+    S1, S2 = coords(n1, n2)
+    g = np.stack([S1.ravel(), S2.ravel()], axis=1)
+    K = A @ dense_sigma(g, g, cov) @ A.T
+    K[np.diag_indices_from(K)] += cov.tau2
+    return K
+
+
+class IrregularProblem:
+    """Irregular sites on an n1 x n2 latent grid (Sec. 2): K v = sigma^2 A Sigma A^T v + tau^2 v
+    with A in sparse form and Sigma applied by the FP64 circulant-embedding FFT on the whole grid
+    (Sec. 3)."""
+
+    def __init__(self, n1, n2, sites, cov):
+        self.n1, self.n2, self.cov = n1, n2, cov
+        self.sites = np.asarray(sites, dtype=np.float64)
+        self.p = self.sites.shape[0]
+        self.rows, self.cols, self.vals = wendland_A(n1, n2, self.sites)
+        self.M1, self.M2 = embed_size(n1), embed_size(n2)
+        self.lam, _ = embedding_eigs(lag_covariance(n1, n2, self.M1, self.M2, cov))
+
+    def A(self, x):
+        """A x for a whole-grid vector x (row-major)."""
+        out = np.zeros(self.p)
+        np.add.at(out, self.rows, self.vals * x[self.cols])
+        return out
+
+    def At(self, v):
+        """A^T v as a whole-grid vector."""
+        out = np.zeros(self.n1 * self.n2)
+        np.add.at(out, self.cols, self.vals * v[self.rows])
+        return out
+
+    def sigma(self, x):
+        """sigma^2 Sigma x on the whole grid."""
+        return sigma_conv_fft(self.n1, self.n2, self.M1, self.M2, self.lam,
+                              x.reshape(self.n1, self.n2)).ravel()
+
+    def matvec(self, v):
+        return self.A(self.sigma(self.At(v))) + self.cov.tau2 * v
+
+    def profile_loglik(self, y, X, nprobe, nsteps, seed, tol=1e-10, reorth=False):
+        vals = []
+        for k in range(nprobe):
+            z = rademacher_probe(seed, k, self.p)
+            a, b = lanczos(self.matvec, z, nsteps, reorth)
+            vals.append(gauss_quadrature_logdet(a, b, float(z @ z)))
+        ld = float(np.mean(vals))
+        cols = [cg(self.matvec, c, tol)[0] for c in np.column_stack([y, X]).T]
+        ll, beta, quad = gls_loglik(ld, cols[0], np.stack(cols[1:], axis=1), y, X)
+        return dict(loglik=ll, beta=beta, logdet=ld, quad=quad)
+
+    def krige_grid(self, y, X, beta, X_grid, tol=1e-10):
+        """Mean of y at every latent cell (A = identity row there): X_grid beta + x_hat, with
+        x_hat = sigma^2 Sigma A^T K^-1 (y - X beta) (Eq. act_xhat by the Woodbury identity)."""
+        w, _ = cg(self.matvec, y - X @ beta, tol)
+        return X_grid @ beta + self.sigma(self.At(w))
