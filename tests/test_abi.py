@@ -1,5 +1,5 @@
 """The C-ABI library loads without a GPU and exports every function that
-include/kry.h declares; the Python binding's signatures cover the header."""
+include/kry.h declares; the Python binding's signatures, structs and enums match the header."""
 import ctypes
 import os
 import re
@@ -41,3 +41,49 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_binding_signatures_cover_header(libpath):
     from paper_2012_13133_gb300 import kry
     assert set(kry.SIGNATURES) == set(declared_functions())
+
+
+STRUCTS = {
+    "kry_grid": ["n1", "n2", "dx1", "dx2"],
+    "kry_cov": ["sigma2", "range", "nu", "tau2", "aniso_angle", "aniso_ratio"],
+    "kry_opts": ["prec", "nprobe", "nsteps", "seed", "rtol", "maxit", "reorth"],
+    "kry_request": ["kind", "n1", "n2", "mask", "y", "X", "ncov", "cov", "opts", "loglik", "logdet", "beta",
+                    "target_cells", "target_X", "mean"],
+}
+
+
+def test_binding_structs_and_enums_match_the_header(libpath, tmp_path):
+    """Compile a C program against include/kry.h that prints every struct's size and field offsets
+    and every enum value; the ctypes binding must agree (same layout on this host's ABI)."""
+    import shutil
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2012_13133_gb300 import kry
+
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kry.h"', "int main(void) {"]
+    for s, fields in STRUCTS.items():
+        lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
+        for f in fields:
+            lines.append(f'printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    enums = [n for n in kry.STATUS_NAMES] + ["KRY_F32", "KRY_F64"]
+    for e in enums:
+        lines.append(f'printf("enum {e} %d\\n", (int){e});')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        parts = line.split()
+        got[tuple(parts[:-1])] = int(parts[-1])
+    for s, fields in STRUCTS.items():
+        cls = getattr(kry, s)
+        assert [f[0] for f in cls._fields_] == fields, s
+        assert got[(s, "size")] == ctypes.sizeof(cls), s
+        for f in fields:
+            assert got[(s, f)] == getattr(cls, f).offset, (s, f)
+    for i, e in enumerate(kry.STATUS_NAMES):
+        assert got[("enum", e)] == i, e
+    assert got[("enum", "KRY_F32")] == kry.KRY_F32 and got[("enum", "KRY_F64")] == kry.KRY_F64
