@@ -122,9 +122,13 @@ def launch_count() -> int:
 
 def _ptr(t):
     """Device pointer of a tensor the library reads as a dense array.  The
-    library takes plain pointers, so strided views must never reach it."""
+    library takes plain device pointers, so host tensors and strided views must
+    never reach it (a host address handed to a kernel is not an error the
+    library could detect)."""
     if t is None:
         return None
+    if t.device.type != "cuda":
+        raise ValueError(f"tensor passed to libkry must be a CUDA tensor (got device {t.device})")
     if not t.is_contiguous():
         raise ValueError("tensor passed to libkry must be contiguous (call .contiguous())")
     return C.c_void_p(t.data_ptr())

@@ -87,3 +87,13 @@ def test_binding_structs_and_enums_match_the_header(libpath, tmp_path):
     for i, e in enumerate(kry.STATUS_NAMES):
         assert got[("enum", e)] == i, e
     assert got[("enum", "KRY_F32")] == kry.KRY_F32 and got[("enum", "KRY_F64")] == kry.KRY_F64
+
+
+def test_binding_refuses_host_and_strided_tensors(libpath):
+    """Device-pointer arguments are checked in the binding before any library call."""
+    torch = pytest.importorskip("torch")
+    from paper_2012_13133_gb300 import kry
+
+    assert kry._ptr(None) is None
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        kry._ptr(torch.zeros(4, dtype=torch.float64))
