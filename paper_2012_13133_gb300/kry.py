@@ -134,6 +134,31 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _dev(*specs):
+    """Device pointers of tensors, each given as (tensor, dtypes, numel, name), after checking them
+    against what the C ABI will read: the dtype (one of ``dtypes``, torch dtype names such as
+    "float64") and the element count.  The library sees only a pointer and the sizes it is given,
+    so a wrong dtype or a short buffer would be read out of bounds rather than reported.  All
+    dtypes and sizes are checked before any device check; None stays None."""
+    for t, dtypes, numel, name in specs:
+        if t is None:
+            continue
+        dt = str(t.dtype).replace("torch.", "")
+        if dt not in dtypes:
+            raise ValueError(f"{name}: expected dtype {' or '.join(dtypes)}, got {dt}")
+        if t.numel() != numel:
+            raise ValueError(f"{name}: expected {numel} elements, got {t.numel()} (shape {tuple(t.shape)})")
+    ptrs = tuple(_ptr(t) for t, _, _, _ in specs)
+    return ptrs if len(ptrs) > 1 else ptrs[0]
+
+
+def _vec_dtype(prec):
+    return ("float32",) if prec == KRY_F32 else ("float64",)
+
+
+F64, I64 = ("float64",), ("int64",)
+
+
 def _np_dp(a):
     return None if a is None else a.ctypes.data_as(_DP)
 
@@ -220,7 +245,8 @@ class Context:
         n1, n2 = mask.shape
         g = kry_grid(n1, n2, 1.0 / n1 if dx1 is None else dx1, 1.0 / n2 if dx2 is None else dx2)
         p = C.c_int64()
-        self._check(_lib.kry_set_mask(self.h, C.byref(g), _ptr(mask.contiguous()), C.byref(p)))
+        m = _dev((mask.contiguous(), ("uint8", "bool"), n1 * n2, "mask"))
+        self._check(_lib.kry_set_mask(self.h, C.byref(g), m, C.byref(p)))
         self.p, self.n1, self.n2 = int(p.value), n1, n2
         return self.p
 
@@ -237,10 +263,13 @@ class Context:
         """v: (nvec, p) or (p,) CUDA tensor (float32 for KRY_F32, float64 for KRY_F64)."""
         squeeze = v.dim() == 1
         V = (v.reshape(1, -1) if squeeze else v).contiguous()
-        assert V.shape[1] == self.p
+        if V.dim() != 2 or V.shape[1] != self.p:
+            raise ValueError(f"v: expected (nvec, {self.p}) or ({self.p},), got {tuple(v.shape)}")
         if out is None:
             out = self.torch.empty(V.shape, dtype=V.dtype, device=V.device)
-        self._check(_lib.kry_matvec(self.h, emb.handle, _ptr(V), _ptr(out), V.shape[0], self.p))
+        n = V.shape[0] * self.p
+        pv, po = _dev((V, _vec_dtype(emb.prec), n, "v"), (out, _vec_dtype(emb.prec), n, "out"))
+        self._check(_lib.kry_matvec(self.h, emb.handle, pv, po, V.shape[0], self.p))
         return out.reshape(-1) if squeeze else out
 
     def logdet(self, emb: Embed, nprobe: int, nsteps: int, seed: int, reorth: int = 0):
@@ -257,7 +286,9 @@ class Context:
         if X is None:
             X = self.torch.empty(Bm.shape, dtype=Bm.dtype, device=Bm.device)
         it, rr = C.c_int32(), C.c_double()
-        st = self._check(_lib.kry_solve(self.h, emb.handle, _ptr(Bm), _ptr(X), Bm.shape[0], self.p, rtol, maxit,
+        n = Bm.shape[0] * self.p
+        pb, px = _dev((Bm, F64, n, "B"), (X, F64, n, "X"))
+        st = self._check(_lib.kry_solve(self.h, emb.handle, pb, px, Bm.shape[0], self.p, rtol, maxit,
                                         C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
         return (X.reshape(-1) if squeeze else X), it.value, rr.value, st
 
@@ -269,7 +300,8 @@ class Context:
         arr = (kry_cov * n)(*[make_cov(t) for t in thetas])
         ll, beta, ld, se = np.zeros(n), np.zeros(n * ncov), np.zeros(n), np.zeros(n)
         o = opts.c()
-        st = self._check(_lib.kry_profile_loglik(self.h, _ptr(y), _ptr(X), ncov, arr, n, C.byref(o), _np_dp(ll),
+        py, pX = _dev((y, F64, self.p, "y"), (X, F64, ncov * self.p, "X"))
+        st = self._check(_lib.kry_profile_loglik(self.h, py, pX, ncov, arr, n, C.byref(o), _np_dp(ll),
                                                  _np_dp(beta), _np_dp(ld), _np_dp(se)), allow=(KRY_ENOCONV,))
         return dict(loglik=ll, beta=beta.reshape(n, ncov), logdet=ld, logdet_se=se, status=st)
 
@@ -288,10 +320,19 @@ class Context:
         beta = np.zeros(ncov)
         c = make_cov(cov)
         o = opts.c()
-        st = self._check(_lib.kry_krige(self.h, C.byref(c), C.byref(o), _ptr(y), _ptr(X), ncov, _ptr(cells), _ptr(Xc),
-                                        ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms), _ptr(vc),
+        a = self._krige_args(y, X, ncov, cells, Xc, ncell, sites, Xs, nsite)
+        st = self._check(_lib.kry_krige(self.h, C.byref(c), C.byref(o), a[0], a[1], ncov, a[2], a[3],
+                                        ncell, a[4], a[5], nsite, _ptr(mc), _ptr(ms), _ptr(vc),
                                         _np_dp(beta)), allow=(KRY_ENOCONV,))
         return dict(mean_cells=mc, mean_sites=ms, var_cells=vc, beta=beta, status=st)
+
+    def _krige_args(self, y, X, ncov, cells, Xc, ncell, sites, Xs, nsite, *more):
+        """Checked device pointers of the kriging inputs: y (p,), X (ncov, p), cells (ncell,) int64,
+        Xc (ncov, ncell), sites (nsite, 2), Xs (ncov, nsite), all float64 but cells; then those of
+        the further (tensor, dtypes, numel, name) specs."""
+        return _dev((y, F64, self.p, "y"), (X, F64, ncov * self.p, "X"), (cells, I64, ncell, "cells"),
+                    (Xc, F64, ncov * ncell, "Xc"), (sites, F64, 2 * nsite, "sites"), (Xs, F64, ncov * nsite, "Xs"),
+                    *more)
 
     def autotune(self, emb: Embed, nvec: int):
         """Time the feasible matvec schedules for batches of nvec; keep the fastest."""
@@ -329,8 +370,10 @@ class Context:
         ll, beta, ld, se = C.c_double(), np.zeros(ncov), C.c_double(), C.c_double()
         c = make_cov(cov)
         o = opts.c()
-        st = self._check(_lib.kry_loglik_krige(self.h, C.byref(c), C.byref(o), _ptr(y), _ptr(X), ncov, _ptr(cells),
-                                               _ptr(Xc), ncell, _ptr(sites), _ptr(Xs), nsite, _ptr(mc), _ptr(ms),
+        a = self._krige_args(y, X, ncov, cells, Xc, ncell, sites, Xs, nsite, (mc, F64, ncell, "mean_cells"))
+        pmc = a[6]
+        st = self._check(_lib.kry_loglik_krige(self.h, C.byref(c), C.byref(o), a[0], a[1], ncov, a[2],
+                                               a[3], ncell, a[4], a[5], nsite, pmc, _ptr(ms),
                                                _ptr(vc), C.byref(ll), _np_dp(beta), C.byref(ld), C.byref(se)),
                          allow=(KRY_ENOCONV,))
         return dict(loglik=ll.value, beta=beta, logdet=ld.value, logdet_se=se.value, mean_cells=mc, mean_sites=ms,
@@ -345,17 +388,22 @@ class Context:
     def sample(self, cov, M1, M2, xi):
         """xi: (2, M1, M2) float64 CUDA normals.  Returns the (n1, n2) float64 field."""
         out = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=xi.device)
-        self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, _ptr(xi.contiguous()), _ptr(out)))
+        pxi = _dev((xi.contiguous(), F64, 2 * M1 * M2, "xi"))
+        self._check(_lib.kry_sample(self.h, C.byref(make_cov(cov)), M1, M2, pxi, _ptr(out)))
         return out
 
     def bootstrap_var(self, cov, opts: Opts, xi, eps, cells):
         """Parametric-bootstrap kriging MSE at grid cells.  xi: (nrep, 2, M1, M2) float64 CUDA white
         noise, eps: (nrep, p) float64 CUDA, cells: (ncell,) int64 CUDA.  Returns (var, status)."""
         xi, eps, cells = xi.contiguous(), eps.contiguous(), cells.contiguous()
+        if xi.dim() != 4 or xi.shape[1] != 2:
+            raise ValueError(f"xi: expected (nrep, 2, M1, M2), got {tuple(xi.shape)}")
         nrep, _, M1, M2 = xi.shape
         var = self.torch.empty(cells.shape[0], dtype=self.torch.float64, device=xi.device)
+        pxi, peps, pc = _dev((xi, F64, nrep * 2 * M1 * M2, "xi"), (eps, F64, nrep * self.p, "eps"),
+                             (cells, I64, cells.numel(), "cells"))
         st = self._check(_lib.kry_bootstrap_var(self.h, C.byref(make_cov(cov)), C.byref(opts.c()), nrep, M1, M2,
-                                                _ptr(xi), _ptr(eps), _ptr(cells), cells.shape[0], _ptr(var)),
+                                                pxi, peps, pc, cells.shape[0], _ptr(var)),
                          allow=(KRY_ENOCONV,))
         return var, st
 
@@ -369,7 +417,8 @@ class Context:
         grad = np.zeros(3) if gradient else None
         al, be = np.zeros(k + 1), np.zeros(k + 1)
         z2, psi2, pl = C.c_double(), C.c_double(), C.c_double()
-        self._check(_lib.kry_genhybr(self.h, C.byref(make_cov(cov)), _ptr(b), k, _ptr(x), _np_dp(al), _np_dp(be),
+        pb = _dev((b, F64, self.p, "b"))
+        self._check(_lib.kry_genhybr(self.h, C.byref(make_cov(cov)), pb, k, _ptr(x), _np_dp(al), _np_dp(be),
                                      C.byref(z2), C.byref(psi2), C.byref(pl), _np_dp(grad), _ptr(psi)))
         return dict(x=x, alphas=al, betas=be, z2=z2.value, psi2=psi2.value, pl=pl.value, grad=grad, psi=psi)
 

@@ -97,3 +97,45 @@ def test_binding_refuses_host_and_strided_tensors(libpath):
     assert kry._ptr(None) is None
     with pytest.raises(ValueError, match="CUDA tensor"):
         kry._ptr(torch.zeros(4, dtype=torch.float64))
+
+
+def test_binding_checks_dtype_and_size_before_calling_the_library(libpath):
+    """Every device buffer is checked against the dtype and element count the C ABI will read, so
+    a wrong dtype or a short buffer raises in Python instead of being read out of bounds.  The
+    context here is never created in the library: each call must raise before reaching it."""
+    torch = pytest.importorskip("torch")
+    import weakref
+
+    from paper_2012_13133_gb300 import kry
+
+    ctx = object.__new__(kry.Context)
+    ctx.h, ctx.p, ctx.n1, ctx.n2, ctx.torch, ctx._embeds = None, 10, 4, 4, torch, weakref.WeakSet()
+    emb = object.__new__(kry.Embed)
+    emb.ctx, emb.handle, emb.min_over_max, emb.prec = ctx, None, 1.0, kry.KRY_F32
+    f32 = lambda *s: torch.zeros(*s, dtype=torch.float32)  # noqa: E731
+    f64 = lambda *s: torch.zeros(*s, dtype=torch.float64)  # noqa: E731
+    opts = kry.Opts()
+    cov = kry.kry_cov(1.0, 0.1, 0.5, 0.1, 0.0, 1.0)
+    cases = [
+        (lambda: ctx.matvec(emb, f64(10)), "dtype float32"),
+        (lambda: ctx.matvec(emb, f32(9)), r"\(nvec, 10\)"),
+        (lambda: ctx.matvec(emb, f32(2, 10), out=f32(1, 10)), "out: expected 20"),
+        (lambda: ctx.matvec(emb, f32(2, 10)), "CUDA tensor"),
+        (lambda: ctx.solve(emb, f32(2, 10)), "B: expected dtype float64"),
+        (lambda: ctx.profile_loglik(f64(10), f64(3, 9), [cov], opts), "X: expected 30"),
+        (lambda: ctx.profile_loglik(f64(10), f64(3, 10), [cov], opts), "CUDA tensor"),
+        (lambda: ctx.krige(cov, opts, f64(10), f64(3, 10), cells=f64(5), Xc=f64(3, 5)), "cells: expected dtype int64"),
+        (lambda: ctx.loglik_krige(cov, opts, f64(10), f64(3, 10), cells=torch.zeros(5, dtype=torch.int64),
+                                  Xc=f64(3, 4)), "Xc: expected 15"),
+        (lambda: ctx.genhybr(cov, f64(11), 5), "b: expected 10"),
+        (lambda: ctx.sample(cov, 8, 8, f64(2, 8, 4)), "xi: expected 128"),
+        (lambda: ctx.bootstrap_var(cov, opts, f64(3, 8, 8), f64(3, 10), torch.zeros(2, dtype=torch.int64)),
+         r"\(nrep, 2, M1, M2\)"),
+        (lambda: ctx.bootstrap_var(cov, opts, f64(3, 2, 8, 8), f64(3, 9), torch.zeros(2, dtype=torch.int64)),
+         "eps: expected 30"),
+        (lambda: ctx.set_mask(f32(4, 4)), "mask: expected dtype"),
+        (lambda: ctx.set_mask(torch.zeros(4, 4, dtype=torch.uint8)), "CUDA tensor"),
+    ]
+    for call, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            call()
