@@ -453,6 +453,17 @@ class Server:
         y = np.ascontiguousarray(y, dtype=np.float64)
         X = np.ascontiguousarray(X, dtype=np.float64)
         ncov = X.shape[0]
+        # the library reads p values of y and X, and N - p of the kriging targets, from the mask alone
+        p = int(np.count_nonzero(m))
+        if m.ndim != 2 or y.size != p or X.ndim != 2 or X.size != ncov * p:
+            raise ValueError(f"request: mask (n1, n2) with p = {p} observed cells needs y ({p},) and X (ncov, {p}); "
+                             f"got mask {m.shape}, y {y.shape}, X {X.shape}")
+        if kind == KRY_REQ_KRIGE:
+            nt = m.size - p
+            if target_cells is None or target_X is None or np.size(target_cells) != nt or \
+                    np.size(target_X) != ncov * nt:
+                raise ValueError(f"kriging request: target_cells ({nt},) and target_X (ncov, {nt}) are required "
+                                 "(every unobserved cell)")
         out = dict(loglik=np.zeros(1), logdet=np.zeros(1), beta=np.zeros(ncov))
         keep = [m, y, X]
         r = kry_request()

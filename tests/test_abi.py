@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -139,3 +140,25 @@ def test_binding_checks_dtype_and_size_before_calling_the_library(libpath):
     for call, msg in cases:
         with pytest.raises(ValueError, match=msg):
             call()
+
+
+def test_server_requests_are_sized_against_their_mask(libpath):
+    """The server reads p values of y and X and N - p kriging targets, counted from the mask alone;
+    requests whose buffers disagree are refused in Python before any library call."""
+    from paper_2012_13133_gb300 import kry
+
+    srv = object.__new__(kry.Server)
+    srv.h, srv._live = None, {}
+    mask = np.zeros((4, 5), dtype=np.uint8)
+    mask[:2] = 1                                   # p = 10, N - p = 10
+    cov = kry.kry_cov(1.0, 0.1, 0.5, 0.1, 0.0, 1.0)
+    opts = kry.Opts()
+    with pytest.raises(ValueError, match="needs y"):
+        srv.submit(kry.KRY_REQ_LOGLIK, mask, np.zeros(9), np.zeros((3, 10)), cov, opts)
+    with pytest.raises(ValueError, match="needs y"):
+        srv.submit(kry.KRY_REQ_LOGLIK, mask, np.zeros(10), np.zeros((3, 9)), cov, opts)
+    with pytest.raises(ValueError, match="every unobserved cell"):
+        srv.submit(kry.KRY_REQ_KRIGE, mask, np.zeros(10), np.zeros((3, 10)), cov, opts,
+                   target_cells=np.arange(10, 19), target_X=np.zeros((3, 9)))
+    with pytest.raises(ValueError, match="every unobserved cell"):
+        srv.submit(kry.KRY_REQ_KRIGE, mask, np.zeros(10), np.zeros((3, 10)), cov, opts)
