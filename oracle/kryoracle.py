@@ -23,7 +23,14 @@ notes of the repository):
     stochastic trace alternative of Sec. 3.3) with Rademacher probes drawn from
     splitmix64 counters;
   * the kriging variance is the simple-kriging variance (the quantity the
-    bootstrap of Sec. 3.5, Eq. bootstrap_uq, estimates).
+    bootstrap of Sec. 3.5, Eq. bootstrap_uq, estimates);
+  * Alg. 1's beta_{i+1} step is read as ||A Sigma v_i - alpha_i u_i|| / tau, like
+    beta_1, which U^T U = tau^2 I (Eq. exact_arith) requires;
+  * the BCCB log-determinant of Sec. 3.3 is offered in two readings: "literal"
+    (the (2n-1)-torus, first n1 x n2 frequencies) and "scaled" (the matvec's
+    power-of-two torus, all frequencies, times n1 n2 / (M1 M2));
+  * the Wendland weights of Sec. 2 are normalised over the cell centres that
+    exist, so near the border of the grid a site may have fewer than four.
 
 Parity of the paper's own tables is unpinned: they are replicate averages of
 unpublished random data and fix no value of this path.
