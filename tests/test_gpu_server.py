@@ -5,7 +5,6 @@ import numpy as np
 import pytest
 
 from oracle import kryoracle as O
-from paper_2012_13133_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
