@@ -46,6 +46,13 @@ class Opts:
     prec = 1  # KRY_F64: the oracle's objective is smooth to rounding
 
 
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    """The fit imports the binding (for its status codes), which loads the built library."""
+    from paper_2012_13133_gb300.build import build_library
+    return build_library()
+
+
 @pytest.fixture(scope="module")
 def problem():
     mask = I.mask_uniform(N1, N2, 0.3, 21)
