@@ -132,17 +132,23 @@ kry_status kry_matvec(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void*
 
 /* Allocation-free form of kry_matvec (the paper has no counterpart; this is a
  * deployment aid).  Same arguments and result as kry_matvec, for callers that
- * cannot allocate device memory at call time: work recorded under a
- * global-mode CUDA stream capture (where cudaMalloc is not allowed), hosts
- * whose device memory is owned by their own pool, and latency-critical loops
- * that cannot absorb the device synchronisation of cudaMalloc/cudaFree.
- * The FFT intermediate lives in a 16 MiB static device array of the library
- * (held by every GPU that loads it, until exit), so n1 * M2 * sizeof(complex)
- * must not exceed 16 MiB (e.g. grids up to 1024 x 1024 in FP32); larger grids
- * return KRY_EUNSUPPORTED.  The call performs no allocation itself; ctx, its
- * mask and e must be set up beforehand.  The first call on a device looks up
- * the array's address: make it before any stream capture.  All calls on a
- * device share the array: calls that overlap on the GPU race.  Asynchronous. */
+ * cannot allocate device memory at call time: applications whose device
+ * memory is all owned by their own pool or arena (cudaMalloc would fail or
+ * fragment it), and latency-critical loops that cannot absorb the
+ * device-wide synchronisation of cudaMalloc / cudaFree.  It runs the same FFT
+ * passes under the same launch schedule as kry_matvec, so on the same context
+ * the two agree bit for bit; only the FFT intermediate differs: it lives in a
+ * 16 MiB static device array of the library (held by every GPU that loads it,
+ * until exit) and is filled as many complex pairs at a time as fit.  Hence
+ * n1 * M2 * sizeof(complex) must not exceed 16 MiB (grids up to 1024 x 1024
+ * in FP32, 1024 x 512 in FP64); larger grids return KRY_EUNSUPPORTED with a
+ * message.  The call performs no allocation itself; ctx, its mask and e must
+ * be set up beforehand (their creation allocates).  The first call on a
+ * device (and the first after that device's CUDA context changes, e.g. after
+ * cudaDeviceReset) looks up the array's device address: make it before any
+ * stream capture.  All calls on a device share the array and it keeps the
+ * last call's contents: calls that overlap on the GPU race, so the caller
+ * must serialise them.  Asynchronous. */
 kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_dev, void* out_dev,
                               int32_t nvec, int64_t ld);
 

@@ -46,14 +46,11 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_library(verbose: bool = False, extra_flags=None, tag: str = "") -> str:
-    """Compile (if stale) and return the path of libkry.so.  A non-empty tag
-    builds a variant (own object directory, libkry<tag>.so) with extra_flags."""
-    BUILD = os.path.join(PKG, "_build" + tag)
-    LIB = os.path.join(PKG, f"libkry{tag}.so")
+def build_library(verbose: bool = False) -> str:
+    """Compile (if stale) and return the path of libkry.so."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = nvcc_path()
-    flags = ARCH + NVFLAGS + ["-I", os.path.join(ROOT, "include")] + list(extra_flags or [])
+    flags = ARCH + NVFLAGS + ["-I", os.path.join(ROOT, "include")]
     common = _deps()
     objs, jobs = [], []
     for src in sources():

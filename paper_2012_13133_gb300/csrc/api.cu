@@ -351,8 +351,6 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         KRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
         KRY_CUDA(cudaMallocHost(&ctx->host_pinned, 4096 * sizeof(double)));
         kry::init_twiddles(ctx);
-        const char* gen = getenv("KRY_MATVEC_GENERIC");
-        ctx->use_spec = !(gen && gen[0] == '1');
         KRY_CUDA(cudaStreamSynchronize(ctx->stream));
         return KRY_OK;
     });

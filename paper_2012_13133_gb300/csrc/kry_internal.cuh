@@ -101,9 +101,8 @@ struct kry_ctx {
     // shared twiddle tables, W[k] = exp(-2 pi i k / KRY_TWN), and the FP32
     // stage table of the specialised passes (row Ns - 1 + k: W_{16 Ns}^{k m})
     DevBuf tw32, tw64, twt32;
-    // FP32 matvecs use the length-specialised passes where they apply (set
-    // KRY_MATVEC_GENERIC=1 in the environment to time the generic radix-16
-    // passes instead; both compute the same transform)
+    // FP32 matvecs use the length-specialised passes where they apply (the
+    // generic radix-16 passes compute the same transform for the other shapes)
     bool use_spec = true;
 
     // scratch

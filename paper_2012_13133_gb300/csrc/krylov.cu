@@ -485,9 +485,10 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
 }
 
 // Gauss quadrature of z^T log(K) z from the Lanczos tridiagonal: implicit QL
-// iterations with Wilkinson shifts (Bowdler, Martin, Reinsch & Wilkinson,
-// "The QR and QL algorithms for symmetric matrices", Numer. Math. 1968),
-// rotating only the first row of the eigenvector matrix (Golub & Welsch 1969).
+// iterations with Wilkinson shifts, the published procedure tql2 (Bowdler,
+// Martin, Reinsch & Wilkinson, "The QR and QL algorithms for symmetric
+// matrices", Numer. Math. 1968; EISPACK's tql2), rotating only the first row of
+// the eigenvector matrix (Golub & Welsch 1969).
 __global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, double znorm2, double* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprobe) return;

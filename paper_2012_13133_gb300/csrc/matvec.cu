@@ -834,18 +834,21 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
 // ------------------------------------------------------------------ allocation-free matvec
 //
 // kry_matvec_noalloc serves callers that cannot allocate device memory when
-// they call: code recorded into a CUDA graph under global-mode stream capture
-// (where cudaMalloc is not permitted), applications whose device memory is all
-// owned by their own pool, and latency-critical loops that cannot afford the
-// device-wide synchronisation of cudaMalloc / cudaFree.  It launches the same
-// three FFT passes as kry_matvec, but its slab lives in a fixed file-scope
-// device array instead of context scratch.  The array is part of the module,
-// so every GPU that loads this library holds it until the process exits.
+// they call: applications whose device memory is all owned by their own pool
+// or arena (a framework's caching allocator that has reserved the GPU), and
+// latency-critical loops that cannot absorb the device-wide synchronisation of
+// cudaMalloc / cudaFree.  It runs the same FFT passes as kry_matvec, chosen by
+// the same schedule, but its slab lives in a fixed file-scope device array
+// instead of context scratch, taking as many complex pairs per batch as the
+// array holds.  The array is part of the module, so every GPU that loads this
+// library holds it until the process exits.
 //
 // Set-up: the first call on a device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current) and caches it; make that
-// first call before any stream capture.  The context, its mask and the
-// embedding must already exist (creating them does allocate).
+// (cudaGetSymbolAddress, with that device current) and caches it with the
+// identity of the device's current CUDA context; a later call under another
+// context (after cudaDeviceReset, say) looks it up again.  Make that first call
+// before any stream capture.  The context, its mask and the embedding must
+// already exist (creating them does allocate).
 //
 // Sharing: every call on a device uses the same array and it keeps the last
 // call's contents.  Nothing needs clearing, because pass A writes every slab
@@ -858,23 +861,58 @@ void sigma_to_grid64(kry_ctx* ctx, const kry_embed* e, const double* vin, double
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[KRY_NOALLOC_SCRATCH_BYTES];
 
+struct NoallocSlot {
+    void* addr = nullptr;
+    unsigned long long ctx_id = 0;
+};
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[KRY_NOALLOC_MAX_DEVICES] = {};
+static NoallocSlot g_noalloc_slot[KRY_NOALLOC_MAX_DEVICES];
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Identity of the calling thread's current CUDA context (driver entry points
+// cuCtxGetCurrent / cuCtxGetId, looked up through the runtime), 0 if unknown.
+static unsigned long long current_ctx_id() {
+    typedef int (*GetCurrentFn)(void**);
+    typedef int (*GetIdFn)(void*, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {   // under g_noalloc_mu
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrentFn>(f1);
+            get_id = reinterpret_cast<GetIdFn>(f2);
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    void* c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != 0 || c == nullptr || get_id(c, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device and context).
 static void* noalloc_scratch(int device) {
     KRY_REQUIRE(device >= 0 && device < KRY_NOALLOC_MAX_DEVICES, KRY_EUNSUPPORTED,
                 "device index too large for the allocation-free matvec");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_addr[device] == nullptr) {
+    NoallocSlot& slot = g_noalloc_slot[device];
+    const unsigned long long id = current_ctx_id();
+    if (slot.addr == nullptr || slot.ctx_id != id) {
         void* ptr = nullptr;
         cudaError_t err = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
         if (err != cudaSuccess)
             throw KryError{KRY_ECUDA, std::string("cudaGetSymbolAddress of the static matvec scratch failed: ") +
                                           cudaGetErrorString(err)};
-        g_noalloc_addr[device] = ptr;
+        slot.addr = ptr;
+        slot.ctx_id = id;
     }
-    return g_noalloc_addr[device];
+    return slot.addr;
 }
 
 template <typename T>
@@ -883,14 +921,26 @@ static void run_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const T* vin, T
     using Cx = typename cx_of<T>::type;
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
-    MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, M1, M2, dbl);
     const size_t slab_pair = (size_t)n1 * M2 * cx_size(dbl);
     KRY_REQUIRE(slab_pair <= KRY_NOALLOC_SCRATCH_BYTES, KRY_EUNSUPPORTED,
                 "grid too large for the allocation-free matvec: n1 * M2 * sizeof(complex) = " +
                     std::to_string(slab_pair) + " bytes exceeds its 16 MiB static scratch");
     const int npairs = (nvec + 1) / 2;
-    const int ppb = std::max(1, std::min(npairs, (int)(KRY_NOALLOC_SCRATCH_BYTES / slab_pair)));
+    const int cap = std::max(1, (int)(KRY_NOALLOC_SCRATCH_BYTES / slab_pair));
     Cx* slab = static_cast<Cx*>(scratch);
+    const double tau2 = e->cov.tau2;
+    if (use16(M1, M2)) {
+        // the passes and schedule of kry_matvec, with at most `cap` pairs per batch
+        const MvSched& want = sched_for(ctx, M1, M2, dbl, nvec);
+        int ppb = want.pairs_per_batch > 0 ? std::min(want.pairs_per_batch, npairs) : npairs;
+        ppb = std::min(ppb, cap);
+        run_matvec16<T>(ctx, e, vin, ld, nullptr, vout, ld, nvec, tau2, nullptr, 0, 0, slab, ppb, 0, nullptr);
+        return;
+    }
+    // transform lengths below 64: the generic radix-8 passes, as kry_matvec
+    MvSched s = pick_sched(ctx, dbl ? ctx->sched64 : ctx->sched32, M1, M2, dbl);
+    int ppb = s.pairs_per_batch > 0 ? std::min(s.pairs_per_batch, npairs) : npairs;
+    ppb = std::min(ppb, cap);
     const T* lamT = dbl ? reinterpret_cast<const T*>(e->lam64T) : reinterpret_cast<const T*>(e->lam32T);
     const int C = s.cols_per_cta;
     const int G = s.rows_per_cta;
@@ -904,7 +954,6 @@ static void run_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const T* vin, T
     const int thrB = C * (M1 / s.ept_col);
     const size_t smB = (size_t)C * (M1 + 1) * cx_size(dbl);
     const int nbx = (n1 + G - 1) / G;
-    const double tau2 = e->cov.tau2;
     for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
         const int np = std::min(ppb, npairs - pair0);
         dim3 gA(nbx, np), gB(M2 / C, np);
@@ -912,11 +961,12 @@ static void run_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const T* vin, T
                         (MvLaunch<T>::template a<E_, G_>(gA, thrA, smA, st, vin, ld, nullptr, nvec, pair0, rowptr,
                                                          colidx, n1, M2, C, slab, tw32, tw64)));
         KRY_DISPATCH_EG(s.ept_col, C,
-                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64)));
+                        (MvLaunch<T>::template b<E_, G_>(gB, thrB, smB, st, slab, lamT, n1, M1, M2, tw32, tw64, pair0,
+                                                         e->lam_stride, 0)));
         KRY_DISPATCH_EG(s.ept_row, G,
                         (MvLaunch<T>::template c<E_, G_, 0>(gA, thrA, smA, st, slab, vin, ld, nullptr, vout, ld,
                                                             nvec, pair0, rowptr, colidx, n1, n2, M2, C, tau2,
-                                                            nullptr, 0, tw32, tw64)));
+                                                            nullptr, 0, tw32, tw64, e->tau2_dev, 0)));
     }
 }
 

@@ -1,18 +1,26 @@
 """Allocation-free matvec (kry_matvec_noalloc).
 
-Some callers cannot allocate device memory when they call the library: work
-captured into a CUDA graph in global capture mode, hosts whose device memory
-is all owned by their own pool, and loops that cannot absorb cudaMalloc's
-device synchronisation.  kry_matvec_noalloc serves them with a static device
-scratch array.  This file checks, through the C ABI, that two calls in a row
-give the same result as kry_matvec (within the FP32 matvec tolerance of the
-parity tests), that it takes no device memory, and that grids too large for
-its scratch are refused.  It is named so that pytest collects it last."""
+Some callers cannot allocate device memory when they call the library: hosts
+whose device memory is all owned by their own pool or arena, and loops that
+cannot absorb the device-wide synchronisation of cudaMalloc / cudaFree.
+kry_matvec_noalloc serves them with a static device scratch array.  This file
+checks, through the C ABI, on two calls in a row:
+
+* that its result equals kry_matvec's (same passes, same schedule) and, within
+  the parity tests' tolerances, the FP64 oracle's (1e-5 relative in FP32,
+  1e-12 in FP64);
+* at 1024 x 1024 in FP32, where one complex pair fills the scratch, that a
+  five-vector call runs its three batches correctly;
+* that the second call takes no device memory;
+* that grids too large for the scratch are refused with a message.
+
+It is named so that pytest collects it last."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+from oracle import kryoracle as O
 from paper_2012_13133_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -24,7 +32,7 @@ if not torch.cuda.is_available():
 from paper_2012_13133_gb300 import kry  # noqa: E402
 
 DEV = torch.device("cuda:0")
-TOL = 1e-5   # FP32 matvec relative l2 tolerance used by the parity tests
+TOL = {kry.KRY_F32: 1e-5, kry.KRY_F64: 1e-12}   # matvec relative l2 tolerances of the parity tests
 
 
 def _noalloc(ctx, emb, V, out):
@@ -33,14 +41,26 @@ def _noalloc(ctx, emb, V, out):
                                   V.shape[0], V.shape[1])
 
 
-def test_noalloc_matches_matvec_twice():
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n1,n2,prec,nvec", [
+    (300, 260, kry.KRY_F32, 7),      # several pairs in one batch
+    (200, 170, kry.KRY_F64, 5),      # FP64 passes
+    (1024, 1024, kry.KRY_F32, 5),    # one pair per batch: three batches
+])
+def test_noalloc_matches_matvec_and_oracle_twice(n1, n2, prec, nvec):
     ctx = kry.Context(0)
-    n1, n2 = 300, 260
     mask = I.mask_uniform(n1, n2, 0.5, 3)
+    cov = I.Cov(1.0, 0.05, 1.5, 0.05)
     p = ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(DEV))
-    emb = ctx.embed(I.Cov(1.0, 0.05, 1.5, 0.05), kry.KRY_F32)
-    V = torch.tensor(I.normals((7, p), 21), dtype=torch.float32, device=DEV)
-    ref = ctx.matvec(emb, V)
+    emb = ctx.embed(cov, prec)
+    dt = torch.float32 if prec == kry.KRY_F32 else torch.float64
+    Vh = I.normals((nvec, p), 21)
+    V = torch.tensor(Vh, dtype=dt, device=DEV)
+    ref_lib = ctx.matvec(emb, V)
+    ref = O.FFTProblem(n1, n2, mask, cov).matvec(V.double().cpu().numpy())
     torch.cuda.synchronize()
     for call in range(2):
         out = torch.full_like(V, float("nan"))
@@ -50,9 +70,12 @@ def test_noalloc_matches_matvec_twice():
         torch.cuda.synchronize()
         free1 = torch.cuda.mem_get_info(0)[0]
         assert st == kry.KRY_OK, kry.lib().kry_last_error(ctx.h)
-        for k in range(V.shape[0]):
-            err = float(torch.linalg.norm(out[k].double() - ref[k].double()) / torch.linalg.norm(ref[k].double()))
-            assert err <= TOL, (call, k, err)
+        got = out.double().cpu().numpy()
+        lib = ref_lib.double().cpu().numpy()
+        for k in range(nvec):
+            assert _rel(got[k], lib[k]) <= TOL[prec], (call, k)
+            assert _rel(got[k], ref[k]) <= TOL[prec], (call, k, _rel(got[k], ref[k]))
+        assert np.array_equal(got, lib), (call, np.abs(got - lib).max())
         if call == 1:
             # the first call may load the module that holds the static array;
             # the second must not take any device memory
