@@ -1,11 +1,23 @@
 """Parity at the benchmark's full size (grid1024: 1024 x 1024 grid, 50% observed,
 Matern 3/2, range 0.05, nugget 0.05) in the launch configuration bench.py
 times: 64 probes x 60 Lanczos steps in one batch with partial
-reorthogonalisation, CG on the four right-hand sides [y, X].  The oracle
-computes sampled outputs one by one (two probes' quadrature values, with full
-reorthogonalisation); the solve is checked through the property that defines
-it, with the FP64 matvec whose full-size parity is tested elsewhere."""
+reorthogonalisation, FP32 CG on the four right-hand sides [y, X] to a true
+relative residual of 1e-6, GLS, and the kriging mean at all 524,288
+unobserved cells.
+
+The data are the oracle's: y = X beta + x + tau eps with x drawn by the
+oracle's circulant-embedding sampler from the seeded white noise.  The
+expected values come from tests/golden/grid1024_oracle.npz, written by
+tests/golden/make_fullsize.py, which calls only the FP64 oracle: the 64
+per-probe quadrature values with the same probes and a fully
+reorthogonalised basis (the exact Gauss rule), CG to 1e-10, the GLS beta, the
+log-likelihood and every kriging mean.
+
+Tolerances (stated in the test): per-probe values, log det and loglik 1e-3
+relative (the log-det tolerance at the stated probe and step counts); the
+kriging means 1e-4 relative l2 over all targets; beta 1e-4 relative l2."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -23,33 +35,75 @@ from paper_2012_13133_gb300 import kry  # noqa: E402
 
 DEV = torch.device("cuda:0")
 W = I.WORKLOADS["grid1024"]
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "grid1024_oracle.npz")
+
+TOL_LOGDET = 1e-3
+TOL_MEAN = 1e-4
+TOL_BETA = 1e-4
+
+
+def oracle_data(w):
+    """The golden script's data recipe (oracle sampler on its PSD torus)."""
+    from tests.golden.make_fullsize import oracle_data as od
+    return od(w)
 
 
 @pytest.fixture(scope="module")
 def problem():
+    gold = dict(np.load(GOLD))
+    mask, X, y, M1, M2 = oracle_data(W)
+    assert (M1, M2) == tuple(gold["sample_M"])
+    assert float(y.sum()) == pytest.approx(float(gold["y_sum"]), rel=1e-9, abs=1e-6)
+    assert float(np.linalg.norm(y)) == pytest.approx(float(gold["y_norm"]), rel=1e-12)
     ctx = kry.Context(0)
-    mask = I.make_mask(W)
     p = ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(DEV))
-    S1, S2 = I.cell_centres(W.n1, W.n2)
-    X = I.covariates(S1[mask], S2[mask])
-    M1, M2, _ = ctx.sample_size(W.cov)
-    xi, eps = I.data_noise(M1, M2, p, W.data_seed)
-    field = ctx.sample(W.cov, M1, M2, torch.tensor(xi, device=DEV)).cpu().numpy()
-    y = X @ np.array(W.beta) + field[mask] + math.sqrt(W.cov.tau2) * eps
-    yield dict(ctx=ctx, mask=mask, p=p, X=X, y=y)
+    assert p == int(gold["p"])
+    yield dict(ctx=ctx, mask=mask, p=p, X=X, y=y, gold=gold)
     ctx.close()
 
 
-def test_logdet_probes_match_oracle_at_full_size(problem):
-    ctx = problem["ctx"]
+def _opts():
+    return kry.Opts(prec=kry.KRY_F32, nprobe=W.nprobe, nsteps=W.nsteps, seed=W.probe_seed, rtol=W.cg_tol,
+                    maxit=20000, reorth=W.reorth)
+
+
+def test_loglik_and_kriging_means_match_oracle_at_full_size(problem):
+    ctx, y, X, mask, gold = problem["ctx"], problem["y"], problem["X"], problem["mask"], problem["gold"]
     emb = ctx.embed(W.cov, kry.KRY_F32)
     ctx.autotune(emb, W.nprobe)
-    ld, se, per = ctx.logdet(emb, W.nprobe, W.nsteps, W.probe_seed, reorth=1)
-    P = O.FFTProblem(W.n1, W.n2, problem["mask"], W.cov)
-    _, _, ref = P.logdet(W.nprobe, W.nsteps, W.probe_seed, probe_ids=[0, W.nprobe - 1], reorth=True)
-    assert per[0] == pytest.approx(ref[0], rel=1e-3)
-    assert per[-1] == pytest.approx(ref[1], rel=1e-3)
+    ctx.autotune(emb, X.shape[1] + 1)
     emb.free()
+    cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+    S1, S2 = I.cell_centres(W.n1, W.n2)
+    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+    res = ctx.loglik_krige(W.cov, _opts(), torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV),
+                           cells=torch.tensor(cells, device=DEV), Xc=torch.tensor(Xc.T.copy(), device=DEV))
+    assert res["status"] == kry.KRY_OK
+    ld_err = abs(res["logdet"] - float(gold["logdet"])) / abs(float(gold["logdet"]))
+    ll_err = abs(res["loglik"] - float(gold["loglik"])) / abs(float(gold["loglik"]))
+    beta_err = np.linalg.norm(res["beta"] - gold["beta"]) / np.linalg.norm(gold["beta"])
+    mc = res["mean_cells"].cpu().numpy()
+    ref = gold["means"].astype(np.float64)
+    mean_err = np.linalg.norm(mc - ref) / np.linalg.norm(ref)
+    print(f"grid1024 vs oracle: logdet {ld_err:.2e}, loglik {ll_err:.2e}, beta {beta_err:.2e}, means {mean_err:.2e}")
+    assert ld_err <= TOL_LOGDET
+    assert ll_err <= TOL_LOGDET
+    assert beta_err <= TOL_BETA
+    assert mc.shape == ref.shape and mean_err <= TOL_MEAN
+
+
+def test_every_probe_matches_oracle_at_full_size(problem):
+    ctx, gold = problem["ctx"], problem["gold"]
+    emb = ctx.embed(W.cov, kry.KRY_F32)
+    ctx.autotune(emb, W.nprobe)
+    ld, se, per = ctx.logdet(emb, W.nprobe, W.nsteps, W.probe_seed, reorth=W.reorth)
+    emb.free()
+    ref = gold["per_probe"]
+    assert per.shape == ref.shape == (W.nprobe,)
+    err = np.abs(per - ref) / np.abs(ref)
+    print(f"grid1024 per-probe quadrature vs oracle: max {err.max():.2e}, median {np.median(err):.2e}")
+    assert err.max() <= TOL_LOGDET
+    assert ld == pytest.approx(float(gold["logdet"]), rel=TOL_LOGDET)
 
 
 def test_solve_meets_its_residual_at_full_size(problem):
@@ -66,39 +120,6 @@ def test_solve_meets_its_residual_at_full_size(problem):
         assert r <= W.cg_tol * 1.0001, (k, r)
     emb32.free()
     emb64.free()
-
-
-def test_loglik_krige_assembles_its_parts_at_full_size(problem):
-    ctx = problem["ctx"]
-    y, X = problem["y"], problem["X"]
-    yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
-    opts = kry.Opts(prec=kry.KRY_F32, nprobe=W.nprobe, nsteps=W.nsteps, seed=W.probe_seed, rtol=W.cg_tol,
-                    maxit=20000, reorth=1)
-    cells = np.flatnonzero(~problem["mask"].ravel()).astype(np.int64)
-    S1, S2 = I.cell_centres(W.n1, W.n2)
-    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
-    res = ctx.loglik_krige(W.cov, opts, yt, Xt, cells=torch.tensor(cells, device=DEV),
-                           Xc=torch.tensor(Xc.T.copy(), device=DEV))
-    assert res["status"] == kry.KRY_OK
-    # the same pieces through the separate entry points
-    emb = ctx.embed(W.cov, kry.KRY_F32)
-    ld, _, _ = ctx.logdet(emb, W.nprobe, W.nsteps, W.probe_seed, reorth=1)
-    Z, _, _, st = ctx.solve(emb, torch.tensor(np.vstack([y, X.T]), device=DEV), rtol=W.cg_tol, maxit=20000)
-    Z = Z.cpu().numpy()
-    # GLS from the symmetrised Gram matrix of [y, X] and K^-1 [y, X] (symmetric in
-    # exact arithmetic; the two triangles differ at the CG tolerance)
-    A = X.T @ Z[1:].T
-    g = 0.5 * (X.T @ Z[0] + Z[1:] @ y)
-    beta = np.linalg.solve(0.5 * (A + A.T), g)
-    quad = y @ Z[0] - beta @ g
-    ll = -0.5 * (ld + quad + y.size * math.log(2 * math.pi))
-    assert res["logdet"] == pytest.approx(ld, rel=1e-9)
-    assert np.allclose(res["beta"], beta, rtol=1e-5, atol=1e-7)
-    assert res["loglik"] == pytest.approx(ll, rel=1e-6)
-    # the kriging means honour the trend at cells far from any data (here: all finite)
-    mc = res["mean_cells"].cpu().numpy()
-    assert np.all(np.isfinite(mc)) and mc.shape == (cells.size,)
-    emb.free()
 
 
 def test_bccb_logdet_at_full_size(problem):
