@@ -112,6 +112,26 @@ const char* kry_last_error(const kry_ctx* ctx);
  * Requires 4 <= n1, n2 <= 4096 and p >= 1.  Synchronises the stream. */
 kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_dev, int64_t* p_out);
 
+/* Irregular observation sites (Sec. 2: y = X beta + A x + eps with A the
+ * p x n mapping matrix of Wendland weights).  sites_dev holds nsite (x1, x2)
+ * FP64 pairs, row-major, inside the domain [0, n1 dx1] x [0, n2 dx2]; the
+ * latent field x lives on the cell centres of grid.  Row i of A weights the
+ * cell centres c_j within one spacing of site s_i along both axes (at most
+ * 2 x 2 of them) by w(d_ij) / sum_k w(d_ik), w(d) = (1 - d)^4 (1 + 4 d) for
+ * d < 1, d_ij = max(|s_i1 - c_j1| / dx1, |s_i2 - c_j2| / dx2); near the border
+ * the centres that exist are normalised over.  A is built on the device by
+ * site and by cell (its transpose, each cell's entries in site order, so
+ * results do not depend on scheduling).  Afterwards p = nsite and every
+ * matvec, log-determinant, solve, likelihood and kriging call on ctx uses
+ * K = sigma2 A Sigma A^T + tau2 I (Sigma applied on the whole grid by the
+ * FFT passes); kriging covers grid cells (the mean of y at a cell: trend plus
+ * the latent prediction there), without variances or off-grid targets;
+ * kry_bootstrap_var, kry_genhybr and kry_matvec_noalloc need a mask and return
+ * KRY_EUNSUPPORTED.  kry_set_mask replaces the sites.  Errors: KRY_EINVAL for
+ * a site outside the domain or bad arguments, KRY_EUNSUPPORTED for grid sides
+ * outside [4, 4096].  Synchronises the stream. */
+kry_status kry_set_sites(kry_ctx* ctx, const kry_grid* grid, const double* sites_dev, int64_t nsite);
+
 /* Eigenvalues of the block-circulant embedding of sigma2 * Sigma on the
  * M1 x M2 torus, M_d = smallest power of two >= 2 n_d (Sec. 3.3; Eq. circ_diag).
  * The lag covariance is evaluated in FP64 (closed forms for nu in {1/2, 3/2,

@@ -100,9 +100,15 @@ void ctx_trim(kry_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->slab32, &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->sites.grid32, &ctx->sites.grid64};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
+    if (!ctx->sites.active) {
+        // the whole-grid index lists are rebuilt on demand unless a site map needs them
+        ctx->rowptr_full.release();
+        ctx->colidx_full.release();
+        ctx->full_n1 = ctx->full_n2 = 0;
+    }
 }
 }  // namespace kry
 
@@ -342,7 +348,9 @@ kry_status kry_create(kry_ctx** out, int device, void* cuda_stream) {
         // pool memory cached in this process instead of returning it at each sync
         DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                           &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
+                          &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full,
+                      &ctx->sites.corner, &ctx->sites.w64, &ctx->sites.w32, &ctx->sites.cellptr, &ctx->sites.ent_site,
+                      &ctx->sites.ent_w64, &ctx->sites.ent_w32, &ctx->sites.cnt, &ctx->sites.grid32, &ctx->sites.grid64};
         for (DevBuf* b : bufs) b->stream = ctx->stream;
         for (auto& b : ctx->work) b.stream = ctx->stream;
         cudaMemPool_t pool;
@@ -370,7 +378,9 @@ void kry_destroy(kry_ctx* ctx) {
     else cudaDeviceSynchronize();
     DevBuf* bufs[] = {&ctx->rowptr, &ctx->colidx, &ctx->cellidx, &ctx->tw32, &ctx->tw64, &ctx->twt32, &ctx->slab32,
                       &ctx->slab64, &ctx->scal, &ctx->eig_c, &ctx->eig_z, &ctx->eig_d, &ctx->red, &ctx->tolbuf,
-                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full};
+                      &ctx->kxbuf, &ctx->cbuf, &ctx->sbuf, &ctx->zbuf, &ctx->gbuf, &ctx->boot, &ctx->gk, &ctx->rowptr_full, &ctx->colidx_full,
+                      &ctx->sites.corner, &ctx->sites.w64, &ctx->sites.w32, &ctx->sites.cellptr, &ctx->sites.ent_site,
+                      &ctx->sites.ent_w64, &ctx->sites.ent_w32, &ctx->sites.cnt, &ctx->sites.grid32, &ctx->sites.grid64};
     for (DevBuf* b : bufs) b->release();
     for (auto& b : ctx->work) b.release();
     prof_clear(ctx);
@@ -389,6 +399,7 @@ kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_
         KRY_REQUIRE(grid->dx1 > 0 && grid->dx2 > 0, KRY_EINVAL, "cell sizes must be > 0");
         const int n1 = grid->n1, n2 = grid->n2;
         ctx->p = 0;
+        ctx->sites.active = false;
         ctx->rowptr.ensure((size_t)(n1 + 1) * sizeof(int));
         ctx->colidx.ensure((size_t)n1 * n2 * sizeof(int));
         ctx->cellidx.ensure((size_t)n1 * n2 * sizeof(int));
@@ -412,6 +423,27 @@ kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_
         ctx->dx2 = grid->dx2;
         ctx->p = p;
         if (p_out) *p_out = p;
+        return KRY_OK;
+    });
+}
+
+kry_status kry_set_sites(kry_ctx* ctx, const kry_grid* grid, const double* sites_dev, int64_t nsite) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_REQUIRE(grid && sites_dev, KRY_EINVAL, "grid and sites_dev must not be NULL");
+        KRY_REQUIRE(grid->n1 >= 4 && grid->n2 >= 4, KRY_EUNSUPPORTED, "grid sides must be >= 4");
+        KRY_REQUIRE(grid->n1 <= KRY_MAX_N && grid->n2 <= KRY_MAX_N, KRY_EUNSUPPORTED, "grid sides must be <= 4096");
+        KRY_REQUIRE(grid->dx1 > 0 && grid->dx2 > 0, KRY_EINVAL, "cell sizes must be > 0");
+        KRY_REQUIRE(nsite >= 1 && nsite <= ((int64_t)1 << 29), KRY_EINVAL, "nsite must be in [1, 2^29]");
+        ctx->p = 0;
+        ctx->sites.active = false;
+        const bool ok = kry::build_sites(ctx, grid->n1, grid->n2, grid->dx1, grid->dx2, sites_dev, nsite);
+        KRY_REQUIRE(ok, KRY_EINVAL, "a site lies outside the domain [0, n1 dx1] x [0, n2 dx2] or is not finite");
+        ctx->n1 = grid->n1;
+        ctx->n2 = grid->n2;
+        ctx->dx1 = grid->dx1;
+        ctx->dx2 = grid->dx2;
+        ctx->p = nsite;
+        ctx->sites.active = true;
         return KRY_OK;
     });
 }
@@ -633,8 +665,10 @@ static kry_status krige_from_solution(kry_ctx* ctx, kry_embed* e, const kry_cov&
 
 static void check_krige_args(const kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
                              const int64_t* cells_dev, const double* Xc_dev, int64_t ncell, const double* sites_dev,
-                             const double* Xs_dev, int64_t nsite, double* mean_cells_dev, double* mean_sites_dev) {
-    (void)ctx;
+                             const double* Xs_dev, int64_t nsite, double* mean_cells_dev, double* mean_sites_dev,
+                             double* var_cells_dev) {
+    KRY_REQUIRE(!ctx->sites.active || (nsite == 0 && var_cells_dev == nullptr), KRY_EUNSUPPORTED,
+                "with irregular sites (kry_set_sites) kriging covers grid cells only, without variances");
     KRY_REQUIRE(y_dev && X_dev, KRY_EINVAL, "y_dev and X_dev must not be NULL");
     KRY_REQUIRE(ncov >= 1 && ncov <= KRY_MAX_COV, KRY_EINVAL, "ncov must be in [1, 8]");
     KRY_REQUIRE(ncell >= 0 && nsite >= 0, KRY_EINVAL, "ncell and nsite must be >= 0");
@@ -655,7 +689,7 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
         check_opts(opts);
         check_cov(cov);
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
-                         mean_cells_dev, mean_sites_dev);
+                         mean_cells_dev, mean_sites_dev, var_cells_dev);
         kry_embed* e = make_embed(ctx, cov, opts->prec);
         kry_status st = KRY_OK;
         try {
@@ -686,7 +720,7 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
         check_cov(cov);
         KRY_REQUIRE(loglik != nullptr, KRY_EINVAL, "loglik must not be NULL");
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
-                         mean_cells_dev, mean_sites_dev);
+                         mean_cells_dev, mean_sites_dev, var_cells_dev);
         kry_embed* e = make_embed(ctx, cov, opts->prec);
         kry_status st = KRY_OK;
         try {
@@ -788,6 +822,7 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
         check_cov(cov);
         check_opts(opts);
         require_mask(ctx);
+        KRY_REQUIRE(!ctx->sites.active, KRY_EUNSUPPORTED, "the bootstrap needs an observation mask (kry_set_mask)");
         KRY_REQUIRE(nrep >= 1, KRY_EINVAL, "nrep must be >= 1");
         KRY_REQUIRE(xi_dev && eps_dev, KRY_EINVAL, "xi_dev and eps_dev must not be NULL");
         KRY_REQUIRE(ncell >= 0 && (ncell == 0 || (cells_dev && var_dev)), KRY_EINVAL,
@@ -832,6 +867,7 @@ kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, in
     return guarded(ctx, [&]() -> kry_status {
         check_cov(cov);
         require_mask(ctx);
+        KRY_REQUIRE(!ctx->sites.active, KRY_EUNSUPPORTED, "genHyBR needs an observation mask (kry_set_mask)");
         KRY_REQUIRE(b_dev != nullptr, KRY_EINVAL, "b_dev must not be NULL");
         KRY_REQUIRE(k >= 1 && k <= 4096, KRY_EINVAL, "k must be in [1, 4096]");
         kry::genhybr(ctx, *cov, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);

@@ -116,8 +116,24 @@ struct kry_ctx {
     DevBuf zbuf, gbuf;            // [y, X] and its solve; kriging grid and weights
     DevBuf boot;                  // bootstrap replicates: fields, predictions, right-hand sides, solves
     DevBuf gk;                    // genGK bases and work vectors
-    DevBuf rowptr_full, colidx_full;   // index lists of the whole grid (genGK's Sigma matvec)
+    DevBuf rowptr_full, colidx_full;   // index lists of the whole grid (genGK's and the sites' Sigma matvec)
     int full_n1 = 0, full_n2 = 0;
+    // the FFT passes add no nugget (set while the sites' whole-grid Sigma matvec runs)
+    bool no_nugget = false;
+
+    // irregular observation sites (kry_set_sites): the Wendland mapping matrix
+    // A of Sec. 2 in two forms, by site (the 2 x 2 cells around each site, -1
+    // where the weight is zero, and the normalised weights) and by cell (A^T:
+    // entries [cellptr[c], cellptr[c + 1]) sorted by site), plus the
+    // whole-grid scratch of the site matvec, one buffer per precision (a
+    // captured FP32 CG loop keeps its address while FP64 residual matvecs run
+    // between its replays)
+    struct SiteMap {
+        bool active = false;
+        DevBuf corner, w64, w32;
+        DevBuf cellptr, ent_site, ent_w64, ent_w32, cnt;
+        DevBuf grid32, grid64;
+    } sites;
     double* host_pinned = nullptr;   // pinned host scratch (4096 doubles)
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -199,6 +215,20 @@ void sample_field(kry_ctx* ctx, const kry_cov& cov, int M1, int M2, const double
 void boot_rhs(kry_ctx* ctx, const double* G, int64_t N, const double* eps, double tau, double* R, int nrep);
 void boot_mse(kry_ctx* ctx, const double* G, const double* H, int64_t N, int nrep, const int64_t* cells,
               int64_t ncell, double* var, int* bad);
+
+// Irregular sites (sites.cu, Sec. 2 Wendland mapping A): build ctx->sites for
+// nsite device coordinate pairs (false if a site lies outside the domain);
+// grid[v] = scale[v] A^T vin[v] on the whole grid; vout[v] = A grid[v] + tau2
+// scale[v] vin[v] with per-block partials of (scale[v] vin[v])^T vout[v]
+// (site_num_partials() blocks when dots is NULL, nds otherwise).
+bool build_sites(kry_ctx* ctx, int n1, int n2, double dx1, double dx2, const double* sites, int64_t nsite);
+int site_num_partials(kry_ctx* ctx);
+template <typename T>
+void site_scatter(kry_ctx* ctx, const T* vin, int64_t ld_in, const double* scale, int nvec, T* grid, const int* skip);
+template <typename T>
+void site_gather(kry_ctx* ctx, const T* grid, const T* vin, int64_t ld_in, const double* scale, T* vout,
+                 int64_t ld_out, int nvec, double tau2, const double* tau2v, int vpt, double* dots, int nds,
+                 const int* skip);
 
 // Overwrite FP64 embedding e's eigenvalues with those of d Sigma / d(range).
 void drange_embedding(kry_ctx* ctx, const kry_cov& cov, kry_embed* e);

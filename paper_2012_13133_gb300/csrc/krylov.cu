@@ -925,147 +925,139 @@ static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int
 // matvec of the iteration runs in FP32.  Convergence is declared only on a
 // true FP64 residual.
 
+// Each iteration is the plain CG recurrence on five launches, none of which
+// starts with a reduction:
+//   q = K p                      (FFT matvec; pass C forms the partials of p^T q)
+//   alpha = gamma / p^T q        (k_rcg_alpha: one block per column, fixed-order sum)
+//   x += alpha p, r -= alpha q   (k_rcg_update: streaming, forms the partials of r^T r)
+//   beta = gamma' / gamma        (k_rcg_beta: one block per column; counts the iteration
+//                                 and asks for a residual replacement)
+//   p = r + beta p               (k_rcg_pupdate: streaming)
+// K p is computed afresh by every matvec, so no auxiliary recurrence can
+// drift in FP32 (single-reduction rearrangements carry K p by a recurrence and
+// broke down on the ill-conditioned grids here).
 struct RcgState {
-    double* rr[2];    // [nrhs] r^T r, double-buffered: iteration it reads rr[it & 1], writes rr[(it + 1) & 1]
-    double* rr_ref;   // [nrhs] r^T r at the last replacement
+    double* gam;      // [nrhs] gamma = r^T r of the current residual
+    double* alpha;    // [nrhs]
+    double* beta;     // [nrhs]
+    double* gam_ref;  // [nrhs] gamma at the last replacement
     double* thr2;     // [nrhs] (rtol ||b||)^2
+    int* want;        // [nrhs] 1: the last iteration asks for a replacement
     int* done;        // [nrhs]
     int* iters;       // [nrhs]
-    int* nwant;       // [1] columns asking for a replacement (or done)
+    int* ndone;       // [1]
 };
 
 // Blocks per right-hand side of the CG vector kernels: 304 (two per SM) for a
 // few right-hand sides, fewer for many, so that a batch keeps about 1216
-// blocks (a block then covers more elements instead of more blocks paying the
-// per-block reductions).
+// blocks.
 static int cg_blocks(int nrhs) { return std::max(8, std::min(304, 1216 / std::max(1, nrhs))); }
 
-// r^T r buffer of parity par (a select, not an indexed load from the parameter struct)
-__device__ __forceinline__ double* rr_buf(const RcgState& S, int par) { return par ? S.rr[1] : S.rr[0]; }
-
-// X = 0 (a double-float pair Xh + Xl), R = (float) B, P = R; partials of
-// ||B||^2 (exact) per column.
+// X = 0 (a double-float pair Xh + Xl), R = P = (float) B; partials of ||B||^2
+// (FP64) per column, one per block.
 __global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, float* __restrict__ Xh, float* __restrict__ Xl,
-                            float* __restrict__ R, float* __restrict__ P, int64_t p, double* __restrict__ part) {
+                            float* __restrict__ R, float* __restrict__ P, int64_t p, double* __restrict__ part_rr) {
     const int k = blockIdx.y;
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
         const double b = B[(int64_t)k * ldb + i];
-        Xh[(int64_t)k * p + i] = 0.f;
-        Xl[(int64_t)k * p + i] = 0.f;
-        const float r = (float)b;
-        R[(int64_t)k * p + i] = r;
-        P[(int64_t)k * p + i] = r;
+        const int64_t o = (int64_t)k * p + i;
+        Xh[o] = 0.f;
+        Xl[o] = 0.f;
+        R[o] = (float)b;
+        P[o] = (float)b;
         acc[0] += b * b;
     }
-    block_sum_store<1>(acc, part + (int64_t)k * gridDim.x + blockIdx.x, 0);
+    block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
-__global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part, int nblk, int nrhs,
+__global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part_rr, int nblk, int nrhs,
                                    const double* __restrict__ tol) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nrhs) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)k * nblk + b];
-        S.rr[0][k] = s;
-        S.rr_ref[k] = s;
+        for (int b = 0; b < nblk; ++b) s += part_rr[(int64_t)k * nblk + b];
+        S.gam[k] = s;
+        S.gam_ref[k] = s;
+        S.alpha[k] = 0.0;
+        S.beta[k] = 0.0;
         S.thr2[k] = tol[k] * tol[k] * s;
+        S.want[k] = 0;
         S.done[k] = (s == 0.0) ? 1 : 0;
         S.iters[k] = 0;
     }
-    if (k == 0) *S.nwant = 0;
 }
 
-// alpha = r^T r / p^T K p from the matvec's partials; every block of the
-// column sums them in the same fixed order, so all blocks agree.
-__device__ __forceinline__ double rcg_alpha(const RcgState& S, const double* __restrict__ part_pq, int nblkC, int k,
-                                            int par) {
-    __shared__ double a_sh;
-    const double pq = block_sum(part_pq + (int64_t)k * nblkC, nblkC);
-    if (threadIdx.x == 0) a_sh = (S.done[k] || !(pq > 0.0)) ? 0.0 : rr_buf(S, par)[k] / pq;
-    __syncthreads();
-    return a_sh;
+// alpha = gamma / p^T q from the matvec's partials (fixed order; 0 if p^T q is
+// not positive).
+__global__ void k_rcg_alpha(RcgState S, const double* __restrict__ part_pq, int nblkC) {
+    const int k = blockIdx.x;
+    if (S.done[k]) return;
+    const double d = block_sum(part_pq + (int64_t)k * nblkC, nblkC);
+    if (threadIdx.x == 0) S.alpha[k] = (d > 0.0) ? S.gam[k] / d : 0.0;
 }
 
 // X += alpha P in double-float (Xh + Xl, FP32 instructions only), R -= alpha Q
-// (FP32); partial ||R||^2 accumulated in double-float.  VW elements per
-// 16-byte access (the internal vectors are 16-byte aligned when p % 4 == 0).
+// (FP32); partials of ||R||^2 in double-float.  VW elements per 16-byte access
+// (the internal vectors are 16-byte aligned when p % 4 == 0).
 template <int VW>
 __global__ void k_rcg_update(float* __restrict__ Xh, float* __restrict__ Xl, float* __restrict__ R,
                              const float* __restrict__ P, const float* __restrict__ Q, int64_t p, RcgState S,
-                             const double* __restrict__ part_pq, int nblkC, double* __restrict__ part_rr, int par) {
+                             double* __restrict__ part_rr) {
     const int k = blockIdx.y;
-    if (k == 0 && blockIdx.x == 0 && threadIdx.x == 0) *S.nwant = 0;
-    // finished columns keep x and r (their r^T r partials are never read)
-    if (S.done[k]) return;
-    const double a = rcg_alpha(S, part_pq, nblkC, k, par);
+    if (S.done[k]) return;   // finished columns keep x and r
+    const double a = S.alpha[k];
     const float af = (float)a;
     float ahi, alo;
     df_split(a, ahi, alo);
-    const bool act = !S.done[k];
     const int64_t off = (int64_t)k * p;
     const int64_t nv = p / VW;
     DFAcc nrm;
     for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = off + xv * VW;
-        float r[VW];
+        float r[VW], pv[VW], qv[VW], xh[VW], xl[VW];
         load_vec<float, VW>(R + o, r);
-        if (act) {
-            float pv[VW], qv[VW], xh[VW], xl[VW];
-            load_vec<float, VW>(P + o, pv);
-            load_vec<float, VW>(Q + o, qv);
-            load_vec<float, VW>(Xh + o, xh);
-            load_vec<float, VW>(Xl + o, xl);
+        load_vec<float, VW>(P + o, pv);
+        load_vec<float, VW>(Q + o, qv);
+        load_vec<float, VW>(Xh + o, xh);
+        load_vec<float, VW>(Xl + o, xl);
 #pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                df_axpy(xh[e], xl[e], ahi, alo, pv[e]);
-                r[e] -= af * qv[e];
-            }
-            store_vec<float, VW>(Xh + o, xh);
-            store_vec<float, VW>(Xl + o, xl);
-            store_vec<float, VW>(R + o, r);
+        for (int e = 0; e < VW; ++e) {
+            df_axpy(xh[e], xl[e], ahi, alo, pv[e]);
+            r[e] -= af * qv[e];
+            nrm.add_prod(r[e], r[e]);
         }
-#pragma unroll
-        for (int e = 0; e < VW; ++e) nrm.add_prod(r[e], r[e]);
+        store_vec<float, VW>(Xh + o, xh);
+        store_vec<float, VW>(Xl + o, xl);
+        store_vec<float, VW>(R + o, r);
     }
     double acc[1] = {nrm.value()};
     block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
-// X = Xh + Xl in FP64 (the caller's layout, leading dimension ldx).
-__global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t p,
-                            double* __restrict__ X, int64_t ldx) {
-    const int k = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
-        X[(int64_t)k * ldx + i] = (double)Xh[(int64_t)k * p + i] + (double)Xl[(int64_t)k * p + i];
+// beta = gamma' / gamma from the update's partials (fixed order); counts the
+// iteration and asks for a replacement when gamma' has fallen 100x since the
+// last one, reached the target, is not finite, or the budget is spent.
+__global__ void k_rcg_beta(RcgState S, const double* __restrict__ part_rr, int nbc, int maxit) {
+    const int k = blockIdx.x;
+    if (S.done[k]) return;
+    const double g = block_sum(part_rr + (int64_t)k * nbc, nbc);
+    if (threadIdx.x == 0) {
+        const double g0 = S.gam[k];
+        S.beta[k] = (g0 > 0.0) ? g / g0 : 0.0;
+        S.gam[k] = g;
+        const int it = S.iters[k] + 1;
+        S.iters[k] = it;
+        S.want[k] = (g <= S.thr2[k] || g <= 1e-2 * S.gam_ref[k] || !(g == g) || it >= maxit) ? 1 : 0;
+    }
 }
 
-// beta = r_new^T r_new / r^T r (every block sums the update's partials in the
-// same order), P = R + beta P.  Block 0 of each column records r_new^T r_new
-// for the next iteration, counts the iteration and asks for a residual
-// replacement when r^T r fell 100x (||r|| 10x) since the last one or reached
-// the target.
+// P = R + beta P (FP32).
 template <int VW>
-__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S,
-                              const double* __restrict__ part_rr, int nblk, int par, int maxit) {
+__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S) {
     const int k = blockIdx.y;
-    if (S.done[k]) return;   // finished columns: no bookkeeping, P unchanged
-    __shared__ double b_sh;
-    const double s = block_sum(part_rr + (int64_t)k * nblk, nblk);
-    if (threadIdx.x == 0) {
-        const bool act = !S.done[k];
-        const double rr = rr_buf(S, par)[k];
-        b_sh = (act && rr > 0.0) ? s / rr : 0.0;
-        if (act && blockIdx.x == 0) {
-            S.iters[k] += 1;
-            rr_buf(S, par ^ 1)[k] = s;
-            const bool want = s <= S.thr2[k] || s <= 1e-2 * S.rr_ref[k] || !(s == s) || S.iters[k] >= maxit;
-            if (want) atomicAdd(S.nwant, 1);
-        }
-    }
-    __syncthreads();
     if (S.done[k]) return;
-    const float b = (float)b_sh;
+    const float b = (float)S.beta[k];
     float* Pk = P + (int64_t)k * p;
     const float* Rk = R + (int64_t)k * p;
     const int64_t nv = p / VW;
@@ -1079,29 +1071,37 @@ __global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R
     }
 }
 
-// Residual replacement: R = (float) R64, rr = rr_ref = ||R64||^2 (into the
-// buffer the next iteration reads); done when ||R64|| <= rtol ||B|| or the
-// iteration budget is spent.
+// X = Xh + Xl in FP64 (the caller's layout, leading dimension ldx).
+__global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t p,
+                            double* __restrict__ X, int64_t ldx) {
+    const int k = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)k * ldx + i] = (double)Xh[(int64_t)k * p + i] + (double)Xl[(int64_t)k * p + i];
+}
+
+// Residual replacement of the columns still running: R = (float) R64,
+// gamma = gamma_ref = ||R64||^2 (P is kept); done when ||R64|| <= rtol ||B|| or
+// the iteration budget is spent (a non-finite residual also ends the column;
+// the caller reports it).
 __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
-                              const double* __restrict__ norms, RcgState S, int maxit, int par) {
+                              const double* __restrict__ norms, RcgState S, int maxit) {
     const int k = blockIdx.y;
     if (S.done[k]) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
         R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rn = norms[2 * k];
-        rr_buf(S, par)[k] = rn * rn;
-        S.rr_ref[k] = rn * rn;
+        S.gam[k] = rn * rn;
+        S.gam_ref[k] = rn * rn;
+        S.want[k] = 0;
         if (rn * rn <= S.thr2[k] || S.iters[k] >= maxit || !(rn == rn)) S.done[k] = 1;
     }
 }
 
-__global__ void k_cg_zero_nwant(int* n) { *n = 0; }
-
 __global__ void k_count_done(RcgState S, int nrhs) {
     int d = 0;
     for (int k = 0; k < nrhs; ++k) d += S.done[k];
-    *S.nwant = d;
+    *S.ndone = d;
 }
 
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
@@ -1120,21 +1120,22 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     float* P = ctx->work[8].as<float>();
     float* Q = ctx->work[9].as<float>();
     const int nblkC = matvec_num_partials(ctx, e, false, nrhs);
-    const int npq = std::max(nblkC, RED_BLOCKS);
     const int nbc = cg_blocks(nrhs);
-    ctx->work[10].ensure((size_t)nrhs * (npq + nbc) * sizeof(double));
-    double* part = ctx->work[10].as<double>();      // matvec partials (p^T K p), and the start's ||B||^2
-    double* part_rr = part + (size_t)nrhs * npq;    // update partials (r^T r)
-    ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 2 * sizeof(int)) + 64);
+    ctx->work[10].ensure((size_t)nrhs * (nblkC + nbc) * sizeof(double));
+    double* part_pq = ctx->work[10].as<double>();        // matvec partials (p^T K p)
+    double* part_rr = part_pq + (size_t)nrhs * nblkC;     // start / update partials (r^T r)
+    ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 3 * sizeof(int)) + 64);
     char* sb = ctx->work[11].as<char>();
     RcgState S;
-    S.rr[0] = reinterpret_cast<double*>(sb);
-    S.rr[1] = S.rr[0] + nrhs;
-    S.rr_ref = S.rr[1] + nrhs;
-    S.thr2 = S.rr_ref + nrhs;
-    S.done = reinterpret_cast<int*>(S.thr2 + nrhs + nrhs);
+    S.gam = reinterpret_cast<double*>(sb);
+    S.alpha = S.gam + nrhs;
+    S.beta = S.alpha + nrhs;
+    S.gam_ref = S.beta + nrhs;
+    S.thr2 = S.gam_ref + nrhs;
+    S.want = reinterpret_cast<int*>(S.thr2 + nrhs);
+    S.done = S.want + nrhs;
     S.iters = S.done + nrhs;
-    S.nwant = S.iters + nrhs;
+    S.ndone = S.iters + nrhs;
     ctx->tolbuf.ensure(nrhs * sizeof(double));
     std::vector<double> tol_h(nrhs, rtol);
     KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1153,67 +1154,66 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
         k_df_to_f64<<<gv, 256, 0, st>>>(Xh, Xl, p, X, ldx);
         KRY_CHECK_LAUNCH();
     };
-    k_rcg_start<<<gv, 256, 0, st>>>(B, ldb, Xh, Xl, R, P, p, part);
+    k_rcg_start<<<gc, 256, 0, st>>>(B, ldb, Xh, Xl, R, P, p, part_rr);
     KRY_CHECK_LAUNCH();
-    k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part, RED_BLOCKS, nrhs, ctx->tolbuf.as<double>());
+    k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part_rr, nbc, nrhs, ctx->tolbuf.as<double>());
     KRY_CHECK_LAUNCH();
     int* hflag = reinterpret_cast<int*>(ctx->host_pinned);
     const int poll = 8;
     nrm.assign(2 * nrhs, 0.0);
     *fresh = false;
-    // one CG iteration of parity par, on ctx->stream (the capture stream while capturing)
-    auto iterate = [&](int par) {
+    // one CG iteration on ctx->stream (the capture stream while capturing)
+    auto iterate = [&]() {
         cudaStream_t s2 = ctx->stream;
         // columns that have converged are not transformed (pairs of finished columns skip every pass)
-        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part, nblkC, vpt, S.done);
-        if (vec)
-            k_rcg_update<4><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part, nblkC, part_rr, par);
-        else
-            k_rcg_update<1><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part, nblkC, part_rr, par);
+        matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part_pq, nblkC, vpt, S.done);
+        k_rcg_alpha<<<nrhs, FIN_THREADS, 0, s2>>>(S, part_pq, nblkC);
         KRY_CHECK_LAUNCH();
         if (vec)
-            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, nbc, par, maxit);
+            k_rcg_update<4><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part_rr);
         else
-            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S, part_rr, nbc, par, maxit);
+            k_rcg_update<1><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part_rr);
+        KRY_CHECK_LAUNCH();
+        k_rcg_beta<<<nrhs, FIN_THREADS, 0, s2>>>(S, part_rr, nbc, maxit);
+        KRY_CHECK_LAUNCH();
+        if (vec)
+            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S);
+        else
+            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S);
         KRY_CHECK_LAUNCH();
     };
-    // Iterations run in blocks of `poll` (an even count, so every block has the
-    // same parity pattern).  The first block runs directly (it sizes every
-    // buffer); later blocks replay one captured graph.
+    // Iterations run in blocks of `poll`.  The first block runs directly (it
+    // sizes every buffer); later blocks replay one captured graph.
     Replay block(ctx);
     for (int it0 = 0; it0 < maxit + poll; it0 += poll) {
         if (it0 == 0 || !ctx->use_graphs) {
-            for (int i = 0; i < poll; ++i) iterate(i & 1);
+            for (int i = 0; i < poll; ++i) iterate();
         } else {
             if (!block.exec)
                 block.capture([&]() {
-                    for (int i = 0; i < poll; ++i) iterate(i & 1);
+                    for (int i = 0; i < poll; ++i) iterate();
                 });
             block.launch();
         }
-        const int it = it0 + poll - 1;   // last iteration of the block
-        const int par = it & 1;
-        {
-            KRY_CUDA(cudaMemcpyAsync(hflag, S.nwant, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KRY_CUDA(cudaMemcpyAsync(hflag, S.want, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+        KRY_CUDA(cudaStreamSynchronize(st));
+        if (block.exec) block.harvest();
+        bool any = false;
+        for (int k = 0; k < nrhs; ++k) any = any || hflag[k] != 0;
+        if (any) {
+            // residual replacement for every column still running
+            to_f64();
+            true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
+            double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
+            k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit);
+            KRY_CHECK_LAUNCH();
+            k_count_done<<<1, 1, 0, st>>>(S, nrhs);
+            KRY_CHECK_LAUNCH();
+            KRY_CUDA(cudaMemcpyAsync(hflag, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
             KRY_CUDA(cudaStreamSynchronize(st));
-            if (block.exec) block.harvest();
-            if (*hflag > 0) {
-                // residual replacement for every column still running
-                to_f64();
-                true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
-                double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
-                k_rcg_replace<<<gv, 256, 0, st>>>(R64, R, p, dn, S, maxit, par ^ 1);
-                KRY_CHECK_LAUNCH();
-                k_count_done<<<1, 1, 0, st>>>(S, nrhs);
-                KRY_CHECK_LAUNCH();
-                KRY_CUDA(cudaMemcpyAsync(hflag, S.nwant, sizeof(int), cudaMemcpyDeviceToHost, st));
-                KRY_CUDA(cudaStreamSynchronize(st));
-                if (*hflag >= nrhs) {
-                    *fresh = true;
-                    break;
-                }
-                k_cg_zero_nwant<<<1, 1, 0, st>>>(S.nwant);
-                KRY_CHECK_LAUNCH();
+            if (*hflag >= nrhs) {
+                *fresh = true;
+                break;
             }
         }
     }
@@ -1256,7 +1256,12 @@ SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, 
     info.relres = 0.0;
     for (int k = 0; k < nrhs; ++k) {
         const double bn = nrm[2 * k + 1];
-        info.relres = std::max(info.relres, bn > 0 ? nrm[2 * k] / bn : 0.0);
+        const double rk = bn > 0 ? nrm[2 * k] / bn : 0.0;
+        if (!(rk == rk)) {   // a non-finite residual is reported, not dropped by max
+            info.relres = rk;
+            break;
+        }
+        info.relres = std::max(info.relres, rk);
     }
     info.converged = info.relres <= rtol * (1.0 + 1e-9);
     return info;

@@ -658,7 +658,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
             a.n1 = n1; a.n2 = n2; a.M1 = M1; a.M2 = M2; a.G = G; a.C = C; a.logC = logC;
             KRY_REQUIRE(e->lam32P != nullptr, KRY_EINVAL, "embedding lacks the permuted eigenvalues");
             a.slab = slab; a.lamP = e->lam32P; a.lam_stride = e->lam_stride; a.vpt = vpt;
-            a.tau2 = tau2; a.tau2v = e->tau2_dev; a.dots = dots; a.nds = nds;
+            a.tau2 = tau2; a.tau2v = ctx->no_nugget ? nullptr : e->tau2_dev; a.dots = dots; a.nds = nds;
             a.twt = ctx->twt32.as<float4>(); a.skip = skip;
             for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
                 a.pair0 = pair0;
@@ -693,7 +693,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
                 KRY_ALLOW_MAX_SMEM(k);
                 KRY_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, KRY_SMEM_CARVEOUT));
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt, skip);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, ctx->no_nugget ? nullptr : e->tau2_dev, vpt, skip);
                 KRY_CHECK_LAUNCH();
             });
         } else {
@@ -701,7 +701,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
                 auto k = k16_pass_c<T, N_, 1>;
                 KRY_ALLOW_MAX_SMEM(k);
                 k<<<gA, thrA, smA, st>>>(slab, vin, ld_in, scale, vout, ld_out, nvec, pair0, rowptr, colidx, n1, n2,
-                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt, skip);
+                                        M2, C, logC, psA, tau2, dots, nds, tw32, tw64, ctx->no_nugget ? nullptr : e->tau2_dev, vpt, skip);
                 KRY_CHECK_LAUNCH();
             });
         }
@@ -711,9 +711,60 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                        int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt = 0,
-                       const int* skip = nullptr) {
+                       const int* skip = nullptr);
+
+// Irregular sites (sites.cu): A^T by scatter onto the whole grid, sigma^2 Sigma
+// on the whole grid by the FFT passes with whole-grid index lists and no
+// nugget, then (mode 0) the gather A, nugget and dot partials; in mode 1 the
+// whole-grid result is the output.
+template <typename T>
+static void run_matvec_sites(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale,
+                             T* vout, int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt,
+                             const int* skip) {
+    const int64_t N = (int64_t)e->n1 * e->n2;
+    KRY_REQUIRE(ctx->rowptr_full.p && ctx->full_n1 == e->n1 && ctx->full_n2 == e->n2, KRY_EINVAL,
+                "the site map's whole-grid index lists are missing");
+    DevBuf& gb = sizeof(T) == 8 ? ctx->sites.grid64 : ctx->sites.grid32;
+    gb.ensure((size_t)(mode == 0 ? 2 : 1) * nvec * N * sizeof(T));
+    T* gin = gb.as<T>();
+    T* gout = (mode == 0) ? gin + (size_t)nvec * N : vout;
+    site_scatter<T>(ctx, vin, ld_in, scale, nvec, gin, skip);
+    struct Scope {   // whole-grid lists in, the site map and the nugget out, for the FFT passes
+        kry_ctx* c;
+        int64_t p;
+        explicit Scope(kry_ctx* x) : c(x), p(x->p) {
+            std::swap(c->rowptr, c->rowptr_full);
+            std::swap(c->colidx, c->colidx_full);
+            c->p = (int64_t)c->n1 * c->n2;
+            c->sites.active = false;
+            c->no_nugget = true;
+        }
+        ~Scope() {
+            std::swap(c->rowptr, c->rowptr_full);
+            std::swap(c->colidx, c->colidx_full);
+            c->p = p;
+            c->sites.active = true;
+            c->no_nugget = false;
+        }
+    } scope(ctx);
+    run_matvec<T>(ctx, e, gin, N, nullptr, gout, mode == 0 ? N : ld_out, nvec, 0.0, nullptr, 0, 0, vpt, skip);
+    if (mode == 0) {
+        ctx->p = scope.p;   // the gather runs over the sites
+        ctx->sites.active = true;
+        site_gather<T>(ctx, gout, vin, ld_in, scale, vout, ld_out, nvec, tau2, e->tau2_dev, vpt, dots, nds, skip);
+    }
+}
+
+template <typename T>
+static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
+                       int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt,
+                       const int* skip) {
     KRY_REQUIRE(vpt == 0 || (vpt % 2 == 0 && nvec % vpt == 0 && nvec / vpt <= e->ntheta), KRY_EINVAL,
                 "vectors per theta must be even and divide the batch");
+    if (ctx->sites.active) {
+        run_matvec_sites<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, vpt, skip);
+        return;
+    }
     using Cx = typename cx_of<T>::type;
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
@@ -779,12 +830,12 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
             KRY_DISPATCH_EG(s.ept_row, G,
                             (MvLaunch<T>::template c<E_, G_, 0>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
                                                                 ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
-                                                                tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt)));
+                                                                tau2, dots, nds, tw32, tw64, ctx->no_nugget ? nullptr : e->tau2_dev, vpt)));
         } else {
             KRY_DISPATCH_EG(s.ept_row, G,
                             (MvLaunch<T>::template c<E_, G_, 1>(gA, thrA, smA, st, slab, vin, ld_in, scale, vout,
                                                                 ld_out, nvec, pair0, rowptr, colidx, n1, n2, M2, C,
-                                                                tau2, dots, nds, tw32, tw64, e->tau2_dev, vpt)));
+                                                                tau2, dots, nds, tw32, tw64, ctx->no_nugget ? nullptr : e->tau2_dev, vpt)));
         }
     }
     if (ctx->prof_on) {
@@ -799,6 +850,7 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
 // Number of per-block dot partials pass C writes per vector for a batch of
 // nvec vectors (the Krylov finalisers sum exactly this many).
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec) {
+    if (ctx->sites.active) return site_num_partials(ctx);
     if (use16(e->M1, e->M2)) {
         int G, C;
         sched16(ctx, e->M1, e->M2, dbl, nvec, &G, &C);
@@ -981,6 +1033,8 @@ extern "C" kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const
         KRY_REQUIRE(e != nullptr && e->ctx == ctx, KRY_EINVAL, "embedding is NULL or belongs to another context");
         KRY_REQUIRE(ctx->p > 0 && e->n1 == ctx->n1 && e->n2 == ctx->n2, KRY_EINVAL,
                     "no mask set, or the embedding grid differs from the mask grid");
+        KRY_REQUIRE(!ctx->sites.active, KRY_EUNSUPPORTED,
+                    "the allocation-free matvec needs an observation mask (kry_set_mask), not sites");
         KRY_REQUIRE(nvec >= 0 && ld >= ctx->p, KRY_EINVAL, "need nvec >= 0 and ld >= p");
         if (nvec == 0) return KRY_OK;
         KRY_REQUIRE(v_dev && out_dev, KRY_EINVAL, "v_dev and out_dev must not be NULL");

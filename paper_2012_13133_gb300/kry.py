@@ -15,8 +15,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-# KRY_LIBRARY names another build of the same library (e.g. a variant built with other flags)
-LIB_PATH = os.environ.get("KRY_LIBRARY") or os.path.join(_PKG, "libkry.so")
+LIB_PATH = os.path.join(_PKG, "libkry.so")
 
 KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ENOTPSD, KRY_ENOCONV, KRY_ENAN, KRY_ETIMEOUT, KRY_ECUDA, KRY_EUNSUPPORTED = range(9)
 STATUS_NAMES = ["KRY_OK", "KRY_EINVAL", "KRY_ENOMEM", "KRY_ENOTPSD", "KRY_ENOCONV", "KRY_ENAN", "KRY_ETIMEOUT",
@@ -62,6 +61,7 @@ SIGNATURES = {
     "kry_destroy": (None, [_P]),
     "kry_last_error": (C.c_char_p, [_P]),
     "kry_set_mask": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.POINTER(C.c_int64)]),
+    "kry_set_sites": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.c_int64]),
     "kry_embed_eigs": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.POINTER(_P), _DP]),
     "kry_embed_free": (None, [_P]),
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
@@ -248,6 +248,17 @@ class Context:
         m = _dev((mask.contiguous(), ("uint8", "bool"), n1 * n2, "mask"))
         self._check(_lib.kry_set_mask(self.h, C.byref(g), m, C.byref(p)))
         self.p, self.n1, self.n2 = int(p.value), n1, n2
+        return self.p
+
+    def set_sites(self, sites, n1, n2, dx1=None, dx2=None) -> int:
+        """Irregular observation sites: sites is a torch float64 CUDA tensor (p, 2) of coordinates in the
+        domain of the n1 x n2 latent grid (the unit square by default); the Wendland mapping matrix A
+        is built on the device.  Returns p."""
+        p = int(sites.shape[0])
+        g = kry_grid(n1, n2, 1.0 / n1 if dx1 is None else dx1, 1.0 / n2 if dx2 is None else dx2)
+        s = _dev((sites.contiguous(), F64, 2 * p, "sites"))
+        self._check(_lib.kry_set_sites(self.h, C.byref(g), s, p))
+        self.p, self.n1, self.n2 = p, n1, n2
         return self.p
 
     # -- embedding
