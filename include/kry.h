@@ -86,7 +86,16 @@ typedef struct {
  * reorthogonalised (as the paper runs it for its results, Sec. 3.2); 1 =
  * partial reorthogonalisation (Sec. 3.2 leaves a scheme to the user; see
  * kry_logdet), which keeps every basis vector on the device
- * (nprobe * nsteps * p values of the embedding's precision). */
+ * (nprobe * nsteps * p values of the embedding's precision).  precond: 0 =
+ * plain CG; 1 = CG preconditioned by M^-1 = A (S + tau2 I)^-1 A^T, S the
+ * circulant embedding of sigma2 Sigma on the matvec's torus (its inverse is
+ * diagonal in the same FFT basis, so M^-1 costs one more FFT matvec per
+ * iteration).  It pays where most of the grid is observed and the gaps are
+ * clustered (cloud-like masks), not under scattered missing cells; it applies
+ * to FP32 solves of one covariance setting with tau2 > 0 on an observation
+ * mask, and is ignored otherwise (with irregular sites, close sites make
+ * A (S + tau2 I)^-1 A^T nearly singular).  The result does not depend on it
+ * beyond the CG tolerance. */
 typedef struct {
     kry_prec prec;
     int32_t nprobe, nsteps;
@@ -94,6 +103,7 @@ typedef struct {
     double rtol;
     int32_t maxit;
     int32_t reorth;
+    int32_t precond;
 } kry_opts;
 
 typedef struct kry_ctx kry_ctx;       /* opaque, library-owned */
@@ -206,6 +216,17 @@ kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t 
 kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev,
                      int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
                      int32_t* iters, double* relres);
+
+/* kry_solve preconditioned by M^-1 = A (S + tau2 I)^-1 A^T (S the circulant
+ * embedding of sigma2 Sigma on the matvec's torus, whose inverse the same FFT
+ * passes apply; see kry_opts.precond).  Same arguments, convergence test and
+ * errors as kry_solve; the result agrees with it to the CG tolerance.  Each
+ * iteration costs two FFT matvecs, so it pays where the iteration count falls
+ * by more than half: masks with clustered gaps.  FP64 embeddings, tau2 = 0 and
+ * irregular sites (kry_set_sites) run plain CG.  Library scratch: one more FP32 vector per right-hand side and
+ * the preconditioner's eigenvalues (16 M1 M2 bytes) for the call. */
+kry_status kry_solve_pre(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev, int32_t nrhs,
+                         int64_t ld, double rtol, int32_t maxit, int32_t* iters, double* relres);
 
 /* Marginal log-likelihood of the observed cells with beta profiled by GLS,
  * for ntheta covariance settings:

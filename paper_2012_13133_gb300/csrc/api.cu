@@ -23,7 +23,7 @@ void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, co
                int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
 void logdet(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth, double* per_probe);
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit, int vpt = 0);
+                double rtol, int maxit, int vpt = 0, const kry_embed* pre = nullptr);
 GlsResult gls(kry_ctx* ctx, const double* V, const double* Z, int ncov, double logdet);
 void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_dev, double* w);
 void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, int64_t ncell, const double* Xc,
@@ -250,6 +250,44 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
         dev_alloc((void**)&e->lam64T, MM * sizeof(double), ctx->stream);
         if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, MM * sizeof(float), ctx->stream);
         if (prec == KRY_F32 && spec_column_pass(ctx, e)) dev_alloc((void**)&e->lam32P, MM * sizeof(float), ctx->stream);
+        kry::store_embedding(ctx, e, 0);
+    } catch (...) {
+        if (e->lam64T) cudaFreeAsync(e->lam64T, ctx->stream);
+        if (e->lam32T) cudaFreeAsync(e->lam32T, ctx->stream);
+        if (e->lam32P) cudaFreeAsync(e->lam32P, ctx->stream);
+        delete e;
+        throw;
+    }
+    return e;
+}
+
+// CG preconditioner for one covariance setting (kry_opts.precond): an FP32
+// embedding whose matvec applies M^-1 = A (S + tau2 I)^-1 A^T, S the circulant
+// embedding of sigma2 Sigma on the torus: eigenvalues 1 / (max(Lambda, 0) +
+// tau2), no nugget.  NULL when it does not apply: FP64 solves, several
+// settings, tau2 = 0, and irregular sites (with Wendland weights, close sites
+// give nearly equal rows of A, so A (S + tau2 I)^-1 A^T is nearly singular and
+// preconditioned CG stalls: measured, 12,000 sites on a 128^2 grid).
+static kry_embed* make_precond_embed(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o, int ntheta) {
+    if (!o->precond || o->prec != KRY_F32 || ntheta != 1 || !(cov->tau2 > 0.0) || ctx->sites.active) return nullptr;
+    kry_embed* e = new kry_embed();
+    e->ctx = ctx;
+    e->device = ctx->device;
+    e->n1 = ctx->n1;
+    e->n2 = ctx->n2;
+    e->M1 = pow2_at_least(2 * (int64_t)ctx->n1);
+    e->M2 = pow2_at_least(2 * (int64_t)ctx->n2);
+    e->cov = *cov;
+    e->cov.tau2 = 0.0;
+    e->prec = KRY_F32;
+    e->stream = ctx->stream;
+    try {
+        kry::compute_eigs(ctx, *cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, e->M1, e->M2, &e->lam_min, &e->lam_max);
+        kry::invert_eigs(ctx, e->M1, e->M2, cov->tau2);
+        const size_t MM = (size_t)e->M1 * e->M2;
+        dev_alloc((void**)&e->lam64T, MM * sizeof(double), ctx->stream);
+        dev_alloc((void**)&e->lam32T, MM * sizeof(float), ctx->stream);
+        if (spec_column_pass(ctx, e)) dev_alloc((void**)&e->lam32P, MM * sizeof(float), ctx->stream);
         kry::store_embedding(ctx, e, 0);
     } catch (...) {
         if (e->lam64T) cudaFreeAsync(e->lam64T, ctx->stream);
@@ -531,6 +569,34 @@ kry_status kry_solve(kry_ctx* ctx, const kry_embed* e, const double* B_dev, doub
     });
 }
 
+kry_status kry_solve_pre(kry_ctx* ctx, const kry_embed* e, const double* B_dev, double* X_dev, int32_t nrhs,
+                         int64_t ld, double rtol, int32_t maxit, int32_t* iters, double* relres) {
+    return guarded(ctx, [&]() -> kry_status {
+        check_embed(ctx, e);
+        KRY_REQUIRE(B_dev && X_dev, KRY_EINVAL, "B_dev and X_dev must not be NULL");
+        KRY_REQUIRE(nrhs >= 1 && nrhs <= 1024 && ld >= ctx->p, KRY_EINVAL, "need 1 <= nrhs <= 1024 and ld >= p");
+        KRY_REQUIRE(rtol > 0 && maxit >= 1, KRY_EINVAL, "need rtol > 0 and maxit >= 1");
+        KRY_REQUIRE(e->ntheta == 1, KRY_EINVAL, "one covariance setting per embedding");
+        kry_opts o{};
+        o.prec = e->prec;
+        o.precond = 1;
+        kry_embed* pre = make_precond_embed(ctx, &e->cov, &o, 1);
+        kry::SolveInfo si;
+        try {
+            si = kry::solve(ctx, e, B_dev, ld, X_dev, ld, nrhs, rtol, maxit, 0, pre);
+        } catch (...) {
+            free_embed(pre);
+            throw;
+        }
+        free_embed(pre);
+        if (iters) *iters = si.iters;
+        if (relres) *relres = si.relres;
+        if (!isfinite(si.relres)) return fail(ctx, KRY_ENAN, "CG residual is NaN/Inf");
+        if (!si.converged) return fail(ctx, KRY_ENOCONV, "CG did not reach rtol");
+        return KRY_OK;
+    });
+}
+
 static void check_opts(const kry_opts* o) {
     KRY_REQUIRE(o != nullptr, KRY_EINVAL, "opts is NULL");
     KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64, KRY_EINVAL, "opts->prec invalid");
@@ -539,7 +605,8 @@ static void check_opts(const kry_opts* o) {
     KRY_REQUIRE(o->reorth == 0 || o->reorth == 1, KRY_EINVAL, "opts->reorth must be 0 or 1");
 }
 
-// [y, X] packed into one (p x (ncov+1)) FP64 block and its solve Z = K^-1 [y, X].
+// [y, X] packed into one (p x (ncov+1)) FP64 block and its solve Z = K^-1 [y, X]
+// (preconditioned when o->precond asks for it and it applies).
 static kry::SolveInfo solve_yx(kry_ctx* ctx, const kry_embed* e, const double* y, const double* X, int ncov,
                                const kry_opts* o, double** V_out, double** Z_out) {
     const int64_t p = ctx->p;
@@ -551,7 +618,16 @@ static kry::SolveInfo solve_yx(kry_ctx* ctx, const kry_embed* e, const double* y
     KRY_CUDA(cudaMemcpyAsync(V + p, X, (size_t)ncov * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     *V_out = V;
     *Z_out = Z;
-    return kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit);
+    kry_embed* pre = make_precond_embed(ctx, &e->cov, o, 1);
+    kry::SolveInfo si;
+    try {
+        si = kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit, 0, pre);
+    } catch (...) {
+        free_embed(pre);
+        throw;
+    }
+    free_embed(pre);
+    return si;
 }
 
 kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X_dev, int32_t ncov,
@@ -597,8 +673,15 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
                     if (ncp > nc)
                         KRY_CUDA(cudaMemsetAsync(blk + (size_t)nc * p, 0, p * sizeof(double), ctx->stream));
                 }
-                kry::SolveInfo si = kry::solve(ctx, e, Vrep, p, Z, p, ng * ncp, opts->rtol, opts->maxit,
-                                               ng > 1 ? ncp : 0);
+                kry_embed* pre = make_precond_embed(ctx, &thetas[t0], opts, ng);
+                kry::SolveInfo si;
+                try {
+                    si = kry::solve(ctx, e, Vrep, p, Z, p, ng * ncp, opts->rtol, opts->maxit, ng > 1 ? ncp : 0, pre);
+                } catch (...) {
+                    free_embed(pre);
+                    throw;
+                }
+                free_embed(pre);
                 for (int t = 0; t < ng; ++t) {
                     std::vector<double> pv(vals.begin() + (size_t)t * opts->nprobe,
                                            vals.begin() + (size_t)(t + 1) * opts->nprobe);
@@ -844,7 +927,14 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
         kry_embed* e = make_embed(ctx, cov, opts->prec);
         kry::SolveInfo si;
         try {
-            si = kry::solve(ctx, e, R, p, Wd, p, nrep, opts->rtol, opts->maxit);
+            kry_embed* pre = make_precond_embed(ctx, cov, opts, 1);
+            try {
+                si = kry::solve(ctx, e, R, p, Wd, p, nrep, opts->rtol, opts->maxit, 0, pre);
+            } catch (...) {
+                free_embed(pre);
+                throw;
+            }
+            free_embed(pre);
             kry::sigma_to_grid64(ctx, e, Wd, H, nrep, p);
         } catch (...) {
             free_embed(e);

@@ -287,6 +287,22 @@ void compute_eigs(kry_ctx* ctx, const kry_cov& cov, int n1, int n2, double dx1, 
     *lam_max = ctx->host_pinned[1];
 }
 
+// Eigenvalues of (S + tau2 I)^-1 from those of the embedding S (in
+// ctx->eig_c): 1 / (max(Lambda, 0) + tau2).  Negative embedding eigenvalues
+// are reset to zero first (Sec. 3.6 caveat) so that the inverse stays
+// positive definite.
+__global__ void k_invert_eigs(double* __restrict__ c, int64_t MM, double tau2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MM; i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = 1.0 / (fmax(c[i], 0.0) + tau2);
+}
+
+void invert_eigs(kry_ctx* ctx, int M1, int M2, double tau2) {
+    const int64_t MM = (int64_t)M1 * M2;
+    k_invert_eigs<<<(unsigned)std::min<int64_t>((MM + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+        ctx->eig_c.as<double>(), MM, tau2);
+    KRY_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ BCCB log-determinant
 //
 // Sec. 3.3's approximation log det Sigma ~ sum log D1 and its range

@@ -43,6 +43,18 @@ extern std::atomic<unsigned long long> g_kry_launches;
         KRY_CUDA(cudaGetLastError());                            \
     } while (0)
 
+// Programmatic dependent launch (sm_90+).  A kernel launched by launch_pdl
+// may start while the kernel before it on the stream is still finishing; it
+// must call pdl_wait() before it touches anything that kernel writes (the wait
+// returns once that grid has completed and its memory is visible; without a
+// programmatic predecessor it returns at once).  pdl_launch_dependents() lets
+// the next kernel be scheduled as soon as every block of this grid has run it
+// (blocks that exit count as having run it), so dependents only fill slots
+// this grid no longer needs.  Neither call can wait on anything but the
+// predecessor grid's completion.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 #define KRY_REQUIRE(cond, status, text)        \
     do {                                       \
         if (!(cond)) throw KryError{status, text}; \
@@ -55,6 +67,23 @@ extern std::atomic<unsigned long long> g_kry_launches;
 // slots) with different launch sizes cannot undercut each other's launches.
 void kry_allow_max_smem(const void* func);
 #define KRY_ALLOW_MAX_SMEM(k) kry_allow_max_smem(reinterpret_cast<const void*>(k))
+
+// Launch kernel k with programmatic stream serialisation (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    KRY_CUDA(cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...));
+    KRY_CHECK_LAUNCH();
+}
 
 // ------------------------------------------------------------------ device buffers
 
@@ -229,6 +258,10 @@ template <typename T>
 void site_gather(kry_ctx* ctx, const T* grid, const T* vin, int64_t ld_in, const double* scale, T* vout,
                  int64_t ld_out, int nvec, double tau2, const double* tau2v, int vpt, double* dots, int nds,
                  const int* skip);
+
+// Replace the eigenvalues Lambda in ctx->eig_c (natural order, unscaled) by
+// 1 / (max(Lambda, 0) + tau2): the torus inverse (S + tau2 I)^-1.
+void invert_eigs(kry_ctx* ctx, int M1, int M2, double tau2);
 
 // Overwrite FP64 embedding e's eigenvalues with those of d Sigma / d(range).
 void drange_embedding(kry_ctx* ctx, const kry_cov& cov, kry_embed* e);

@@ -20,6 +20,7 @@
 #include "fft.cuh"
 #include "kry_internal.cuh"
 #include "matern.cuh"
+#include "mvspec.cuh"
 
 namespace kry {
 
@@ -27,6 +28,10 @@ template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
+
+bool matvec_cg_fusable(kry_ctx* ctx, const kry_embed* e, int nvec);
+void matvec_cg(kry_ctx* ctx, const kry_embed* e, float* P, int64_t ld, float* Q, int nvec, double* dots, int nds,
+               int vpt, const int* skip, const kspec::CgFuse& cg);
 
 static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
 
@@ -192,6 +197,21 @@ __device__ __forceinline__ double block_sum(const double* __restrict__ part, int
     __shared__ double ws[32];
     double v = 0.0;
     for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    return t;
+}
+
+// block_sum over partials written by other blocks of the running grid (read
+// through L2, after the caller's __threadfence).
+__device__ __forceinline__ double block_sum_cg(const double* __restrict__ part, int n) {
+    __shared__ double ws[32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) v += __ldcg(part + b);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -936,11 +956,22 @@ static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int
 // K p is computed afresh by every matvec, so no auxiliary recurrence can
 // drift in FP32 (single-reduction rearrangements carry K p by a recurrence and
 // broke down on the ill-conditioned grids here).
+//
+// With a preconditioner (an embedding `pre` whose matvec applies M^-1 = A (S +
+// tau2 I)^-1 A^T, S the circulant embedding of sigma2 Sigma on the matvec's
+// torus: the inverse of the torus covariance, restricted to the observed
+// cells), the same launches run preconditioned CG: after the update, z = M^-1 r
+// by the FFT passes (pass C forms the partials of r^T z), gamma = r^T z,
+// beta = gamma' / gamma, p = z + beta p; convergence is still judged on r^T r.
+// M^-1 is symmetric positive definite (a principal block of an SPD matrix).
+// It approximates K^-1 well where most of the grid is observed and the gaps
+// are clustered, and poorly under scattered missing cells.
 struct RcgState {
-    double* gam;      // [nrhs] gamma = r^T r of the current residual
+    double* gam;      // [nrhs] gamma = r^T z (r^T r without a preconditioner)
+    double* rr;       // [nrhs] r^T r of the current residual
     double* alpha;    // [nrhs]
     double* beta;     // [nrhs]
-    double* gam_ref;  // [nrhs] gamma at the last replacement
+    double* rr_ref;   // [nrhs] r^T r at the last replacement
     double* thr2;     // [nrhs] (rtol ||b||)^2
     int* want;        // [nrhs] 1: the last iteration asks for a replacement
     int* done;        // [nrhs]
@@ -971,19 +1002,28 @@ __global__ void k_rcg_start(const double* __restrict__ B, int64_t ldb, float* __
     block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
-__global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part_rr, int nblk, int nrhs,
+// rr = ||B||^2 from the start's partials; gamma = r^T z from the
+// preconditioner matvec's partials (part_rz, nrz per column) or = rr.
+__global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part_rr, int nblk,
+                                   const double* __restrict__ part_rz, int nrz, int nrhs,
                                    const double* __restrict__ tol) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nrhs) {
         double s = 0.0;
         for (int b = 0; b < nblk; ++b) s += part_rr[(int64_t)k * nblk + b];
-        S.gam[k] = s;
-        S.gam_ref[k] = s;
+        double g = s;
+        if (part_rz) {
+            g = 0.0;
+            for (int b = 0; b < nrz; ++b) g += part_rz[(int64_t)k * nrz + b];
+        }
+        S.gam[k] = g;
+        S.rr[k] = s;
+        S.rr_ref[k] = s;
         S.alpha[k] = 0.0;
         S.beta[k] = 0.0;
         S.thr2[k] = tol[k] * tol[k] * s;
         S.want[k] = 0;
-        S.done[k] = (s == 0.0) ? 1 : 0;
+        S.done[k] = (s == 0.0 || !(g > 0.0)) ? 1 : 0;
         S.iters[k] = 0;
     }
 }
@@ -991,6 +1031,8 @@ __global__ void k_rcg_init_scalars(RcgState S, const double* __restrict__ part_r
 // alpha = gamma / p^T q from the matvec's partials (fixed order; 0 if p^T q is
 // not positive).
 __global__ void k_rcg_alpha(RcgState S, const double* __restrict__ part_pq, int nblkC) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int k = blockIdx.x;
     if (S.done[k]) return;
     const double d = block_sum(part_pq + (int64_t)k * nblkC, nblkC);
@@ -1004,6 +1046,8 @@ template <int VW>
 __global__ void k_rcg_update(float* __restrict__ Xh, float* __restrict__ Xl, float* __restrict__ R,
                              const float* __restrict__ P, const float* __restrict__ Q, int64_t p, RcgState S,
                              double* __restrict__ part_rr) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int k = blockIdx.y;
     if (S.done[k]) return;   // finished columns keep x and r
     const double a = S.alpha[k];
@@ -1035,38 +1079,51 @@ __global__ void k_rcg_update(float* __restrict__ Xh, float* __restrict__ Xl, flo
     block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
 }
 
-// beta = gamma' / gamma from the update's partials (fixed order); counts the
-// iteration and asks for a replacement when gamma' has fallen 100x since the
-// last one, reached the target, is not finite, or the budget is spent.
-__global__ void k_rcg_beta(RcgState S, const double* __restrict__ part_rr, int nbc, int maxit) {
+// rr' = r^T r from the update's partials and gamma' = r^T z from part_rz (nrz
+// per column; NULL without a preconditioner: gamma' = rr'), both in a fixed
+// order; beta = gamma' / gamma.  Counts the iteration and asks for a
+// replacement when rr' has fallen 100x since the last one, reached the
+// target, is not finite, or the budget is spent.
+__global__ void k_rcg_beta(RcgState S, const double* __restrict__ part_rr, int nbc, const double* __restrict__ part_rz,
+                           int nrz, int maxit) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int k = blockIdx.x;
     if (S.done[k]) return;
-    const double g = block_sum(part_rr + (int64_t)k * nbc, nbc);
+    const double rr = block_sum(part_rr + (int64_t)k * nbc, nbc);
+    double g = rr;
+    if (part_rz) {
+        __syncthreads();   // block_sum's shared slots are reused
+        g = block_sum(part_rz + (int64_t)k * nrz, nrz);
+    }
     if (threadIdx.x == 0) {
         const double g0 = S.gam[k];
         S.beta[k] = (g0 > 0.0) ? g / g0 : 0.0;
         S.gam[k] = g;
+        S.rr[k] = rr;
         const int it = S.iters[k] + 1;
         S.iters[k] = it;
-        S.want[k] = (g <= S.thr2[k] || g <= 1e-2 * S.gam_ref[k] || !(g == g) || it >= maxit) ? 1 : 0;
+        S.want[k] = (rr <= S.thr2[k] || rr <= 1e-2 * S.rr_ref[k] || !(rr == rr) || !(g == g) || it >= maxit) ? 1 : 0;
     }
 }
 
-// P = R + beta P (FP32).
+// P = Z + beta P (FP32); Z = R without a preconditioner.
 template <int VW>
-__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ R, int64_t p, RcgState S) {
+__global__ void k_rcg_pupdate(float* __restrict__ P, const float* __restrict__ Z, int64_t p, RcgState S) {
+    pdl_wait();
+    pdl_launch_dependents();
     const int k = blockIdx.y;
     if (S.done[k]) return;
     const float b = (float)S.beta[k];
     float* Pk = P + (int64_t)k * p;
-    const float* Rk = R + (int64_t)k * p;
+    const float* Zk = Z + (int64_t)k * p;
     const int64_t nv = p / VW;
     for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
-        float r[VW], pv[VW];
-        load_vec<float, VW>(Rk + xv * VW, r);
+        float z[VW], pv[VW];
+        load_vec<float, VW>(Zk + xv * VW, z);
         load_vec<float, VW>(Pk + xv * VW, pv);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) pv[e] = r[e] + b * pv[e];
+        for (int e = 0; e < VW; ++e) pv[e] = z[e] + b * pv[e];
         store_vec<float, VW>(Pk + xv * VW, pv);
     }
 }
@@ -1080,22 +1137,113 @@ __global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restric
 }
 
 // Residual replacement of the columns still running: R = (float) R64,
-// gamma = gamma_ref = ||R64||^2 (P is kept); done when ||R64|| <= rtol ||B|| or
-// the iteration budget is spent (a non-finite residual also ends the column;
-// the caller reports it).
+// rr = rr_ref = ||R64||^2 and, without a preconditioner, gamma = rr (P is
+// kept); done when ||R64|| <= rtol ||B|| or the iteration budget is spent (a
+// non-finite residual also ends the column; the caller reports it).
 __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
-                              const double* __restrict__ norms, RcgState S, int maxit) {
+                              const double* __restrict__ norms, RcgState S, int maxit, int precond) {
     const int k = blockIdx.y;
     if (S.done[k]) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
         R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double rn = norms[2 * k];
-        S.gam[k] = rn * rn;
-        S.gam_ref[k] = rn * rn;
+        if (!precond) S.gam[k] = rn * rn;
+        S.rr[k] = rn * rn;
+        S.rr_ref[k] = rn * rn;
         S.want[k] = 0;
         if (rn * rn <= S.thr2[k] || S.iters[k] >= maxit || !(rn == rn)) S.done[k] = 1;
     }
+}
+
+// gamma = r^T z after a replacement (preconditioned runs): the fixed-order sum
+// of the preconditioner matvec's partials.
+__global__ void k_rcg_regamma(RcgState S, const double* __restrict__ part_rz, int nrz) {
+    const int k = blockIdx.x;
+    if (S.done[k]) return;
+    const double g = block_sum(part_rz + (int64_t)k * nrz, nrz);
+    if (threadIdx.x == 0) S.gam[k] = g;
+}
+
+// Fused iterations: R -= alpha Q with the partials of ||R||^2; the last block
+// of each column (a ticket per column, taken after its partial is stored)
+// sums them in a fixed order and does the scalar step of k_rcg_beta.  (The
+// x and p updates run in the next pass A, the step alpha in pass C.)
+template <int VW>
+__global__ void k_rcg_rupdate(float* __restrict__ R, const float* __restrict__ Q, int64_t p, RcgState S,
+                              double* __restrict__ part_rr, unsigned* __restrict__ cnt, int maxit) {
+    pdl_wait();
+    pdl_launch_dependents();
+    const int k = blockIdx.y;
+    if (S.done[k]) return;
+    const float af = (float)S.alpha[k];
+    const int64_t off = (int64_t)k * p;
+    const int64_t nv = p / VW;
+    DFAcc nrm;
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off + xv * VW;
+        float r[VW], qv[VW];
+        load_vec<float, VW>(R + o, r);
+        load_vec<float, VW>(Q + o, qv);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            r[e] -= af * qv[e];
+            nrm.add_prod(r[e], r[e]);
+        }
+        store_vec<float, VW>(R + o, r);
+    }
+    double acc[1] = {nrm.value()};
+    block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
+    __shared__ unsigned ticket;
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's partial before its ticket
+        ticket = atomicAdd(&cnt[k], 1u);
+    }
+    __syncthreads();
+    if (ticket != gridDim.x - 1) return;
+    __threadfence();
+    const double rr = block_sum_cg(part_rr + (int64_t)k * gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+        const double g0 = S.gam[k];
+        S.beta[k] = (g0 > 0.0) ? rr / g0 : 0.0;
+        S.gam[k] = rr;
+        S.rr[k] = rr;
+        const int it = S.iters[k] + 1;
+        S.iters[k] = it;
+        S.want[k] = (rr <= S.thr2[k] || rr <= 1e-2 * S.rr_ref[k] || !(rr == rr) || it >= maxit) ? 1 : 0;
+        cnt[k] = 0u;
+    }
+}
+
+// The x update still pending in fused iterations: X += alpha P for the
+// columns that are not done (before a residual replacement and at the end).
+template <int VW>
+__global__ void k_rcg_xflush(float* __restrict__ Xh, float* __restrict__ Xl, const float* __restrict__ P, int64_t p,
+                             RcgState S) {
+    const int k = blockIdx.y;
+    if (S.done[k]) return;
+    const double a = S.alpha[k];
+    if (a == 0.0) return;
+    float ahi, alo;
+    df_split(a, ahi, alo);
+    const int64_t off = (int64_t)k * p;
+    const int64_t nv = p / VW;
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off + xv * VW;
+        float pv[VW], xh[VW], xl[VW];
+        load_vec<float, VW>(P + o, pv);
+        load_vec<float, VW>(Xh + o, xh);
+        load_vec<float, VW>(Xl + o, xl);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) df_axpy(xh[e], xl[e], ahi, alo, pv[e]);
+        store_vec<float, VW>(Xh + o, xh);
+        store_vec<float, VW>(Xl + o, xl);
+    }
+}
+
+__global__ void k_rcg_zero_alpha(RcgState S, int nrhs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrhs && !S.done[k]) S.alpha[k] = 0.0;
 }
 
 __global__ void k_count_done(RcgState S, int nrhs) {
@@ -1107,9 +1255,11 @@ __global__ void k_count_done(RcgState S, int nrhs) {
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
                           int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt);
 
-// Returns the largest per-column iteration count.
+// Returns the largest per-column iteration count.  pre: preconditioner
+// embedding (NULL: plain CG).
 static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx,
-                       int nrhs, double rtol, int maxit, std::vector<double>& nrm, bool* fresh, int vpt) {
+                       int nrhs, double rtol, int maxit, std::vector<double>& nrm, bool* fresh, int vpt,
+                       const kry_embed* pre) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     const size_t vb = (size_t)nrhs * p * sizeof(float);
@@ -1119,23 +1269,38 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     float* R = ctx->work[7].as<float>();
     float* P = ctx->work[8].as<float>();
     float* Q = ctx->work[9].as<float>();
+    float* Z = R;
+    if (pre) {
+        ctx->work[3].ensure(vb);
+        Z = ctx->work[3].as<float>();
+    }
     const int nblkC = matvec_num_partials(ctx, e, false, nrhs);
     const int nbc = cg_blocks(nrhs);
-    ctx->work[10].ensure((size_t)nrhs * (nblkC + nbc) * sizeof(double));
+    ctx->work[10].ensure((size_t)nrhs * (2 * nblkC + nbc) * sizeof(double));
     double* part_pq = ctx->work[10].as<double>();        // matvec partials (p^T K p)
     double* part_rr = part_pq + (size_t)nrhs * nblkC;     // start / update partials (r^T r)
-    ctx->work[11].ensure((size_t)nrhs * (5 * sizeof(double) + 3 * sizeof(int)) + 64);
+    double* part_rz = pre ? part_rr + (size_t)nrhs * nbc : nullptr;   // preconditioner partials (r^T z)
+    // fused iterations: x and p updates in pass A, alpha in pass C (plain CG on
+    // the length-specialised passes)
+    const bool fused = !pre && matvec_cg_fusable(ctx, e, nrhs);
+    const int npairs = (nrhs + 1) / 2;
+    ctx->work[11].ensure((size_t)nrhs * (6 * sizeof(double) + 4 * sizeof(int)) + (size_t)npairs * sizeof(unsigned) +
+                         64);
     char* sb = ctx->work[11].as<char>();
     RcgState S;
     S.gam = reinterpret_cast<double*>(sb);
-    S.alpha = S.gam + nrhs;
+    S.rr = S.gam + nrhs;
+    S.alpha = S.rr + nrhs;
     S.beta = S.alpha + nrhs;
-    S.gam_ref = S.beta + nrhs;
-    S.thr2 = S.gam_ref + nrhs;
+    S.rr_ref = S.beta + nrhs;
+    S.thr2 = S.rr_ref + nrhs;
     S.want = reinterpret_cast<int*>(S.thr2 + nrhs);
     S.done = S.want + nrhs;
     S.iters = S.done + nrhs;
     S.ndone = S.iters + nrhs;
+    unsigned* cnt_col = reinterpret_cast<unsigned*>(S.ndone + 1);   // tickets of the fused kernels
+    unsigned* cnt_pair = cnt_col + nrhs;
+    KRY_CUDA(cudaMemsetAsync(cnt_col, 0, (size_t)(nrhs + npairs) * sizeof(unsigned), st));
     ctx->tolbuf.ensure(nrhs * sizeof(double));
     std::vector<double> tol_h(nrhs, rtol);
     KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1151,13 +1316,39 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
     const bool vec = p % 4 == 0;   // 16-byte accesses: every column start is 16-byte aligned
     auto to_f64 = [&]() {
+        if (fused) {   // the x update the next pass A would have applied
+            if (vec)
+                k_rcg_xflush<4><<<gc, 256, 0, st>>>(Xh, Xl, P, p, S);
+            else
+                k_rcg_xflush<1><<<gc, 256, 0, st>>>(Xh, Xl, P, p, S);
+            KRY_CHECK_LAUNCH();
+            k_rcg_zero_alpha<<<1, tbeta, 0, st>>>(S, nrhs);
+            KRY_CHECK_LAUNCH();
+        }
         k_df_to_f64<<<gv, 256, 0, st>>>(Xh, Xl, p, X, ldx);
         KRY_CHECK_LAUNCH();
     };
+    kspec::CgFuse cgf{};
+    if (fused) {
+        cgf.P = P;
+        cgf.R = R;
+        cgf.Xh = Xh;
+        cgf.Xl = Xl;
+        cgf.alpha = S.alpha;
+        cgf.beta = S.beta;
+        cgf.done = S.done;
+        cgf.cnt = cnt_pair;
+        cgf.gam = S.gam;
+        cgf.alpha_out = S.alpha;
+    }
     k_rcg_start<<<gc, 256, 0, st>>>(B, ldb, Xh, Xl, R, P, p, part_rr);
     KRY_CHECK_LAUNCH();
-    k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part_rr, nbc, nrhs, ctx->tolbuf.as<double>());
+    if (pre) matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, nullptr);   // z = M^-1 r
+    k_rcg_init_scalars<<<1, tbeta, 0, st>>>(S, part_rr, nbc, part_rz, nblkC, nrhs, ctx->tolbuf.as<double>());
     KRY_CHECK_LAUNCH();
+    if (pre) {   // p = z (beta = 0)
+        launch_pdl(vec ? k_rcg_pupdate<4> : k_rcg_pupdate<1>, gc, dim3(256), 0, st, P, (const float*)Z, p, S);
+    }
     int* hflag = reinterpret_cast<int*>(ctx->host_pinned);
     const int poll = 8;
     nrm.assign(2 * nrhs, 0.0);
@@ -1165,22 +1356,23 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     // one CG iteration on ctx->stream (the capture stream while capturing)
     auto iterate = [&]() {
         cudaStream_t s2 = ctx->stream;
-        // columns that have converged are not transformed (pairs of finished columns skip every pass)
+        if (fused) {   // pass A: x += alpha p, p = r + beta p; pass C: alpha; then r -= alpha q and beta
+            matvec_cg(ctx, e, P, p, Q, nrhs, part_pq, nblkC, vpt, S.done, cgf);
+            launch_pdl(vec ? k_rcg_rupdate<4> : k_rcg_rupdate<1>, gc, dim3(256), 0, s2, R, (const float*)Q, p, S,
+                       part_rr, cnt_col, maxit);
+            return;
+        }
+        // kernels launched back to back with programmatic dependent launch: each
+        // waits for its predecessor's completion before touching its outputs;
+        // columns that have converged are not transformed (pairs of finished
+        // columns skip every pass)
         matvec_ex<float>(ctx, e, P, p, nullptr, Q, p, nrhs, part_pq, nblkC, vpt, S.done);
-        k_rcg_alpha<<<nrhs, FIN_THREADS, 0, s2>>>(S, part_pq, nblkC);
-        KRY_CHECK_LAUNCH();
-        if (vec)
-            k_rcg_update<4><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part_rr);
-        else
-            k_rcg_update<1><<<gc, 256, 0, s2>>>(Xh, Xl, R, P, Q, p, S, part_rr);
-        KRY_CHECK_LAUNCH();
-        k_rcg_beta<<<nrhs, FIN_THREADS, 0, s2>>>(S, part_rr, nbc, maxit);
-        KRY_CHECK_LAUNCH();
-        if (vec)
-            k_rcg_pupdate<4><<<gc, 256, 0, s2>>>(P, R, p, S);
-        else
-            k_rcg_pupdate<1><<<gc, 256, 0, s2>>>(P, R, p, S);
-        KRY_CHECK_LAUNCH();
+        launch_pdl(k_rcg_alpha, dim3(nrhs), dim3(FIN_THREADS), 0, s2, S, part_pq, nblkC);
+        launch_pdl(vec ? k_rcg_update<4> : k_rcg_update<1>, gc, dim3(256), 0, s2, Xh, Xl, R, P, Q, p, S, part_rr);
+        if (pre) matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, S.done);
+        launch_pdl(k_rcg_beta, dim3(nrhs), dim3(FIN_THREADS), 0, s2, S, part_rr, nbc, (const double*)part_rz, nblkC,
+                   maxit);
+        launch_pdl(vec ? k_rcg_pupdate<4> : k_rcg_pupdate<1>, gc, dim3(256), 0, s2, P, (const float*)Z, p, S);
     };
     // Iterations run in blocks of `poll`.  The first block runs directly (it
     // sizes every buffer); later blocks replay one captured graph.
@@ -1205,8 +1397,13 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             to_f64();
             true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
             double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
-            k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit);
+            k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit, pre ? 1 : 0);
             KRY_CHECK_LAUNCH();
+            if (pre) {   // z = M^-1 r and gamma = r^T z for the replaced r
+                matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, S.done);
+                k_rcg_regamma<<<nrhs, FIN_THREADS, 0, st>>>(S, part_rz, nblkC);
+                KRY_CHECK_LAUNCH();
+            }
             k_count_done<<<1, 1, 0, st>>>(S, nrhs);
             KRY_CHECK_LAUNCH();
             KRY_CUDA(cudaMemcpyAsync(hflag, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1227,7 +1424,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
 }
 
 SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, double* X, int64_t ldx, int nrhs,
-                double rtol, int maxit, int vpt) {
+                double rtol, int maxit, int vpt = 0, const kry_embed* pre = nullptr) {
     SolveInfo info;
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
@@ -1249,7 +1446,7 @@ SolveInfo solve(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, 
                                    cudaMemcpyDeviceToDevice, st));
     } else {
         // FP32 CG with FP64 solution and residual replacement
-        info.iters = cg_reliable(ctx, e, B, ldb, X, ldx, nrhs, rtol, maxit, nrm, &fresh, vpt);
+        info.iters = cg_reliable(ctx, e, B, ldb, X, ldx, nrhs, rtol, maxit, nrm, &fresh, vpt, pre);
     }
     // the reported residual is always the true FP64 residual of the returned X
     if (!fresh) true_residual(ctx, e, B, ldb, X, ldx, nrhs, R, ctx->kxbuf.as<double>(), nrm, vpt);

@@ -14,9 +14,8 @@ struct RunB {
         auto k = ks_pass_b<B, NT>;
         KRY_ALLOW_MAX_SMEM(k);
         dim3 grid(a.M2 / NT, a.np);
-        k<<<grid, tpb(B, NT), smem_bytes(B, NT), st>>>(a.slab, a.lamP, a.n1, a.M2, a.twt, a.pair0, a.lam_stride,
+        launch_pdl(k, grid, dim3(tpb(B, NT)), smem_bytes(B, NT), st, a.slab, a.lamP, a.n1, a.M2, a.twt, a.pair0, a.lam_stride,
                                                        a.vpt, a.skip, a.nvec);
-        KRY_CHECK_LAUNCH();
         return true;
     }
 };

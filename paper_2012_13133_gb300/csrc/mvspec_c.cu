@@ -14,10 +14,9 @@ struct RunC {
         auto k = ks_pass_c<B, NT>;
         KRY_ALLOW_MAX_SMEM(k);
         dim3 grid((a.n1 + NT - 1) / NT, a.np);
-        k<<<grid, tpb(B, NT), smem_bytes(B, NT), st>>>(a.slab, a.vin, a.ld_in, a.scale, a.vout, a.ld_out, a.nvec,
+        launch_pdl(k, grid, dim3(tpb(B, NT)), smem_bytes(B, NT), st, a.slab, a.vin, a.ld_in, a.scale, a.vout, a.ld_out, a.nvec,
                                                        a.pair0, a.rowptr, a.colidx, a.n1, a.n2, a.C, a.logC, a.tau2,
-                                                       a.dots, a.nds, a.twt, a.tau2v, a.vpt, a.skip);
-        KRY_CHECK_LAUNCH();
+                                                       a.dots, a.nds, a.twt, a.tau2v, a.vpt, a.skip, a.cg);
         return true;
     }
 };

@@ -88,6 +88,7 @@ int64_t estimate_bytes(const kry_request& r, int64_t p) {
     b += (int64_t)r.n1 * M2 * 16 * ((nc + 1) / 2);    // FP64 slab (true residuals)
     b += 4 * vecs * p * 4 + 4 * nc * p * 8;        // Lanczos / CG vectors, FP64 residual work
     b += 3 * (int64_t)nc * p * 8 + (N + p) * 8;    // [y, X], solutions, kriging grid
+    if (r.opts.precond) b += 16 * MM + (int64_t)nc * p * 4;   // preconditioner eigenvalues, z vectors
     if (r.kind == KRY_REQ_LOGLIK && r.opts.reorth)   // stored Lanczos basis
         b += (int64_t)r.opts.nprobe * r.opts.nsteps * p * (r.opts.prec == KRY_F64 ? 8 : 4);
     b += N + p * 8 * (1 + r.ncov) + (N - p) * 8 * (2 + r.ncov);   // inputs and outputs

@@ -40,7 +40,7 @@ class kry_cov(C.Structure):
 
 class kry_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("nprobe", C.c_int32), ("nsteps", C.c_int32), ("seed", C.c_uint64),
-                ("rtol", C.c_double), ("maxit", C.c_int32), ("reorth", C.c_int32)]
+                ("rtol", C.c_double), ("maxit", C.c_int32), ("reorth", C.c_int32), ("precond", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -69,6 +69,8 @@ SIGNATURES = {
     "kry_logdet": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, _DP, _DP, _DP]),
     "kry_solve": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32,
                             C.POINTER(C.c_int32), _DP]),
+    "kry_solve_pre": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64, C.c_double, C.c_int32,
+                                C.POINTER(C.c_int32), _DP]),
     "kry_profile_loglik": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(kry_cov), C.c_int32, C.POINTER(kry_opts),
                                      _DP, _DP, _DP, _DP]),
     "kry_krige": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), _P, _P, C.c_int32, _P, _P, C.c_int64,
@@ -180,9 +182,11 @@ class Opts:
     rtol: float = 1e-6
     maxit: int = 5000
     reorth: int = 0   # 1: partial reorthogonalisation of the Lanczos basis
+    precond: int = 0  # 1: CG preconditioned by the torus inverse (clustered gaps)
 
     def c(self) -> kry_opts:
-        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.reorth)
+        return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.reorth,
+                        self.precond)
 
 
 class Embed:
@@ -290,8 +294,9 @@ class Context:
                                     C.byref(se), _np_dp(per)))
         return ld.value, se.value, per
 
-    def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, X=None):
-        """B: (nrhs, p) float64 CUDA tensor.  Returns (X, iters, relres, status)."""
+    def solve(self, emb: Embed, B, rtol=1e-8, maxit=5000, X=None, precond=False):
+        """B: (nrhs, p) float64 CUDA tensor.  Returns (X, iters, relres, status).  precond: CG
+        preconditioned by the torus inverse (kry_solve_pre)."""
         squeeze = B.dim() == 1
         Bm = (B.reshape(1, -1) if squeeze else B).contiguous()
         if X is None:
@@ -299,8 +304,9 @@ class Context:
         it, rr = C.c_int32(), C.c_double()
         n = Bm.shape[0] * self.p
         pb, px = _dev((Bm, F64, n, "B"), (X, F64, n, "X"))
-        st = self._check(_lib.kry_solve(self.h, emb.handle, pb, px, Bm.shape[0], self.p, rtol, maxit,
-                                        C.byref(it), C.byref(rr)), allow=(KRY_ENOCONV,))
+        fn = _lib.kry_solve_pre if precond else _lib.kry_solve
+        st = self._check(fn(self.h, emb.handle, pb, px, Bm.shape[0], self.p, rtol, maxit, C.byref(it),
+                            C.byref(rr)), allow=(KRY_ENOCONV,))
         return (X.reshape(-1) if squeeze else X), it.value, rr.value, st
 
     def profile_loglik(self, y, X, thetas, opts: Opts):

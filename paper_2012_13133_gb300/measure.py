@@ -2,6 +2,7 @@
 
   python -m paper_2012_13133_gb300.measure --workload search512   # batched vs one setting at a time
   python -m paper_2012_13133_gb300.measure --workload large4096   # log-likelihood + kriging means, wall time
+  python -m paper_2012_13133_gb300.measure --workload large4096 --solves   # CG on [y, X], plain vs preconditioned
   python -m paper_2012_13133_gb300.measure --workload tiny32      # FP64 evaluations per second
   python -m paper_2012_13133_gb300.measure --workload grid1024 --bccb   # BCCB log-det + derivative
   python -m paper_2012_13133_gb300.measure --workload grid1024 --bootstrap 20   # bootstrap kriging MSE
@@ -62,6 +63,9 @@ def main():
     ap.add_argument("--genhybr", type=int, default=0, help="time genHyBR (Alg. 1 + Eq. prof_lik) with k steps")
     ap.add_argument("--bootstrap", type=int, default=0,
                     help="time the parametric-bootstrap kriging MSE with this many replicates at all missing cells")
+    ap.add_argument("--precond", type=int, default=0, help="kry_opts.precond for the CG solves (1: torus inverse)")
+    ap.add_argument("--solves", action="store_true",
+                    help="time CG on [y, X] with and without the torus-inverse preconditioner")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
@@ -80,10 +84,11 @@ def main():
         xi = torch.tensor(rng.standard_normal((nrep, 2, M1, M2)), device=dev)
         eps = torch.tensor(rng.standard_normal((nrep, p)), device=dev)
         cells = torch.tensor(np.flatnonzero(~mask.ravel()).astype(np.int64), device=dev)
-        opts = kry.Opts(prec=kry.KRY_F32, rtol=w.cg_tol, maxit=30000)
+        opts = kry.Opts(prec=kry.KRY_F32, rtol=w.cg_tol, maxit=30000, precond=args.precond)
         (var, st), t = timed(lambda: ctx.bootstrap_var(w.cov, opts, xi, eps, cells))
         v = var.cpu().numpy()
         out.update({"replicates": nrep, "cells": int(cells.numel()), "bootstrap_s": t, "status": int(st),
+                    "precond": args.precond,
                     "mean_var": float(v.mean()), "min_var": float(v.min()), "max_var": float(v.max())})
     elif args.bccb:
         ctx.bccb_logdet(w.cov)
@@ -106,9 +111,19 @@ def main():
                     "one_at_a_time_evals_per_s": len(thetas) / ts, "max_rel_loglik_diff": diff,
                     "best_setting": {"range": thetas[best].range, "nu": thetas[best].nu},
                     "status": int(batch["status"])})
+    elif args.solves:
+        emb = ctx.embed(w.cov, kry.KRY_F32)
+        B = torch.cat([y.reshape(1, -1), X], 0).contiguous()
+        res = {}
+        for pre in (False, True):
+            (Z, it, rr, st), t = timed(lambda: ctx.solve(emb, B, rtol=w.cg_tol, maxit=60000, precond=pre))
+            res["preconditioned" if pre else "plain"] = {"iterations": it, "relres": rr, "status": int(st),
+                                                         "solve_s": t}
+        emb.free()
+        out.update({"rhs": int(B.shape[0]), "rtol": w.cg_tol, **res})
     elif args.workload == "large4096":
         opts = kry.Opts(prec=kry.KRY_F32, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,
-                        maxit=60000, reorth=w.reorth)
+                        maxit=60000, reorth=w.reorth, precond=args.precond)
         cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
         Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
         ct, xt = torch.tensor(cells, device=dev), torch.tensor(Xc.T.copy(), device=dev)
@@ -117,7 +132,7 @@ def main():
         emb.free()
         res, t = timed(lambda: ctx.loglik_krige(w.cov, opts, y, X, cells=ct, Xc=xt))
         out.update({"probes": w.nprobe, "lanczos_steps": w.nsteps, "kriging_cells": int(cells.size),
-                    "loglik_krige_s": t, "loglik": res["loglik"], "status": int(res["status"]),
+                    "loglik_krige_s": t, "loglik": res["loglik"], "status": int(res["status"]), "precond": args.precond,
                     "tuned_schedules": tuned})
     else:
         opts = kry.Opts(prec=kry.KRY_F64, nprobe=w.nprobe, nsteps=w.nsteps, seed=w.probe_seed, rtol=w.cg_tol,

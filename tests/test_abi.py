@@ -47,7 +47,7 @@ def test_binding_signatures_cover_header(libpath):
 STRUCTS = {
     "kry_grid": ["n1", "n2", "dx1", "dx2"],
     "kry_cov": ["sigma2", "range", "nu", "tau2", "aniso_angle", "aniso_ratio"],
-    "kry_opts": ["prec", "nprobe", "nsteps", "seed", "rtol", "maxit", "reorth"],
+    "kry_opts": ["prec", "nprobe", "nsteps", "seed", "rtol", "maxit", "reorth", "precond"],
     "kry_request": ["kind", "n1", "n2", "mask", "y", "X", "ncov", "cov", "opts", "loglik", "logdet", "beta",
                     "target_cells", "target_X", "mean"],
 }
