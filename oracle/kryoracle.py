@@ -325,6 +325,34 @@ def cg(matvec, b, tol=1e-10, maxit=100000):
     return x, maxit
 
 
+def pcg(matvec, precond, b, tol=1e-10, maxit=100000):
+    """Preconditioned CG from x0 = 0 with the stopping rule of ``cg`` (||r|| <= tol ||b||):
+    z = M^-1 r, alpha = r^T z / p^T A p, x += alpha p, r -= alpha A p, p = z + (r'^T z' / r^T z) p.
+    For symmetric positive definite A and M^-1 it converges to the same solution A^-1 b as plain
+    CG (the solves of Sec. 3 need only matvecs).  Returns (x, iterations)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = math.sqrt(float(b @ b))
+    if bnorm == 0.0:
+        return x, 0
+    z = precond(r)
+    p = z.copy()
+    rz = float(r @ z)
+    for it in range(1, maxit + 1):
+        Ap = matvec(p)
+        a = rz / float(p @ Ap)
+        x += a * p
+        r -= a * Ap
+        if math.sqrt(float(r @ r)) <= tol * bnorm:
+            return x, it
+        z = precond(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit
+
+
 # --------------------------------------------------------------------------------------
 # Profile log-likelihood and kriging
 # --------------------------------------------------------------------------------------
@@ -389,11 +417,25 @@ class FFTProblem:
         g[self.mask] = v
         return sigma_conv_fft(self.n1, self.n2, self.M1, self.M2, self.lam, g).ravel()[cells]
 
-    def solve(self, B, tol=1e-10):
+    def torus_inverse(self, v):
+        """A (S + tau^2 I)^-1 A^T v with S the circulant embedding of sigma^2 Sigma on the M1 x M2
+        torus: the inverse of the torus covariance plus nugget, restricted to the observed cells
+        (eigenvalues 1 / (max(Lambda, 0) + tau^2) in the FFT basis; a CG preconditioner)."""
+        lam_inv = 1.0 / (np.maximum(self.lam, 0.0) + self.cov.tau2)
+        g = np.zeros((self.n1, self.n2))
+        g[self.mask] = v
+        return sigma_conv_fft(self.n1, self.n2, self.M1, self.M2, lam_inv, g)[self.mask]
+
+    def solve(self, B, tol=1e-10, precond=False):
+        """K^-1 B by CG (precond=True: CG preconditioned by ``torus_inverse``, same solution)."""
         B = np.asarray(B, dtype=np.float64)
+
+        def one(b):
+            return pcg(self.matvec, self.torus_inverse, b, tol) if precond else cg(self.matvec, b, tol)
+
         if B.ndim == 1:
-            return cg(self.matvec, B, tol)
-        cols, its = zip(*(cg(self.matvec, B[:, j], tol) for j in range(B.shape[1])))
+            return one(B)
+        cols, its = zip(*(one(B[:, j]) for j in range(B.shape[1])))
         return np.stack(cols, axis=1), max(its)
 
     def logdet(self, nprobe, nsteps, seed, probe_ids=None, reorth=False):

@@ -20,7 +20,6 @@
 #include "fft.cuh"
 #include "kry_internal.cuh"
 #include "matern.cuh"
-#include "mvspec.cuh"
 
 namespace kry {
 
@@ -28,10 +27,6 @@ template <typename T>
 void matvec_ex(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                int64_t ld_out, int nvec, double* dots, int nds, int vpt = 0, const int* skip = nullptr);
 int matvec_num_partials(kry_ctx* ctx, const kry_embed* e, bool dbl, int nvec);
-
-bool matvec_cg_fusable(kry_ctx* ctx, const kry_embed* e, int nvec);
-void matvec_cg(kry_ctx* ctx, const kry_embed* e, float* P, int64_t ld, float* Q, int nvec, double* dots, int nds,
-               int vpt, const int* skip, const kspec::CgFuse& cg);
 
 static const int RED_BLOCKS = 128;   // fixed block count of the vector reductions
 
@@ -197,21 +192,6 @@ __device__ __forceinline__ double block_sum(const double* __restrict__ part, int
     __shared__ double ws[32];
     double v = 0.0;
     for (int b = threadIdx.x; b < n; b += blockDim.x) v += part[b];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-    return t;
-}
-
-// block_sum over partials written by other blocks of the running grid (read
-// through L2, after the caller's __threadfence).
-__device__ __forceinline__ double block_sum_cg(const double* __restrict__ part, int n) {
-    __shared__ double ws[32];
-    double v = 0.0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) v += __ldcg(part + b);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
     __syncthreads();
@@ -1165,87 +1145,6 @@ __global__ void k_rcg_regamma(RcgState S, const double* __restrict__ part_rz, in
     if (threadIdx.x == 0) S.gam[k] = g;
 }
 
-// Fused iterations: R -= alpha Q with the partials of ||R||^2; the last block
-// of each column (a ticket per column, taken after its partial is stored)
-// sums them in a fixed order and does the scalar step of k_rcg_beta.  (The
-// x and p updates run in the next pass A, the step alpha in pass C.)
-template <int VW>
-__global__ void k_rcg_rupdate(float* __restrict__ R, const float* __restrict__ Q, int64_t p, RcgState S,
-                              double* __restrict__ part_rr, unsigned* __restrict__ cnt, int maxit) {
-    pdl_wait();
-    pdl_launch_dependents();
-    const int k = blockIdx.y;
-    if (S.done[k]) return;
-    const float af = (float)S.alpha[k];
-    const int64_t off = (int64_t)k * p;
-    const int64_t nv = p / VW;
-    DFAcc nrm;
-    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = off + xv * VW;
-        float r[VW], qv[VW];
-        load_vec<float, VW>(R + o, r);
-        load_vec<float, VW>(Q + o, qv);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-            r[e] -= af * qv[e];
-            nrm.add_prod(r[e], r[e]);
-        }
-        store_vec<float, VW>(R + o, r);
-    }
-    double acc[1] = {nrm.value()};
-    block_sum_store<1>(acc, part_rr + (int64_t)k * gridDim.x + blockIdx.x, 0);
-    __shared__ unsigned ticket;
-    if (threadIdx.x == 0) {
-        __threadfence();   // this block's partial before its ticket
-        ticket = atomicAdd(&cnt[k], 1u);
-    }
-    __syncthreads();
-    if (ticket != gridDim.x - 1) return;
-    __threadfence();
-    const double rr = block_sum_cg(part_rr + (int64_t)k * gridDim.x, gridDim.x);
-    if (threadIdx.x == 0) {
-        const double g0 = S.gam[k];
-        S.beta[k] = (g0 > 0.0) ? rr / g0 : 0.0;
-        S.gam[k] = rr;
-        S.rr[k] = rr;
-        const int it = S.iters[k] + 1;
-        S.iters[k] = it;
-        S.want[k] = (rr <= S.thr2[k] || rr <= 1e-2 * S.rr_ref[k] || !(rr == rr) || it >= maxit) ? 1 : 0;
-        cnt[k] = 0u;
-    }
-}
-
-// The x update still pending in fused iterations: X += alpha P for the
-// columns that are not done (before a residual replacement and at the end).
-template <int VW>
-__global__ void k_rcg_xflush(float* __restrict__ Xh, float* __restrict__ Xl, const float* __restrict__ P, int64_t p,
-                             RcgState S) {
-    const int k = blockIdx.y;
-    if (S.done[k]) return;
-    const double a = S.alpha[k];
-    if (a == 0.0) return;
-    float ahi, alo;
-    df_split(a, ahi, alo);
-    const int64_t off = (int64_t)k * p;
-    const int64_t nv = p / VW;
-    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = off + xv * VW;
-        float pv[VW], xh[VW], xl[VW];
-        load_vec<float, VW>(P + o, pv);
-        load_vec<float, VW>(Xh + o, xh);
-        load_vec<float, VW>(Xl + o, xl);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) df_axpy(xh[e], xl[e], ahi, alo, pv[e]);
-        store_vec<float, VW>(Xh + o, xh);
-        store_vec<float, VW>(Xl + o, xl);
-    }
-}
-
-__global__ void k_rcg_zero_alpha(RcgState S, int nrhs) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nrhs && !S.done[k]) S.alpha[k] = 0.0;
-}
-
 __global__ void k_count_done(RcgState S, int nrhs) {
     int d = 0;
     for (int k = 0; k < nrhs; ++k) d += S.done[k];
@@ -1280,12 +1179,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     double* part_pq = ctx->work[10].as<double>();        // matvec partials (p^T K p)
     double* part_rr = part_pq + (size_t)nrhs * nblkC;     // start / update partials (r^T r)
     double* part_rz = pre ? part_rr + (size_t)nrhs * nbc : nullptr;   // preconditioner partials (r^T z)
-    // fused iterations: x and p updates in pass A, alpha in pass C (plain CG on
-    // the length-specialised passes)
-    const bool fused = !pre && matvec_cg_fusable(ctx, e, nrhs);
-    const int npairs = (nrhs + 1) / 2;
-    ctx->work[11].ensure((size_t)nrhs * (6 * sizeof(double) + 4 * sizeof(int)) + (size_t)npairs * sizeof(unsigned) +
-                         64);
+    ctx->work[11].ensure((size_t)nrhs * (6 * sizeof(double) + 3 * sizeof(int)) + 64);
     char* sb = ctx->work[11].as<char>();
     RcgState S;
     S.gam = reinterpret_cast<double*>(sb);
@@ -1298,9 +1192,6 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     S.done = S.want + nrhs;
     S.iters = S.done + nrhs;
     S.ndone = S.iters + nrhs;
-    unsigned* cnt_col = reinterpret_cast<unsigned*>(S.ndone + 1);   // tickets of the fused kernels
-    unsigned* cnt_pair = cnt_col + nrhs;
-    KRY_CUDA(cudaMemsetAsync(cnt_col, 0, (size_t)(nrhs + npairs) * sizeof(unsigned), st));
     ctx->tolbuf.ensure(nrhs * sizeof(double));
     std::vector<double> tol_h(nrhs, rtol);
     KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1316,31 +1207,9 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     const int tbeta = std::max(32, ((nrhs + 31) / 32) * 32);
     const bool vec = p % 4 == 0;   // 16-byte accesses: every column start is 16-byte aligned
     auto to_f64 = [&]() {
-        if (fused) {   // the x update the next pass A would have applied
-            if (vec)
-                k_rcg_xflush<4><<<gc, 256, 0, st>>>(Xh, Xl, P, p, S);
-            else
-                k_rcg_xflush<1><<<gc, 256, 0, st>>>(Xh, Xl, P, p, S);
-            KRY_CHECK_LAUNCH();
-            k_rcg_zero_alpha<<<1, tbeta, 0, st>>>(S, nrhs);
-            KRY_CHECK_LAUNCH();
-        }
         k_df_to_f64<<<gv, 256, 0, st>>>(Xh, Xl, p, X, ldx);
         KRY_CHECK_LAUNCH();
     };
-    kspec::CgFuse cgf{};
-    if (fused) {
-        cgf.P = P;
-        cgf.R = R;
-        cgf.Xh = Xh;
-        cgf.Xl = Xl;
-        cgf.alpha = S.alpha;
-        cgf.beta = S.beta;
-        cgf.done = S.done;
-        cgf.cnt = cnt_pair;
-        cgf.gam = S.gam;
-        cgf.alpha_out = S.alpha;
-    }
     k_rcg_start<<<gc, 256, 0, st>>>(B, ldb, Xh, Xl, R, P, p, part_rr);
     KRY_CHECK_LAUNCH();
     if (pre) matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, nullptr);   // z = M^-1 r
@@ -1356,12 +1225,6 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     // one CG iteration on ctx->stream (the capture stream while capturing)
     auto iterate = [&]() {
         cudaStream_t s2 = ctx->stream;
-        if (fused) {   // pass A: x += alpha p, p = r + beta p; pass C: alpha; then r -= alpha q and beta
-            matvec_cg(ctx, e, P, p, Q, nrhs, part_pq, nblkC, vpt, S.done, cgf);
-            launch_pdl(vec ? k_rcg_rupdate<4> : k_rcg_rupdate<1>, gc, dim3(256), 0, s2, R, (const float*)Q, p, S,
-                       part_rr, cnt_col, maxit);
-            return;
-        }
         // kernels launched back to back with programmatic dependent launch: each
         // waits for its predecessor's completion before touching its outputs;
         // columns that have converged are not transformed (pairs of finished

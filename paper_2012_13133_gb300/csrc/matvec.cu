@@ -633,8 +633,7 @@ static void sched16(kry_ctx* ctx, int M1, int M2, bool dbl, int nvec, int* G, in
 template <typename T>
 static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                          int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode,
-                         typename cx_of<T>::type* slab, int ppb, int vpt, const int* skip,
-                         const kspec::CgFuse* cg = nullptr) {
+                         typename cx_of<T>::type* slab, int ppb, int vpt, const int* skip) {
     const bool dbl = sizeof(T) == 8;
     const int n1 = e->n1, n2 = e->n2, M1 = e->M1, M2 = e->M2;
     int G, C;
@@ -661,7 +660,6 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
             a.slab = slab; a.lamP = e->lam32P; a.lam_stride = e->lam_stride; a.vpt = vpt;
             a.tau2 = tau2; a.tau2v = ctx->no_nugget ? nullptr : e->tau2_dev; a.dots = dots; a.nds = nds;
             a.twt = ctx->twt32.as<float4>(); a.skip = skip;
-            if (cg) a.cg = *cg;
             for (int pair0 = 0; pair0 < npairs; pair0 += ppb) {
                 a.pair0 = pair0;
                 a.np = std::min(ppb, npairs - pair0);
@@ -713,7 +711,7 @@ static void run_matvec16(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                        int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt = 0,
-                       const int* skip = nullptr, const kspec::CgFuse* cg = nullptr);
+                       const int* skip = nullptr);
 
 // Irregular sites (sites.cu): A^T by scatter onto the whole grid, sigma^2 Sigma
 // on the whole grid by the FFT passes with whole-grid index lists and no
@@ -760,7 +758,7 @@ static void run_matvec_sites(kry_ctx* ctx, const kry_embed* e, const T* vin, int
 template <typename T>
 static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t ld_in, const double* scale, T* vout,
                        int64_t ld_out, int nvec, double tau2, double* dots, int nds, int mode, int vpt,
-                       const int* skip, const kspec::CgFuse* cg) {
+                       const int* skip) {
     KRY_REQUIRE(vpt == 0 || (vpt % 2 == 0 && nvec % vpt == 0 && nvec / vpt <= e->ntheta), KRY_EINVAL,
                 "vectors per theta must be even and divide the batch");
     if (ctx->sites.active) {
@@ -783,7 +781,7 @@ static void run_matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, int64_t l
             prof_record(ctx, ev0);
         }
         run_matvec16<T>(ctx, e, vin, ld_in, scale, vout, ld_out, nvec, tau2, dots, nds, mode, sb.as<Cx>(), ppb, vpt,
-                        skip, cg);
+                        skip);
         if (ctx->prof_on) {
             prof_record(ctx, ev1);
             ctx->prof_ev.push_back(ev0);
@@ -872,22 +870,6 @@ template void matvec_ex<float>(kry_ctx*, const kry_embed*, const float*, int64_t
                                double*, int, int, const int*);
 template void matvec_ex<double>(kry_ctx*, const kry_embed*, const double*, int64_t, const double*, double*, int64_t,
                                 int, double*, int, int, const int*);
-
-// True if FP32 CG on e with nvec right-hand sides can fuse its vector work
-// into the specialised passes (observation mask, length-specialised shape).
-bool matvec_cg_fusable(kry_ctx* ctx, const kry_embed* e, int nvec) {
-    if (ctx->sites.active || e->prec != KRY_F32 || !ctx->use_spec || !use16(e->M1, e->M2)) return false;
-    int G, C;
-    sched16(ctx, e->M1, e->M2, false, nvec, &G, &C);
-    return kspec::supported(e->M1, e->M2, G, C);
-}
-
-// FP32 matvec Q = K P with the CG work of `cg` fused into passes A and C
-// (requires matvec_cg_fusable).
-void matvec_cg(kry_ctx* ctx, const kry_embed* e, float* P, int64_t ld, float* Q, int nvec, double* dots, int nds,
-               int vpt, const int* skip, const kspec::CgFuse& cg) {
-    run_matvec<float>(ctx, e, P, ld, nullptr, Q, ld, nvec, e->cov.tau2, dots, nds, 0, vpt, skip, &cg);
-}
 
 template <typename T>
 void matvec(kry_ctx* ctx, const kry_embed* e, const T* vin, T* vout, int nvec, int64_t ld, double) {

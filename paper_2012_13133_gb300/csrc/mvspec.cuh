@@ -40,36 +40,15 @@ constexpr size_t smem_bytes(int B, int NT) {
     return (size_t)((1 << B) + ((1 << B) >> pad_shift(1 << B, NT))) * NT * sizeof(float2);
 }
 
-// CG vector work fused into the passes (a plain matvec leaves every pointer
-// NULL).  Pass A, for each column v that is not done: x_v += alpha_v p_v in
-// double-float (the update pending from the previous iteration; skipped when
-// alpha_v = 0) and p_v = r_v + beta_v p_v, written back in place, and the new
-// p_v is what it scatters.  Pass C: the last block of each pair to finish (a
-// ticket per pair, taken after its partials are stored) sums the pair's p^T q
-// partials in a fixed order and writes alpha_v = gamma_v / p^T q, then resets
-// the ticket.  No block waits for another.
-struct CgFuse {
-    float* P;                  // directions: the matvec input, updated in place by pass A
-    const float* R;            // residuals
-    float* Xh;                 // solution, double-float high words
-    float* Xl;                 // ... and low words
-    const double* alpha;       // pending step of each column (pass A)
-    const double* beta;        // direction coefficient of each column (pass A)
-    const int* done;           // finished columns (left untouched)
-    unsigned* cnt;             // pass C: tickets, one per complex pair, zero between calls
-    const double* gam;         // pass C: r^T r of each column
-    double* alpha_out;         // pass C: the new step of each column
-};
-
 // ---------------------------------------------------------------- pass A
 // Scatter the observed values of NT rows (two real vectors as re/im) into
 // zeroed rows, forward row FFT (half-input first stage: columns >= n2 are
 // zero), store the n1 x M2 slab in column tiles of width C (C <= L/16).
-template <int B, int NT, bool FUSE>
+template <int B, int NT>
 __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
     ks_pass_a(const float* __restrict__ vin, int64_t ld, const double* __restrict__ scale, int nvec, int pair0,
               const int* __restrict__ rowptr, const int* __restrict__ colidx, int n1, int n2, int C, int logC,
-              float2* __restrict__ slab, const float4* __restrict__ twt, const int* __restrict__ skip, CgFuse cg) {
+              float2* __restrict__ slab, const float4* __restrict__ twt, const int* __restrict__ skip) {
     using P = Plan<B>;
     constexpr int L = P::L, LT = P::LT, PS = pad_shift(L, NT);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,35 +73,8 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
         const float sa = scale ? (float)scale[va] : 1.f;
         const float sbv = (scale && has_b) ? (float)scale[vb] : 1.f;
         const int q0 = rowptr[row] + t, q1 = rowptr[row + 1];
-        if constexpr (FUSE) {
-            // the CG vector update of this row's observed cells, column by column
-            for (int c = 0; c < (has_b ? 2 : 1); ++c) {
-                const int v = c ? vb : va;
-                if (cg.done[v]) continue;
-                const double a = cg.alpha[v];
-                const float bf = (float)cg.beta[v];
-                float ahi, alo;
-                kry::df_split(a, ahi, alo);
-                float* P = cg.P + (int64_t)v * ld;
-                const float* R = cg.R + (int64_t)v * ld;
-                float* Xh = cg.Xh + (int64_t)v * ld;
-                float* Xl = cg.Xl + (int64_t)v * ld;
-#pragma unroll 2
-                for (int q = q0; q < q1; q += LT) {
-                    const float pold = P[q];
-                    if (a != 0.0) {
-                        float h = Xh[q], l = Xl[q];
-                        kry::df_axpy(h, l, ahi, alo, pold);
-                        Xh[q] = h;
-                        Xl[q] = l;
-                    }
-                    P[q] = R[q] + bf * pold;
-                }
-            }
-        }
-        // the fused path reads the directions it has just written through the same pointer
-        const float* pa = (FUSE ? cg.P : vin) + (int64_t)va * ld;
-        const float* pb = (FUSE ? cg.P : vin) + (int64_t)vb * ld;
+        const float* pa = vin + (int64_t)va * ld;
+        const float* pb = vin + (int64_t)vb * ld;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int q = q0 + i * LT;
@@ -235,7 +187,7 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
               const double* __restrict__ scale, float* __restrict__ vout, int64_t ld_out, int nvec, int pair0,
               const int* __restrict__ rowptr, const int* __restrict__ colidx, int n1, int n2, int C, int logC,
               double tau2, double* __restrict__ dots, int ndot_stride, const float4* __restrict__ twt,
-              const double* __restrict__ tau2v, int vpt, const int* __restrict__ skip, CgFuse cg) {
+              const double* __restrict__ tau2v, int vpt, const int* __restrict__ skip) {
     using P = Plan<B>;
     constexpr int L = P::L, LT = P::LT, PS = pad_shift(L, NT);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -327,41 +279,6 @@ __global__ void __launch_bounds__(tpb(B, NT), minb(B, NT))
             dots[(int64_t)va * ndot_stride + blockIdx.x] = s0;
             if (has_b) dots[(int64_t)vb * ndot_stride + blockIdx.x] = s1;
         }
-        if (cg.cnt != nullptr) {
-            // CG step of the pair from its p^T q partials, by the pair's last block
-            __shared__ unsigned ticket;
-            if (threadIdx.x == 0) {
-                __threadfence();   // this block's partials before its ticket
-                ticket = atomicAdd(&cg.cnt[pair], 1u);
-            }
-            __syncthreads();
-            if (ticket == gridDim.x - 1) {
-                __threadfence();
-                double* rs = reinterpret_cast<double*>(smem_raw);   // the FFT buffer is free now
-                const int bd = blockDim.x;
-                double ta = 0.0, tb = 0.0;
-                for (int b = threadIdx.x; b < (int)gridDim.x; b += bd) {
-                    ta += __ldcg(dots + (int64_t)va * ndot_stride + b);
-                    if (has_b) tb += __ldcg(dots + (int64_t)vb * ndot_stride + b);
-                }
-                rs[threadIdx.x] = ta;
-                rs[bd + threadIdx.x] = tb;
-                __syncthreads();
-                for (int o = bd >> 1; o > 0; o >>= 1) {   // fixed-order tree (bd is a power of two)
-                    if ((int)threadIdx.x < o) {
-                        rs[threadIdx.x] += rs[threadIdx.x + o];
-                        rs[bd + threadIdx.x] += rs[bd + threadIdx.x + o];
-                    }
-                    __syncthreads();
-                }
-                if (threadIdx.x == 0) {
-                    const double pa = rs[0], pb = rs[bd];
-                    if (!cg.done[va]) cg.alpha_out[va] = (pa > 0.0) ? cg.gam[va] / pa : 0.0;
-                    if (has_b && !cg.done[vb]) cg.alpha_out[vb] = (pb > 0.0) ? cg.gam[vb] / pb : 0.0;
-                    cg.cnt[pair] = 0u;
-                }
-            }
-        }
     }
 }
 
@@ -389,7 +306,6 @@ struct SpecArgs {
     int nds;
     const float4* twt;
     const int* skip;
-    CgFuse cg;   // fused CG vector work (all NULL: plain matvec)
 };
 
 // True if the specialised kernels cover this shape: 64 <= M <= 8192, rows and

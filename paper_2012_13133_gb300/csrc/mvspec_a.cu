@@ -34,11 +34,11 @@ struct RunA {
     cudaStream_t st;
     template <int B, int NT>
     bool run() const {
-        auto k = a.cg.P ? ks_pass_a<B, NT, true> : ks_pass_a<B, NT, false>;
+        auto k = ks_pass_a<B, NT>;
         KRY_ALLOW_MAX_SMEM(k);
         dim3 grid((a.n1 + NT - 1) / NT, a.np);
         launch_pdl(k, grid, dim3(tpb(B, NT)), smem_bytes(B, NT), st, a.vin, a.ld_in, a.scale, a.nvec, a.pair0,
-                   a.rowptr, a.colidx, a.n1, a.n2, a.C, a.logC, a.slab, a.twt, a.skip, a.cg);
+                   a.rowptr, a.colidx, a.n1, a.n2, a.C, a.logC, a.slab, a.twt, a.skip);
         return true;
     }
 };

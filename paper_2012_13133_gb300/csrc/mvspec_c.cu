@@ -16,7 +16,7 @@ struct RunC {
         dim3 grid((a.n1 + NT - 1) / NT, a.np);
         launch_pdl(k, grid, dim3(tpb(B, NT)), smem_bytes(B, NT), st, a.slab, a.vin, a.ld_in, a.scale, a.vout, a.ld_out, a.nvec,
                                                        a.pair0, a.rowptr, a.colidx, a.n1, a.n2, a.C, a.logC, a.tau2,
-                                                       a.dots, a.nds, a.twt, a.tau2v, a.vpt, a.skip, a.cg);
+                                                       a.dots, a.nds, a.twt, a.tau2v, a.vpt, a.skip);
         return true;
     }
 };

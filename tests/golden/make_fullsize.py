@@ -14,8 +14,10 @@ What the oracle computes, per workload (all FP64, the paper's definitions):
   workload's Rademacher probes and step count, with the Lanczos basis fully
   reorthogonalised (the exact Gauss rule; stochastic trace alternative of
   Sec. 3.3);
-* K^-1 [y, X] by CG to a relative residual of ``--tol`` (Sec. 3), the GLS
-  beta and the marginal log-likelihood;
+* K^-1 [y, X] by CG to a relative residual of ``--tol`` (Sec. 3; with
+  ``--precond`` preconditioned by the torus inverse, which reaches the same
+  solution in far fewer iterations on clustered gaps), the GLS beta and the
+  marginal log-likelihood;
 * kriging means X_t beta + sigma^2 Sigma_{t,o} w, w = K^-1 (y - X beta)
   (Eq. act_xhat plus the trend), at every unobserved cell (grid1024) or at a
   seeded sample of them (large4096).
@@ -23,7 +25,7 @@ What the oracle computes, per workload (all FP64, the paper's definitions):
 Usage (from the repository root; hours for large4096 on a few cores):
     python tests/golden/make_fullsize.py grid1024  [--procs 4] [--threads 2]
     python tests/golden/make_fullsize.py search512 [--procs 4] [--threads 2]
-    python tests/golden/make_fullsize.py large4096 [--procs 4] [--threads 2]
+    python tests/golden/make_fullsize.py large4096 --tol 1e-8 --precond [--procs 4] [--threads 2]
 """
 from __future__ import annotations
 
@@ -94,14 +96,14 @@ def _probe(args):
 
 
 def _cg(args):
-    """CG solve of one right-hand side."""
-    j, b, tol = args
-    from oracle import kryoracle as O
-    x, it = O.cg(_P.matvec, b, tol)
+    """CG solve of one right-hand side (preconditioned by the torus inverse if asked: the same
+    solution in fewer iterations)."""
+    j, b, tol, precond = args
+    x, it = _P.solve(b, tol, precond=precond)
     return j, x, it
 
 
-def run_problem(name, cov_index, y, X, tol, procs, threads, log):
+def run_problem(name, cov_index, y, X, tol, procs, threads, log, precond=False):
     """Per-probe SLQ values, the CG solve of [y, X], GLS beta and loglik for one setting."""
     from oracle import kryoracle as O
     from paper_2012_13133_gb300 import inputs as I
@@ -110,7 +112,8 @@ def run_problem(name, cov_index, y, X, tol, procs, threads, log):
     t0 = time.time()
     B = np.column_stack([y, X])
     with ctx.Pool(min(procs, B.shape[1]), initializer=_init, initargs=(name, threads, cov_index)) as pool:
-        sols = sorted(pool.map(_cg, [(j, B[:, j], tol) for j in range(B.shape[1])]), key=lambda r: r[0])
+        sols = sorted(pool.map(_cg, [(j, B[:, j], tol, precond) for j in range(B.shape[1])]),
+                      key=lambda r: r[0])
     Z = np.stack([s[1] for s in sols], axis=1)
     iters = [s[2] for s in sols]
     log(f"  CG {iters} iterations, {time.time() - t0:.0f} s")
@@ -134,6 +137,8 @@ def main():
     ap.add_argument("--procs", type=int, default=4)
     ap.add_argument("--threads", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--precond", action="store_true",
+                    help="CG preconditioned by the torus inverse (same solution, fewer iterations)")
     args = ap.parse_args()
 
     from oracle import kryoracle as O
@@ -147,12 +152,12 @@ def main():
 
     mask, X, y, M1, M2 = oracle_data(w)
     log(f"{w.name}: p = {y.size}, sampling torus {M1} x {M2}")
-    out = dict(tol=args.tol, sample_M=np.array([M1, M2]), y_sum=float(y.sum()), y_norm=float(np.linalg.norm(y)),
-               p=y.size)
+    out = dict(tol=args.tol, precond=int(args.precond), sample_M=np.array([M1, M2]), y_sum=float(y.sum()),
+               y_norm=float(np.linalg.norm(y)), p=y.size)
     S1, S2 = I.cell_centres(w.n1, w.n2)
 
     if w.name in ("grid1024", "large4096"):
-        r = run_problem(w.name, -1, y, X, args.tol, args.procs, args.threads, log)
+        r = run_problem(w.name, -1, y, X, args.tol, args.procs, args.threads, log, args.precond)
         Z = r.pop("Z")
         out.update(r)
         wts = Z[:, 0] - Z[:, 1:] @ r["beta"]
