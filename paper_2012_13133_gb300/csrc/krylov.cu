@@ -895,11 +895,13 @@ __global__ void k_set(double* x, int64_t n, double v) {
 
 // FP64 true residual R = B - K X; returns per-column (||R||, ||B||) on the host.
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
-                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt) {
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt,
+                          const int* skip) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
-    // KX = K X (FP64 matvec); X has leading dimension ldx
-    matvec_ex<double>(ctx, e, X, ldx, nullptr, KX, p, nrhs, nullptr, 0, vpt);
+    // KX = K X (FP64 matvec); X has leading dimension ldx.  Columns flagged in
+    // skip (pairs of them) are not transformed: their residual norms are stale.
+    matvec_ex<double>(ctx, e, X, ldx, nullptr, KX, p, nrhs, nullptr, 0, vpt, skip);
     ctx->red.ensure((size_t)nrhs * RED_BLOCKS * 2 * sizeof(double) + (size_t)nrhs * 2 * sizeof(double));
     double* part = ctx->red.as<double>();
     double* fin = part + (size_t)nrhs * RED_BLOCKS * 2;
@@ -1116,22 +1118,21 @@ __global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restric
         X[(int64_t)k * ldx + i] = (double)Xh[(int64_t)k * p + i] + (double)Xl[(int64_t)k * p + i];
 }
 
-// Residual replacement of the columns still running: R = (float) R64,
+// Residual replacement of the columns that ask for one: R = (float) R64,
 // rr = rr_ref = ||R64||^2 and, without a preconditioner, gamma = rr (P is
 // kept); done when ||R64|| <= rtol ||B|| or the iteration budget is spent (a
 // non-finite residual also ends the column; the caller reports it).
 __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
                               const double* __restrict__ norms, RcgState S, int maxit, int precond) {
     const int k = blockIdx.y;
-    if (S.done[k]) return;
+    if (S.done[k] || !S.want[k]) return;   // only the columns that asked (the others' norms are stale)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
         R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // (want is cleared by k_count_done, after every block)
         const double rn = norms[2 * k];
         if (!precond) S.gam[k] = rn * rn;
         S.rr[k] = rn * rn;
         S.rr_ref[k] = rn * rn;
-        S.want[k] = 0;
         if (rn * rn <= S.thr2[k] || S.iters[k] >= maxit || !(rn == rn)) S.done[k] = 1;
     }
 }
@@ -1140,19 +1141,31 @@ __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict_
 // of the preconditioner matvec's partials.
 __global__ void k_rcg_regamma(RcgState S, const double* __restrict__ part_rz, int nrz) {
     const int k = blockIdx.x;
-    if (S.done[k]) return;
+    if (S.done[k] || !S.want[k]) return;
     const double g = block_sum(part_rz + (int64_t)k * nrz, nrz);
     if (threadIdx.x == 0) S.gam[k] = g;
 }
 
+// Ends a replacement round: counts the finished columns and clears the requests.
 __global__ void k_count_done(RcgState S, int nrhs) {
     int d = 0;
-    for (int k = 0; k < nrhs; ++k) d += S.done[k];
+    for (int k = 0; k < nrhs; ++k) {
+        d += S.done[k];
+        S.want[k] = 0;
+    }
     *S.ndone = d;
 }
 
 static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int64_t ldb, const double* X,
-                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt);
+                          int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt,
+                          const int* skip = nullptr);
+
+// Skip flags of a replacement round: the columns that are done or do not ask
+// for a replacement.
+__global__ void k_rcg_select(RcgState S, int nrhs, int* __restrict__ skip) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nrhs) skip[k] = (S.done[k] || !S.want[k]) ? 1 : 0;
+}
 
 // Returns the largest per-column iteration count.  pre: preconditioner
 // embedding (NULL: plain CG).
@@ -1179,7 +1192,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     double* part_pq = ctx->work[10].as<double>();        // matvec partials (p^T K p)
     double* part_rr = part_pq + (size_t)nrhs * nblkC;     // start / update partials (r^T r)
     double* part_rz = pre ? part_rr + (size_t)nrhs * nbc : nullptr;   // preconditioner partials (r^T z)
-    ctx->work[11].ensure((size_t)nrhs * (6 * sizeof(double) + 3 * sizeof(int)) + 64);
+    ctx->work[11].ensure((size_t)nrhs * (6 * sizeof(double) + 4 * sizeof(int)) + 64);
     char* sb = ctx->work[11].as<char>();
     RcgState S;
     S.gam = reinterpret_cast<double*>(sb);
@@ -1192,6 +1205,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
     S.done = S.want + nrhs;
     S.iters = S.done + nrhs;
     S.ndone = S.iters + nrhs;
+    int* sel = S.ndone + 1;   // skip flags of a replacement round
     ctx->tolbuf.ensure(nrhs * sizeof(double));
     std::vector<double> tol_h(nrhs, rtol);
     KRY_CUDA(cudaMemcpyAsync(ctx->tolbuf.p, tol_h.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1253,17 +1267,20 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
         KRY_CUDA(cudaMemcpyAsync(hflag, S.want, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
         KRY_CUDA(cudaStreamSynchronize(st));
         if (block.exec) block.harvest();
-        bool any = false;
-        for (int k = 0; k < nrhs; ++k) any = any || hflag[k] != 0;
-        if (any) {
-            // residual replacement for every column still running
+        int nwant = 0;
+        for (int k = 0; k < nrhs; ++k) nwant += hflag[k] != 0;
+        if (nwant > 0) {
+            // residual replacement for the columns that ask for one: the FP64
+            // matvec transforms only their pairs
+            k_rcg_select<<<1, tbeta, 0, st>>>(S, nrhs, sel);
+            KRY_CHECK_LAUNCH();
             to_f64();
-            true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt);
+            true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt, sel);
             double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
             k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit, pre ? 1 : 0);
             KRY_CHECK_LAUNCH();
             if (pre) {   // z = M^-1 r and gamma = r^T z for the replaced r
-                matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, S.done);
+                matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, sel);
                 k_rcg_regamma<<<nrhs, FIN_THREADS, 0, st>>>(S, part_rz, nblkC);
                 KRY_CHECK_LAUNCH();
             }
@@ -1272,12 +1289,13 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             KRY_CUDA(cudaMemcpyAsync(hflag, S.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
             KRY_CUDA(cudaStreamSynchronize(st));
             if (*hflag >= nrhs) {
-                *fresh = true;
+                // the last residuals are every column's only if every column took part
+                *fresh = nwant == nrhs;
                 break;
             }
         }
     }
-    if (!*fresh) to_f64();   // after a converged replacement X already holds this solution
+    to_f64();   // X, after the loop or its last replacement round (idempotent)
     std::vector<int> its(nrhs);
     KRY_CUDA(cudaMemcpyAsync(its.data(), S.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
     KRY_CUDA(cudaStreamSynchronize(st));

@@ -188,7 +188,11 @@ __global__ void k_site_scatter(const int* __restrict__ cellptr, const int* __res
                                const double* __restrict__ scale, int64_t N, T* __restrict__ grid,
                                const int* __restrict__ skip) {
     const int v = blockIdx.y;
-    if (skip && skip[v]) return;
+    // skipped as the FFT passes skip: only when both columns of the complex
+    // pair are (a skipped column's grid still enters its partner's transform,
+    // and rounding there depends on it)
+    const int w = v ^ 1;
+    if (skip && skip[v] && (w >= (int)gridDim.y || skip[w])) return;
     const T s = scale ? (T)scale[v] : (T)1;
     const T* x = vin + (int64_t)v * ld_in;
     T* g = grid + (int64_t)v * N;

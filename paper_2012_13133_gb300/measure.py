@@ -104,6 +104,24 @@ def main():
         ctx.profile_loglik(y, X, thetas[:2], opts)                       # warm-up
         batch, tb = timed(lambda: ctx.profile_loglik(y, X, thetas, opts))
         singles, ts = timed(lambda: [ctx.profile_loglik(y, X, [t], opts) for t in thetas])
+        # FP32 matvec work of each form (one more run of each, CUDA events per matvec)
+        work = {}
+        for name, fn in (("batched", lambda: ctx.profile_loglik(y, X, thetas, opts)),
+                         ("one_at_a_time", lambda: [ctx.profile_loglik(y, X, [t], opts) for t in thetas])):
+            ctx.profile_enable(True)
+            fn()
+            pr = ctx.profile_read(kry.KRY_F32)
+            ctx.profile_enable(False)
+            work[name] = {"matvec_calls": pr["calls"], "real_vectors": pr["vectors"], "matvec_ms": pr["ms"]}
+        out["fp32_matvec_work"] = work
+        # CG iterations of each setting alone (4 right-hand sides [y, X])
+        B = torch.cat([y.reshape(1, -1), X], 0).contiguous()
+        its = []
+        for t in thetas:
+            emb = ctx.embed(t, kry.KRY_F32)
+            its.append(ctx.solve(emb, B, rtol=w.cg_tol, maxit=30000)[1])
+            emb.free()
+        out["cg_iterations_per_setting"] = its
         diff = max(abs(batch["loglik"][k] - s["loglik"][0]) / abs(s["loglik"][0]) for k, s in enumerate(singles))
         best = int(np.argmax(batch["loglik"]))
         out.update({"settings": len(thetas), "probes": w.nprobe, "lanczos_steps": w.nsteps,

@@ -6,10 +6,12 @@ log-uniformly, masks with 10-90% missing cells (half in circular gaps like
 cloud cover, half uniform), Matern nu in {1/2, 3/2}, random range and nugget,
 and GP data drawn by the library's circulant-embedding sampler.  The stream
 is replayed against a one-slot server (one request at a time) and against a
-multi-slot server at the same arrival times; each prints p50/p99 latency and
-requests/s.
+multi-slot server: saturated (every request queued at once: the capacity of
+each form) and at Poisson arrivals of a given multiple of the one-slot
+throughput; each reports p50/p99 latency and requests/s.
 
   python -m paper_2012_13133_gb300.serve --n-requests 200 --slots 8
+  python -m paper_2012_13133_gb300.serve --n-requests 2000 --precond 1 --rates 0.5,1,2 --sweep-requests 500
 """
 from __future__ import annotations
 
@@ -30,7 +32,20 @@ if ROOT not in sys.path:
 from paper_2012_13133_gb300 import inputs as I  # noqa: E402
 
 
-def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000, reorth=1):
+def _mask_of(sp):
+    return I.mask_mixed(sp["n"], sp["n"], sp["frac_missing"], sp["mask_seed"])
+
+
+def make_masks(specs, procs):
+    """The request masks (host work), in a process pool started with spawn before any GPU use."""
+    if procs <= 1:
+        return [_mask_of(sp) for sp in specs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_mask_of, specs, chunksize=4)
+
+
+def build_requests(specs, masks, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000, reorth=1, precond=0):
     """Materialise request specs (inputs.serve_requests) into host arrays,
     drawing each data set with the GPU sampler."""
     import torch
@@ -39,9 +54,8 @@ def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000,
     ctx = kry.Context(device)
     dev = torch.device("cuda", device)
     out = []
-    for sp in specs:
+    for sp, mask in zip(specs, masks):
         n = sp["n"]
-        mask = I.mask_mixed(n, n, sp["frac_missing"], sp["mask_seed"])
         cov = I.Cov(1.0, sp["range"], sp["nu"], sp["tau2"])
         p = ctx.set_mask(torch.from_numpy(mask.astype(np.uint8)).to(dev))
         M1, M2, _ = ctx.sample_size(cov)
@@ -53,7 +67,7 @@ def build_requests(specs, device=0, nprobe=16, nsteps=50, rtol=1e-6, maxit=5000,
         req = dict(spec=sp, kind=kry.KRY_REQ_LOGLIK if sp["kind"] == "loglik" else kry.KRY_REQ_KRIGE,
                    mask=mask, y=y, X=np.ascontiguousarray(X.T), cov=cov,
                    opts=kry.Opts(prec=kry.KRY_F32, nprobe=nprobe, nsteps=nsteps, seed=sp["id"], rtol=rtol,
-                                 maxit=maxit, reorth=reorth))
+                                 maxit=maxit, reorth=reorth, precond=precond))
         if sp["kind"] == "krige":
             cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
             req["target_cells"] = cells
@@ -105,43 +119,61 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--rate-factor", type=float, default=1.5,
                     help="arrival rate as a multiple of the measured one-slot throughput")
+    ap.add_argument("--rates", default="",
+                    help="comma-separated extra rate factors replayed on the multi-slot server")
+    ap.add_argument("--sweep-requests", type=int, default=0,
+                    help="requests of the stream replayed at each extra rate (0: all)")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=2048)
     ap.add_argument("--budget-gb", type=float, default=96.0)
     ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--maxit", type=int, default=5000)
+    ap.add_argument("--precond", type=int, default=0, help="kry_opts.precond of every request")
+    ap.add_argument("--mask-procs", type=int, default=8)
     args = ap.parse_args()
 
     w = I.WORKLOADS["serve"]
     specs = I.serve_requests(args.n_requests, args.seed, args.side_min, args.side_max, rate=1.0)
     t = time.perf_counter()
-    reqs = build_requests(specs)
+    masks = make_masks(specs, args.mask_procs)
+    reqs = build_requests(specs, masks, maxit=args.maxit, precond=args.precond)
     prep_s = time.perf_counter() - t
     budget = int(args.budget_gb * (1 << 30))
+    out = {"metric": "serving p50/p99 latency and requests/s", "workload": w.name, "n_requests": len(reqs),
+           "slots": args.slots, "precond": args.precond, "prep_s": prep_s}
 
-    # one request at a time: measure service throughput with all requests queued at t = 0
+    # capacity: every request queued at t = 0, on one slot (one request at a time) and on all slots
     one = kry.Server(0, 1, budget)
     res1, wall1 = replay(one, reqs, np.zeros(len(reqs)))
     one.close()
-    mu1 = len(reqs) / wall1
-    rate = args.rate_factor * mu1
-    gaps = np.random.default_rng(args.seed + 1).exponential(1.0 / rate, size=len(reqs))
-    arrivals = np.cumsum(gaps) - gaps[0]
-
-    single = kry.Server(0, 1, budget)
-    res_s, wall_s = replay(single, reqs, arrivals)
-    single.close()
+    out["one_slot_saturated"] = summarise(res1, wall1)
     multi = kry.Server(0, args.slots, budget)
-    res_m, wall_m = replay(multi, reqs, arrivals)
+    resm, wallm = replay(multi, reqs, np.zeros(len(reqs)))
     multi.close()
+    out[f"{args.slots}_slots_saturated"] = summarise(resm, wallm)
+    mu1 = len(reqs) / wall1
+    out["served_over_one_at_a_time"] = (len(reqs) / wallm) / mu1
 
-    same = max(abs(a["loglik"] - b["loglik"]) / max(1.0, abs(a["loglik"]))
-               for a, b, r in zip(res_s, res_m, reqs) if r["kind"] == kry.KRY_REQ_LOGLIK) if any(
-        r["kind"] == kry.KRY_REQ_LOGLIK for r in reqs) else 0.0
-    print(json.dumps({"metric": "serving p50/p99 latency and requests/s", "workload": w.name,
-                      "n_requests": len(reqs), "arrival_rate_per_s": rate, "prep_s": prep_s,
-                      "one_slot_saturated": summarise(res1, wall1),
-                      "one_slot": summarise(res_s, wall_s), f"{args.slots}_slots": summarise(res_m, wall_m),
-                      "max_rel_loglik_diff_single_vs_mixed": same}))
+    def at_rate(factor, server_slots, n):
+        rate = factor * mu1
+        gaps = np.random.default_rng(args.seed + 1).exponential(1.0 / rate, size=n)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        srv = kry.Server(0, server_slots, budget)
+        res, wall = replay(srv, reqs[:n], arrivals)
+        srv.close()
+        return res, dict(summarise(res, wall), rate_factor=factor, arrival_rate_per_s=rate)
+
+    res_s, out["one_slot_at_rate"] = at_rate(args.rate_factor, 1, len(reqs))
+    res_m, out[f"{args.slots}_slots_at_rate"] = at_rate(args.rate_factor, args.slots, len(reqs))
+    sweep = []
+    for f in [float(x) for x in args.rates.split(",") if x.strip()]:
+        n = args.sweep_requests or len(reqs)
+        sweep.append(at_rate(f, args.slots, n)[1])
+    out["rate_sweep"] = sweep
+    lik = [(a, b) for a, b, r in zip(res_s, res_m, reqs) if r["kind"] == kry.KRY_REQ_LOGLIK]
+    out["max_rel_loglik_diff_single_vs_mixed"] = max(
+        (abs(a["loglik"] - b["loglik"]) / max(1.0, abs(a["loglik"])) for a, b in lik), default=0.0)
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

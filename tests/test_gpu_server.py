@@ -31,7 +31,8 @@ def specs():
 
 @pytest.fixture(scope="module")
 def reqs():
-    return serve.build_requests(specs(), nprobe=8, nsteps=30, rtol=1e-8, maxit=5000)
+    sp = specs()
+    return serve.build_requests(sp, serve.make_masks(sp, 1), nprobe=8, nsteps=30, rtol=1e-8, maxit=5000)
 
 
 def run(server, reqs):
