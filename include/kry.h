@@ -94,8 +94,11 @@ typedef struct {
  * clustered (cloud-like masks), not under scattered missing cells; it applies
  * to FP32 solves of one covariance setting with tau2 > 0 on an observation
  * mask, and is ignored otherwise (with irregular sites, close sites make
- * A (S + tau2 I)^-1 A^T nearly singular).  The result does not depend on it
- * beyond the CG tolerance. */
+ * A (S + tau2 I)^-1 A^T nearly singular).  2 = automatic: preconditioned when
+ * at least 0.4 of the observed cells have all four grid neighbours observed
+ * (kry_mask_interior; on 512^2 masks that is where the preconditioned solve
+ * was the faster one).  The result does not depend on it beyond the CG
+ * tolerance. */
 typedef struct {
     kry_prec prec;
     int32_t nprobe, nsteps;
@@ -121,6 +124,13 @@ const char* kry_last_error(const kry_ctx* ctx);
  * lists on the device and returns the number of observed cells p in *p_out.
  * Requires 4 <= n1, n2 <= 4096 and p >= 1.  Synchronises the stream. */
 kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_dev, int64_t* p_out);
+
+/* Share of the observed cells of the last kry_set_mask whose four grid
+ * neighbours are observed too (a neighbour beyond the grid edge counts as
+ * observed): near 1 for clustered gaps, about (1 - missing share)^4 for
+ * scattered holes; 0 without a mask or with sites.  It decides
+ * kry_opts.precond = 2.  (No counterpart in the paper.) */
+kry_status kry_mask_interior(kry_ctx* ctx, double* interior);
 
 /* Irregular observation sites (Sec. 2: y = X beta + A x + eps with A the
  * p x n mapping matrix of Wendland weights).  sites_dev holds nsite (x1, x2)

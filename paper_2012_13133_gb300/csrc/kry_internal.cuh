@@ -123,6 +123,10 @@ struct kry_ctx {
     int n1 = 0, n2 = 0;
     double dx1 = 0, dx2 = 0;
     int64_t p = 0;
+    // share of the observed cells whose four grid neighbours are observed too
+    // (cells beyond the grid edge count as observed): near 1 for clustered
+    // gaps, low for scattered holes; kry_opts.precond = 2 reads it
+    double interior = 0.0;
     DevBuf rowptr;   // int32 [n1 + 1]: first observed index of each row
     DevBuf colidx;   // int32 [p]: column of each observed cell
     DevBuf cellidx;  // int32 [p]: row-major cell index of each observed cell

@@ -1118,14 +1118,15 @@ __global__ void k_df_to_f64(const float* __restrict__ Xh, const float* __restric
         X[(int64_t)k * ldx + i] = (double)Xh[(int64_t)k * p + i] + (double)Xl[(int64_t)k * p + i];
 }
 
-// Residual replacement of the columns that ask for one: R = (float) R64,
+// Residual replacement of the running columns of the round: R = (float) R64,
 // rr = rr_ref = ||R64||^2 and, without a preconditioner, gamma = rr (P is
 // kept); done when ||R64|| <= rtol ||B|| or the iteration budget is spent (a
 // non-finite residual also ends the column; the caller reports it).
 __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict__ R, int64_t p,
-                              const double* __restrict__ norms, RcgState S, int maxit, int precond) {
+                              const double* __restrict__ norms, RcgState S, int maxit, int precond,
+                              const int* __restrict__ sel) {
     const int k = blockIdx.y;
-    if (S.done[k] || !S.want[k]) return;   // only the columns that asked (the others' norms are stale)
+    if (S.done[k] || sel[k]) return;   // only the columns of the round (the others' norms are stale)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x)
         R[(int64_t)k * p + i] = (float)R64[(int64_t)k * p + i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // (want is cleared by k_count_done, after every block)
@@ -1139,9 +1140,9 @@ __global__ void k_rcg_replace(const double* __restrict__ R64, float* __restrict_
 
 // gamma = r^T z after a replacement (preconditioned runs): the fixed-order sum
 // of the preconditioner matvec's partials.
-__global__ void k_rcg_regamma(RcgState S, const double* __restrict__ part_rz, int nrz) {
+__global__ void k_rcg_regamma(RcgState S, const double* __restrict__ part_rz, int nrz, const int* __restrict__ sel) {
     const int k = blockIdx.x;
-    if (S.done[k] || !S.want[k]) return;
+    if (S.done[k] || sel[k]) return;
     const double g = block_sum(part_rz + (int64_t)k * nrz, nrz);
     if (threadIdx.x == 0) S.gam[k] = g;
 }
@@ -1160,11 +1161,12 @@ static void true_residual(kry_ctx* ctx, const kry_embed* e, const double* B, int
                           int64_t ldx, int nrhs, double* R, double* KX, std::vector<double>& nrm, int vpt,
                           const int* skip = nullptr);
 
-// Skip flags of a replacement round: the columns that are done or do not ask
-// for a replacement.
-__global__ void k_rcg_select(RcgState S, int nrhs, int* __restrict__ skip) {
+// Skip flags of a replacement round: with `all`, no column is skipped (every
+// running column is replaced, and the FP64 residual covers the finished ones
+// too); otherwise the columns that are done or do not ask for a replacement.
+__global__ void k_rcg_select(RcgState S, int nrhs, int* __restrict__ skip, int all) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nrhs) skip[k] = (S.done[k] || !S.want[k]) ? 1 : 0;
+    if (k < nrhs) skip[k] = (!all && (S.done[k] || !S.want[k])) ? 1 : 0;
 }
 
 // Returns the largest per-column iteration count.  pre: preconditioner
@@ -1270,18 +1272,21 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
         int nwant = 0;
         for (int k = 0; k < nrhs; ++k) nwant += hflag[k] != 0;
         if (nwant > 0) {
-            // residual replacement for the columns that ask for one: the FP64
-            // matvec transforms only their pairs
-            k_rcg_select<<<1, tbeta, 0, st>>>(S, nrhs, sel);
+            // Residual replacement.  A few right-hand sides (which converge
+            // together) are all replaced in one round; in larger batches only
+            // the columns that ask for it, and the FP64 matvec transforms only
+            // their pairs.
+            const int all = nrhs <= 8 ? 1 : 0;
+            k_rcg_select<<<1, tbeta, 0, st>>>(S, nrhs, sel, all);
             KRY_CHECK_LAUNCH();
             to_f64();
             true_residual(ctx, e, B, ldb, X, ldx, nrhs, R64, ctx->kxbuf.as<double>(), nrm, vpt, sel);
             double* dn = ctx->red.as<double>() + (size_t)nrhs * RED_BLOCKS * 2;   // device norms
-            k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit, pre ? 1 : 0);
+            k_rcg_replace<<<gc, 256, 0, st>>>(R64, R, p, dn, S, maxit, pre ? 1 : 0, sel);
             KRY_CHECK_LAUNCH();
             if (pre) {   // z = M^-1 r and gamma = r^T z for the replaced r
                 matvec_ex<float>(ctx, pre, R, p, nullptr, Z, p, nrhs, part_rz, nblkC, vpt, sel);
-                k_rcg_regamma<<<nrhs, FIN_THREADS, 0, st>>>(S, part_rz, nblkC);
+                k_rcg_regamma<<<nrhs, FIN_THREADS, 0, st>>>(S, part_rz, nblkC, sel);
                 KRY_CHECK_LAUNCH();
             }
             k_count_done<<<1, 1, 0, st>>>(S, nrhs);
@@ -1290,7 +1295,7 @@ static int cg_reliable(kry_ctx* ctx, const kry_embed* e, const double* B, int64_
             KRY_CUDA(cudaStreamSynchronize(st));
             if (*hflag >= nrhs) {
                 // the last residuals are every column's only if every column took part
-                *fresh = nwant == nrhs;
+                *fresh = all || nwant == nrhs;
                 break;
             }
         }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "kry_last_error": (C.c_char_p, [_P]),
     "kry_set_mask": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.POINTER(C.c_int64)]),
     "kry_set_sites": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.c_int64]),
+    "kry_mask_interior": (C.c_int, [_P, _DP]),
     "kry_embed_eigs": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.POINTER(_P), _DP]),
     "kry_embed_free": (None, [_P]),
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
@@ -182,7 +183,7 @@ class Opts:
     rtol: float = 1e-6
     maxit: int = 5000
     reorth: int = 0   # 1: partial reorthogonalisation of the Lanczos basis
-    precond: int = 0  # 1: CG preconditioned by the torus inverse (clustered gaps)
+    precond: int = 0  # 1: CG preconditioned by the torus inverse (clustered gaps); 2: automatic
 
     def c(self) -> kry_opts:
         return kry_opts(self.prec, self.nprobe, self.nsteps, self.seed, self.rtol, self.maxit, self.reorth,
@@ -253,6 +254,12 @@ class Context:
         self._check(_lib.kry_set_mask(self.h, C.byref(g), m, C.byref(p)))
         self.p, self.n1, self.n2 = int(p.value), n1, n2
         return self.p
+
+    def mask_interior(self) -> float:
+        """Share of the observed cells whose four grid neighbours are observed (kry_mask_interior)."""
+        v = C.c_double()
+        self._check(_lib.kry_mask_interior(self.h, C.byref(v)))
+        return v.value
 
     def set_sites(self, sites, n1, n2, dx1=None, dx2=None) -> int:
         """Irregular observation sites: sites is a torch float64 CUDA tensor (p, 2) of coordinates in the

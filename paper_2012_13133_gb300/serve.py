@@ -123,21 +123,30 @@ def main():
                     help="comma-separated extra rate factors replayed on the multi-slot server")
     ap.add_argument("--sweep-requests", type=int, default=0,
                     help="requests of the stream replayed at each extra rate (0: all)")
+    ap.add_argument("--at-rate-requests", type=int, default=0,
+                    help="requests of the stream replayed at --rate-factor on each server (0: all)")
     ap.add_argument("--side-min", type=int, default=128)
     ap.add_argument("--side-max", type=int, default=2048)
     ap.add_argument("--budget-gb", type=float, default=96.0)
     ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--maxit", type=int, default=5000)
-    ap.add_argument("--precond", type=int, default=0, help="kry_opts.precond of every request")
+    ap.add_argument("--precond", type=int, default=2,
+                    help="kry_opts.precond of every request (2: automatic, from the mask's interior share)")
     ap.add_argument("--mask-procs", type=int, default=8)
     args = ap.parse_args()
 
     w = I.WORKLOADS["serve"]
     specs = I.serve_requests(args.n_requests, args.seed, args.side_min, args.side_max, rate=1.0)
     t = time.perf_counter()
+
+    def note(msg):
+        print(f"[{time.perf_counter() - t:8.1f} s] {msg}", file=sys.stderr, flush=True)
+
     masks = make_masks(specs, args.mask_procs)
+    note(f"{len(masks)} masks")
     reqs = build_requests(specs, masks, maxit=args.maxit, precond=args.precond)
     prep_s = time.perf_counter() - t
+    note("requests built")
     budget = int(args.budget_gb * (1 << 30))
     out = {"metric": "serving p50/p99 latency and requests/s", "workload": w.name, "n_requests": len(reqs),
            "slots": args.slots, "precond": args.precond, "prep_s": prep_s}
@@ -147,10 +156,12 @@ def main():
     res1, wall1 = replay(one, reqs, np.zeros(len(reqs)))
     one.close()
     out["one_slot_saturated"] = summarise(res1, wall1)
+    note(f"one slot, saturated: {wall1:.1f} s")
     multi = kry.Server(0, args.slots, budget)
     resm, wallm = replay(multi, reqs, np.zeros(len(reqs)))
     multi.close()
     out[f"{args.slots}_slots_saturated"] = summarise(resm, wallm)
+    note(f"{args.slots} slots, saturated: {wallm:.1f} s")
     mu1 = len(reqs) / wall1
     out["served_over_one_at_a_time"] = (len(reqs) / wallm) / mu1
 
@@ -161,10 +172,12 @@ def main():
         srv = kry.Server(0, server_slots, budget)
         res, wall = replay(srv, reqs[:n], arrivals)
         srv.close()
+        note(f"{server_slots} slot(s) at {factor} x: {wall:.1f} s")
         return res, dict(summarise(res, wall), rate_factor=factor, arrival_rate_per_s=rate)
 
-    res_s, out["one_slot_at_rate"] = at_rate(args.rate_factor, 1, len(reqs))
-    res_m, out[f"{args.slots}_slots_at_rate"] = at_rate(args.rate_factor, args.slots, len(reqs))
+    n_at = args.at_rate_requests or len(reqs)
+    res_s, out["one_slot_at_rate"] = at_rate(args.rate_factor, 1, n_at)
+    res_m, out[f"{args.slots}_slots_at_rate"] = at_rate(args.rate_factor, args.slots, n_at)
     sweep = []
     for f in [float(x) for x in args.rates.split(",") if x.strip()]:
         n = args.sweep_requests or len(reqs)

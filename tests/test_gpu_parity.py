@@ -668,3 +668,29 @@ def test_precond_leaves_loglik_and_kriging_unchanged(ctx, sites):
     assert np.allclose(out[1]["beta"], out[0]["beta"], rtol=1e-4, atol=1e-6)
     m0, m1 = out[0]["mean_cells"].cpu().numpy(), out[1]["mean_cells"].cpu().numpy()
     assert np.linalg.norm(m1 - m0) / np.linalg.norm(m0) <= 1e-5
+
+
+def test_mask_interior_share_and_automatic_precond(ctx):
+    """The interior share that kry_opts.precond = 2 reads, against its definition on the host
+    (exact integer counts), and the automatic choice leaves the results as they are."""
+    n = 96
+    masks = [I.mask_circles(n, n, 0.3, 12), I.mask_uniform(n, n, 0.5, 13), np.ones((n, n), bool)]
+    for m in masks:
+        ctx.set_mask(torch.from_numpy(m.astype(np.uint8)).to(DEV))
+        pad = np.pad(m, 1, constant_values=True)
+        inner = m & pad[:-2, 1:-1] & pad[2:, 1:-1] & pad[1:-1, :-2] & pad[1:-1, 2:]
+        assert ctx.mask_interior() == inner.sum() / m.sum()
+    assert ctx.mask_interior() == 1.0   # the full mask, set last
+    cov = I.Cov(1.0, 0.1, 1.5, 0.05)
+    for m in masks[:2]:
+        p = ctx.set_mask(torch.from_numpy(m.astype(np.uint8)).to(DEV))
+        S1, S2 = I.cell_centres(n, n)
+        X = I.covariates(S1[m], S2[m])
+        y = X @ np.array([1.0, 0.5, -0.5]) + I.normals(p, 14)
+        yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
+        ll = []
+        for pre in (0, 2):
+            opts = kry.Opts(prec=kry.KRY_F32, nprobe=8, nsteps=30, seed=3, rtol=1e-7, maxit=20000, reorth=1,
+                            precond=pre)
+            ll.append(ctx.profile_loglik(yt, Xt, [cov], opts)["loglik"][0])
+        assert ll[1] == pytest.approx(ll[0], rel=1e-7)
