@@ -327,6 +327,20 @@ kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, in
                        double* alphas, double* betas, double* z2, double* psi2, double* pl, double* grad,
                        double* psi_dev);
 
+/* kry_genhybr in a chosen arithmetic.  prec = KRY_F64 is kry_genhybr itself.
+ * prec = KRY_F32 keeps the Krylov vectors u_i, v_i and Sigma v_i in FP32 and
+ * applies Sigma by the FP32 whole-grid embedding matvec, while every norm and
+ * inner product of Alg. 1 (alpha_i, beta_i, w^T Sigma w), the projected
+ * problem, ||z_k||^2, ||psi_k*||^2, pl and the gradient are accumulated and
+ * kept in FP64; x_dev and psi_dev are written in FP64 from the FP32 vectors.
+ * FP32 rounding perturbs the bidiagonal at the 1e-6 level and the estimate
+ * and pl accordingly.  Library scratch: (2k + 6) n1 n2 floats (FP32) or
+ * doubles (FP64).  Arguments, outputs and errors as for kry_genhybr, plus
+ * KRY_EINVAL for another prec.  Synchronises the stream. */
+kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, const double* b_dev, int32_t k,
+                            double* x_dev, double* alphas, double* betas, double* z2, double* psi2, double* pl,
+                            double* grad, double* psi_dev);
+
 /* Parametric-bootstrap MSE of the kriging prediction of the latent field at
  * grid cells (Sec. 3.5, Eq. bootstrap_uq), theta and beta known: replicate b
  * draws x_b on the n1 x n2 grid of the last kry_set_mask with the

@@ -1,6 +1,6 @@
 // genHyBR for the latent field (Sec. 3.2): generalized Golub-Kahan
 // bidiagonalization (Alg. 1) with A = the observed-cell selection, Sigma =
-// the correlation matrix (sigma^2 = 1) applied on the whole grid by the FP64
+// the correlation matrix (sigma^2 = 1) applied on the whole grid by the
 // circulant-embedding matvec, R = tau^2 I; the projected Tikhonov problem
 // (B_k^T B_k + I / sigma^2) z = B_k^T beta1 e1; x_k* = Sigma V_k z_k (Eq.
 // xhat_est); and the approximate profile log-likelihood of Eq. prof_lik with
@@ -11,9 +11,13 @@
 // what U^T U = tau^2 I (Eq. exact_arith) requires.  No reorthogonalisation
 // (the paper runs without it).
 //
-// The whole-grid matvec reuses the FP64 passes of the observed-cell matvec
-// with the row/column index lists of a full mask swapped in for the duration
-// of each call; pass C's fused dot product gives w^T Sigma w, the squared
+// Two precisions: FP64 throughout, or FP32 Krylov vectors (u_i, v_i, Sigma v_i
+// and the whole-grid FP32 matvec) with every norm, inner product and scalar
+// of the recurrence accumulated and kept in FP64.
+//
+// The whole-grid matvec reuses the passes of the observed-cell matvec with
+// the row/column index lists of a full mask swapped in for the duration of
+// each call; pass C's fused dot product gives w^T Sigma w, the squared
 // Sigma-norm of Alg. 1.
 #include <math.h>
 
@@ -56,11 +60,14 @@ struct FullGrid {
     }
 };
 
-// Per-block partial sums of x[i]^2 (fixed order within a block).
-__global__ void k_sq_partials(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+// Per-block partial sums of x[i]^2 in FP64 (fixed order within a block).
+template <typename T>
+__global__ void k_sq_partials(const T* __restrict__ x, int64_t n, double* __restrict__ part) {
     double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += x[i] * x[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        s += v * v;
+    }
     __shared__ double sh[256];
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -72,35 +79,42 @@ __global__ void k_sq_partials(const double* __restrict__ x, int64_t n, double* _
 }
 
 // t[q] = sv[cell q] - alpha u[q]
-__global__ void k_gk_gather(const double* __restrict__ sv, const int* __restrict__ cellidx, const double* __restrict__ u,
-                            double alpha, double* __restrict__ t, int64_t p) {
+template <typename TS, typename TU, typename TO>
+__global__ void k_gk_gather(const TS* __restrict__ sv, const int* __restrict__ cellidx, const TU* __restrict__ u,
+                            double alpha, TO* __restrict__ t, int64_t p) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x)
-        t[q] = sv[cellidx[q]] - alpha * u[q];
+        t[q] = (TO)((double)sv[cellidx[q]] - alpha * (double)u[q]);
 }
 
-__global__ void k_scale_copy(const double* __restrict__ x, double s, double* __restrict__ y, int64_t n) {
+template <typename TI, typename TO>
+__global__ void k_scale_copy(const TI* __restrict__ x, double s, TO* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = s * x[i];
+        y[i] = (TO)(s * (double)x[i]);
 }
 
 // w = -beta v (whole grid), then w[cell q] += u[q] / tau^2 (cells are distinct)
-__global__ void k_gk_fill(const double* __restrict__ v, double beta, double* __restrict__ w, int64_t N) {
+template <typename T>
+__global__ void k_gk_fill(const T* __restrict__ v, double beta, T* __restrict__ w, int64_t N) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        w[i] = -beta * v[i];
+        w[i] = (T)(-beta * (double)v[i]);
 }
-__global__ void k_gk_scatter_add(const double* __restrict__ u, const int* __restrict__ cellidx, double inv_tau2,
-                                 double* __restrict__ w, int64_t p) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x)
-        w[cellidx[q]] += inv_tau2 * u[q];
+template <typename T>
+__global__ void k_gk_scatter_add(const T* __restrict__ u, const int* __restrict__ cellidx, double inv_tau2,
+                                 T* __restrict__ w, int64_t p) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = cellidx[q];
+        w[c] = (T)((double)w[c] + inv_tau2 * (double)u[q]);
+    }
 }
 
-// out[i] = sum_j z[j] V[j][i]  (j < k, fixed order)
-__global__ void k_gk_combine(const double* __restrict__ V, const double* __restrict__ z, int k, int64_t N,
-                             double* __restrict__ out) {
+// out[i] = sum_j z[j] V[j][i]  (j < k, fixed order, FP64 accumulation)
+template <typename T>
+__global__ void k_gk_combine(const T* __restrict__ V, const double* __restrict__ z, int k, int64_t N,
+                             T* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int j = 0; j < k; ++j) s += z[j] * V[(int64_t)j * N + i];
-        out[i] = s;
+        for (int j = 0; j < k; ++j) s += z[j] * (double)V[(int64_t)j * N + i];
+        out[i] = (T)s;
     }
 }
 
@@ -108,8 +122,9 @@ const int NB = 256;
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
 
-double sum_sq(kry_ctx* ctx, const double* x, int64_t n, double* part) {
-    k_sq_partials<<<NB, 256, 0, ctx->stream>>>(x, n, part);
+template <typename T>
+double sum_sq(kry_ctx* ctx, const T* x, int64_t n, double* part) {
+    k_sq_partials<T><<<NB, 256, 0, ctx->stream>>>(x, n, part);
     KRY_CHECK_LAUNCH();
     KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, part, NB * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -119,11 +134,12 @@ double sum_sq(kry_ctx* ctx, const double* x, int64_t n, double* part) {
 }
 
 // sw = Sigma w on the whole grid; returns w^T Sigma w.
-double sigma_full(kry_ctx* ctx, const kry_embed* e, const double* w, double* sw, double* dots, int nds) {
+template <typename T>
+double sigma_full(kry_ctx* ctx, const kry_embed* e, const T* w, T* sw, double* dots, int nds) {
     {
         FullGrid fg(ctx);
         const int64_t N = ctx->p;
-        matvec_ex<double>(ctx, e, w, N, nullptr, sw, N, 1, dots, nds);
+        matvec_ex<T>(ctx, e, w, N, nullptr, sw, N, 1, dots, nds);
     }
     KRY_CUDA(cudaMemcpyAsync(ctx->host_pinned, dots, nds * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -134,8 +150,12 @@ double sigma_full(kry_ctx* ctx, const kry_embed* e, const double* w, double* sw,
 
 }  // namespace
 
-void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
-             double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+namespace {
+
+template <typename T>
+void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
+               double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+    constexpr kry_prec prec = sizeof(T) == 8 ? KRY_F64 : KRY_F32;
     const int n1 = ctx->n1, n2 = ctx->n2;
     const int64_t N = (int64_t)n1 * n2, p = ctx->p;
     KRY_REQUIRE(cov.tau2 > 0.0 && cov.sigma2 > 0.0, KRY_EINVAL, "genHyBR needs tau2 > 0 and sigma2 > 0");
@@ -155,77 +175,82 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
     corr.sigma2 = 1.0;
     corr.tau2 = 0.0;
     const double tau2 = cov.tau2, tau = sqrt(tau2);
-    // scratch: V [k+1][N], SV, W, X (whole grid); U [k+1][p], T (observed); partials; z
+    // scratch: partials, pass C partials (at most 8192), k coefficients (FP64);
+    // then V [k+1][N], SV, W, X (whole grid) and U [k+1][p], T (observed) as T
     int nds = 0;
-    ctx->gk.ensure(((size_t)(k + 4) * N + (size_t)(k + 2) * p + 2 * NB + 8192 + (size_t)k + 1) * sizeof(double));
-    double* V = ctx->gk.as<double>();
-    double* SV = V + (size_t)(k + 1) * N;
-    double* W = SV + N;
-    double* X = W + N;
-    double* U = X + N;
-    double* T = U + (size_t)(k + 1) * p;
-    double* part = T + p;
-    double* dots = part + 2 * NB;   // pass C partials (at most 8192)
-    double* zdev = dots + 8192;     // k coefficients
+    const size_t nd = 2 * NB + 8192 + (size_t)k + 1;
+    ctx->gk.ensure(nd * sizeof(double) + ((size_t)(k + 4) * N + (size_t)(k + 2) * p) * sizeof(T));
+    double* part = ctx->gk.as<double>();
+    double* dots = part + 2 * NB;
+    double* zdev = dots + 8192;
+    T* V = reinterpret_cast<T*>(part + nd);
+    T* SV = V + (size_t)(k + 1) * N;
+    T* W = SV + N;
+    T* X = W + N;
+    T* U = X + N;
+    T* Tt = U + (size_t)(k + 1) * p;
 
-    kry_embed* e = make_embed_internal(ctx, &corr, KRY_F64);
+    kry_embed* e = make_embed_internal(ctx, &corr, prec);
     try {
-        nds = matvec_num_partials(ctx, e, true, 1);
+        {
+            FullGrid fg(ctx);
+            nds = matvec_num_partials(ctx, e, sizeof(T) == 8, 1);
+        }
         KRY_REQUIRE(nds <= 4096, KRY_EUNSUPPORTED, "too many matvec partials");   // the pinned host buffer
         std::vector<double> al(k + 1, 0.0), be(k + 1, 0.0);
         // u_1 = b / beta_1, beta_1 = ||b|| / tau
-        const double beta1 = sqrt(sum_sq(ctx, b, p, part)) / tau;
+        const double beta1 = sqrt(sum_sq<double>(ctx, b, p, part)) / tau;
         KRY_REQUIRE(beta1 > 0.0 && isfinite(beta1), KRY_EINVAL, "b must be finite and nonzero");
         be[0] = beta1;
-        k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(b, 1.0 / beta1, U, p);
+        k_scale_copy<double, T><<<grid_for(p), 256, 0, ctx->stream>>>(b, 1.0 / beta1, U, p);
         KRY_CHECK_LAUNCH();
         // w = A^T u_1 / tau^2, alpha_1 = ||w||_Sigma, v_1 = w / alpha_1
-        KRY_CUDA(cudaMemsetAsync(W, 0, N * sizeof(double), ctx->stream));
-        k_gk_scatter_add<<<grid_for(p), 256, 0, ctx->stream>>>(U, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
+        KRY_CUDA(cudaMemsetAsync(W, 0, N * sizeof(T), ctx->stream));
+        k_gk_scatter_add<T><<<grid_for(p), 256, 0, ctx->stream>>>(U, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
         KRY_CHECK_LAUNCH();
-        double a2 = sigma_full(ctx, e, W, SV, dots, nds);
+        double a2 = sigma_full<T>(ctx, e, W, SV, dots, nds);
         KRY_REQUIRE(a2 > 0.0 && isfinite(a2), KRY_ENAN, "alpha_1 is not positive");
         al[0] = sqrt(a2);
-        k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[0], V, N);
+        k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[0], V, N);
         KRY_CHECK_LAUNCH();
-        k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[0], SV, N);
+        k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[0], SV, N);
         KRY_CHECK_LAUNCH();
         // A step whose beta or alpha falls below 1e-13 of the first one ends the bidiagonalization:
         // the Krylov space then holds the solution (an exact breakdown up to rounding), and the
         // projected problem uses the keff steps taken.
         int keff = k;
         for (int i = 0; i < k; ++i) {
-            double* ui = U + (size_t)i * p;
-            double* un = U + (size_t)(i + 1) * p;
-            double* vi = V + (size_t)i * N;
-            double* vn = V + (size_t)(i + 1) * N;
+            T* ui = U + (size_t)i * p;
+            T* un = U + (size_t)(i + 1) * p;
+            T* vi = V + (size_t)i * N;
+            T* vn = V + (size_t)(i + 1) * N;
             // t = A Sigma v_i - alpha_i u_i, beta_{i+1} = ||t|| / tau, u_{i+1} = t / beta_{i+1}
-            k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(SV, ctx->cellidx.as<int>(), ui, al[i], T, p);
+            k_gk_gather<T, T, T><<<grid_for(p), 256, 0, ctx->stream>>>(SV, ctx->cellidx.as<int>(), ui, al[i], Tt, p);
             KRY_CHECK_LAUNCH();
-            be[i + 1] = sqrt(sum_sq(ctx, T, p, part)) / tau;
+            be[i + 1] = sqrt(sum_sq<T>(ctx, Tt, p, part)) / tau;
             KRY_REQUIRE(isfinite(be[i + 1]), KRY_ENAN, "genGK: beta is NaN/Inf");
             if (!(be[i + 1] > 1e-13 * beta1)) {
                 be[i + 1] = 0.0;
                 keff = i + 1;
                 break;
             }
-            k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(T, 1.0 / be[i + 1], un, p);
+            k_scale_copy<T, T><<<grid_for(p), 256, 0, ctx->stream>>>(Tt, 1.0 / be[i + 1], un, p);
             KRY_CHECK_LAUNCH();
             // w = A^T u_{i+1} / tau^2 - beta_{i+1} v_i, alpha_{i+1} = ||w||_Sigma
-            k_gk_fill<<<grid_for(N), 256, 0, ctx->stream>>>(vi, be[i + 1], W, N);
+            k_gk_fill<T><<<grid_for(N), 256, 0, ctx->stream>>>(vi, be[i + 1], W, N);
             KRY_CHECK_LAUNCH();
-            k_gk_scatter_add<<<grid_for(p), 256, 0, ctx->stream>>>(un, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
+            k_gk_scatter_add<T><<<grid_for(p), 256, 0, ctx->stream>>>(un, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
             KRY_CHECK_LAUNCH();
-            a2 = sigma_full(ctx, e, W, SV, dots, nds);
+            a2 = sigma_full<T>(ctx, e, W, SV, dots, nds);
             KRY_REQUIRE(isfinite(a2), KRY_ENAN, "genGK: alpha is NaN/Inf");
             if (!(a2 > 1e-26 * al[0] * al[0])) {
                 keff = i + 1;
                 break;
             }
             al[i + 1] = sqrt(a2);
-            k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[i + 1], vn, N);
+            k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[i + 1], vn, N);
             KRY_CHECK_LAUNCH();
-            k_scale_copy<<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[i + 1], SV, N);
+            k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[i + 1], SV, N);
             KRY_CHECK_LAUNCH();
         }
         // projected Tikhonov problem: (B^T B + I / sigma^2) z = B^T beta1 e1, B (k+1) x k lower
@@ -247,22 +272,26 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
         for (int j = 0; j < kk; ++j) z2 += zz[j] * zz[j];
         // x* = Sigma V_k z, psi = b - A x*
         KRY_CUDA(cudaMemcpyAsync(zdev, zz.data(), kk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        k_gk_combine<<<grid_for(N), 256, 0, ctx->stream>>>(V, zdev, kk, N, W);
+        k_gk_combine<T><<<grid_for(N), 256, 0, ctx->stream>>>(V, zdev, kk, N, W);
         KRY_CHECK_LAUNCH();
-        sigma_full(ctx, e, W, X, dots, nds);
-        k_gk_gather<<<grid_for(p), 256, 0, ctx->stream>>>(X, ctx->cellidx.as<int>(), b, 1.0, T, p);   // x*[c] - b
+        sigma_full<T>(ctx, e, W, X, dots, nds);
+        // x*[c] - b, formed in FP64 from the x* the caller receives
+        k_gk_gather<T, double, T><<<grid_for(p), 256, 0, ctx->stream>>>(X, ctx->cellidx.as<int>(), b, 1.0, Tt, p);
         KRY_CHECK_LAUNCH();
-        const double psi2 = sum_sq(ctx, T, p, part);
-        if (x_out) KRY_CUDA(cudaMemcpyAsync(x_out, X, N * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        const double psi2 = sum_sq<T>(ctx, Tt, p, part);
+        if (x_out) {
+            k_scale_copy<T, double><<<grid_for(N), 256, 0, ctx->stream>>>(X, 1.0, x_out, N);
+            KRY_CHECK_LAUNCH();
+        }
         if (psi_out) {   // psi = b - A x* = -T
-            k_scale_copy<<<grid_for(p), 256, 0, ctx->stream>>>(T, -1.0, psi_out, p);
+            k_scale_copy<T, double><<<grid_for(p), 256, 0, ctx->stream>>>(Tt, -1.0, psi_out, p);
             KRY_CHECK_LAUNCH();
         }
         // Appendix A, Eq. approx_grad: (V_k z_k)^T dSigma (V_k z_k), V_k z_k still in W
         double qdq = 0.0;
         if (grad) {
             drange_embedding(ctx, corr, e);   // e now applies dSigma
-            qdq = sigma_full(ctx, e, W, SV, dots, nds);
+            qdq = sigma_full<T>(ctx, e, W, SV, dots, nds);
         }
         double ld = 0.0, dl = 0.0;
         bccb_logdet(ctx, corr, grad != nullptr, &ld, grad ? &dl : nullptr);
@@ -285,6 +314,16 @@ void genhybr(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x
         throw;
     }
     free_embed_internal(e);
+}
+
+}  // namespace
+
+void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, const double* b, int k, double* x_out, double* alphas,
+             double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+    if (prec == KRY_F32)
+        genhybr_t<float>(ctx, cov, b, k, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
+    else
+        genhybr_t<double>(ctx, cov, b, k, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
 }
 
 }  // namespace kry

@@ -489,9 +489,18 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
 // Martin, Reinsch & Wilkinson, "The QR and QL algorithms for symmetric
 // matrices", Numer. Math. 1968; EISPACK's tql2), rotating only the first row of
 // the eigenvector matrix (Golub & Welsch 1969).
-__global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, double znorm2, double* __restrict__ out) {
+//
+// K = sigma2 A Sigma A^T + tau2 I has every eigenvalue >= tau2, and so has
+// every Ritz value of exact arithmetic.  Rounding in the matvec can move the
+// smallest computed Ritz values below that bound (to zero or below once it is
+// of the order of tau2, where the log would be undefined), so the nodes are
+// taken as max(d_i, tau2) of the vector's setting (tau2v[v / vpt] for a
+// batched embedding, tau2 otherwise).
+__global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, double znorm2, double* __restrict__ out,
+                             double tau2, const double* __restrict__ tau2v, int vpt) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprobe) return;
+    const double lb = (tau2v && vpt > 0) ? tau2v[k / vpt] : tau2;
     const int n = S.m_eff[k];
     double d[KRY_MAX_STEPS], e[KRY_MAX_STEPS], z[KRY_MAX_STEPS];
     for (int i = 0; i < n; ++i) {
@@ -542,7 +551,7 @@ __global__ void k_quadrature(const LanczosState S, int nprobe, int nsteps, doubl
         }
     }
     double acc = 0.0;
-    for (int i = 0; i < n; ++i) acc += z[i] * z[i] * log(d[i]);
+    for (int i = 0; i < n; ++i) acc += z[i] * z[i] * log(fmax(d[i], lb));
     out[k] = znorm2 * acc;
 }
 
@@ -663,7 +672,8 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
         run_captured(ctx, [&]() {
             for (int j = 1; j < nsteps; ++j) step(j);
         });
-    k_quadrature<<<(nvec + 63) / 64, 64, 0, ctx->stream>>>(S, nvec, nsteps, (double)p, res);
+    k_quadrature<<<(nvec + 63) / 64, 64, 0, ctx->stream>>>(S, nvec, nsteps, (double)p, res, e->cov.tau2,
+                                                         e->ntheta > 1 ? e->tau2_dev : nullptr, vpt);
     KRY_CHECK_LAUNCH();
     KRY_CUDA(cudaMemcpyAsync(per_vec, res, nvec * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));
