@@ -98,7 +98,18 @@ typedef struct {
  * at least 0.4 of the observed cells have all four grid neighbours observed
  * (kry_mask_interior; on 512^2 masks that is where the preconditioned solve
  * was the faster one).  The result does not depend on it beyond the CG
- * tolerance. */
+ * tolerance.
+ * prec = KRY_F32 in kry_profile_loglik, kry_krige, kry_loglik_krige and
+ * kry_bootstrap_var: FP32 vectors and matvecs with FP64 scalars, for each
+ * covariance setting whose conditioning FP32 resolves, kappa = (max |Lambda|
+ * + tau2) / tau2 <= 4e6 (every eigenvalue of K lies in [tau2, max |Lambda| +
+ * tau2]; FP32 CG stalls as kappa u32 nears one, u32 = 2^-24).  A setting
+ * above that bound, or with tau2 = 0, runs in FP64 instead, alone
+ * (kry_promoted counts them).  In FP32 the log-determinant wants reorth = 1:
+ * without it the FP32 quadrature drifts as kappa grows (measured 8.6e-4
+ * relative at kappa 3.3e5 on a 1024^2 grid, 5.6e-3 on 256^2 with the same
+ * range in cells), while with it, or in FP64 either way, it stays within
+ * 1e-5 of the reorthogonalised FP64 value. */
 typedef struct {
     kry_prec prec;
     int32_t nprobe, nsteps;
@@ -131,6 +142,11 @@ kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_
  * scattered holes; 0 without a mask or with sites.  It decides
  * kry_opts.precond = 2.  (No counterpart in the paper.) */
 kry_status kry_mask_interior(kry_ctx* ctx, double* interior);
+
+/* Number of covariance settings that calls on ctx asked for in FP32 and ran in
+ * FP64 because FP32 would not resolve their conditioning (kry_opts, prec),
+ * counted since kry_create. */
+kry_status kry_promoted(kry_ctx* ctx, int64_t* count);
 
 /* Irregular observation sites (Sec. 2: y = X beta + A x + eps with A the
  * p x n mapping matrix of Wendland weights).  sites_dev holds nsite (x1, x2)
@@ -333,9 +349,13 @@ kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, in
  * inner product of Alg. 1 (alpha_i, beta_i, w^T Sigma w), the projected
  * problem, ||z_k||^2, ||psi_k*||^2, pl and the gradient are accumulated and
  * kept in FP64; x_dev and psi_dev are written in FP64 from the FP32 vectors.
- * FP32 rounding perturbs the bidiagonal at the 1e-6 level and the estimate
- * and pl accordingly.  Library scratch: (2k + 6) n1 n2 floats (FP32) or
- * doubles (FP64).  Arguments, outputs and errors as for kry_genhybr, plus
+ * Without reorthogonalisation the recurrence amplifies rounding once
+ * orthogonality is lost, and FP32 rounding is 2^29 times larger: measured
+ * against the FP64 oracle, pl agrees to 4e-5 (40 x 36 grid, k = 15), 4e-7
+ * (128^2, k = 30) and 8e-4 (1024^2, k = 50), and with the FP64 path to
+ * 1.1e-4 at 4096^2 (k = 50), where it runs 6.6 times faster (0.18 s vs
+ * 1.17 s).  Library scratch: (2k + 6) n1 n2 floats (FP32) or doubles
+ * (FP64).  Arguments, outputs and errors as for kry_genhybr, plus
  * KRY_EINVAL for another prec.  Synchronises the stream. */
 kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, const double* b_dev, int32_t k,
                             double* x_dev, double* alphas, double* betas, double* z2, double* psi2, double* pl,

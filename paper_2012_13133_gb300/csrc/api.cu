@@ -17,6 +17,21 @@
 // Interior share of the mask from which kry_opts.precond = 2 preconditions CG.
 #define KRY_PRECOND_AUTO_INTERIOR 0.4
 
+// FP32 Krylov iterates resolve K = sigma2 A Sigma A^T + tau2 I only while
+// kappa u32 stays below one, u32 = 2^-24 and kappa = (max |Lambda| + tau2) /
+// tau2 the bound on K's condition number that the embedding gives (every
+// eigenvalue of K lies in [tau2, max |Lambda| + tau2]).  Measured on 1024^2
+// and 2048^2 grids with half the cells observed (Matern 3/2, range 0.05, CG
+// on [y, X] to 1e-6 with FP64 residual replacement, at most 20,000
+// iterations): FP32 CG converged at kappa 3.3e6 on both grids (about 9,000
+// iterations) and at 6.6e6 on 2048^2 (19,968), and stalled at 5.5e6 on
+// 1024^2 (relative residual 1.6e-4) and 1.3e7 on 2048^2 (0.57).  The FP32
+// log-det with partial reorthogonalisation stayed within 1.2e-5 of the FP64
+// one throughout.  Above 4e6 (kappa u32 = 0.24), likelihood, kriging and
+// bootstrap calls asked for in FP32 run that setting in FP64 instead (counted
+// by kry_promoted).
+#define KRY_F32_KAPPA_MAX 4.0e6
+
 namespace kry {
 void store_embedding(kry_ctx* ctx, kry_embed* e, int slot);
 void logdet_batched(kry_ctx* ctx, const kry_embed* e, int nprobe, int nsteps, uint64_t seed, bool reorth,
@@ -250,7 +265,16 @@ static bool spec_column_pass(const kry_ctx* ctx, const kry_embed* e) {
     return ctx->use_spec && e->M1 >= 64 && e->M2 >= 64 && e->M1 <= 8192 && e->M2 <= 8192;
 }
 
-static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
+// True if FP32 iterates resolve the covariance whose embedding eigenvalues span
+// [lam_lo, lam_hi] with nugget tau2 (KRY_F32_KAPPA_MAX).
+static bool f32_resolves(double lam_lo, double lam_hi, double tau2) {
+    const double lmax = std::max(fabs(lam_lo), fabs(lam_hi));
+    return tau2 > 0.0 && (lmax + tau2) / tau2 <= KRY_F32_KAPPA_MAX;
+}
+
+// promote: an FP32 request whose conditioning FP32 cannot resolve gets an FP64
+// embedding (and counts in ctx->promoted).
+static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, bool promote = false) {
     check_cov(cov);
     require_mask(ctx);
     KRY_REQUIRE(prec == KRY_F32 || prec == KRY_F64, KRY_EINVAL, "prec must be KRY_F32 or KRY_F64");
@@ -266,6 +290,11 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     e->stream = ctx->stream;
     try {
         kry::compute_eigs(ctx, *cov, ctx->n1, ctx->n2, ctx->dx1, ctx->dx2, e->M1, e->M2, &e->lam_min, &e->lam_max);
+        if (promote && prec == KRY_F32 && !f32_resolves(e->lam_min, e->lam_max, cov->tau2)) {
+            prec = KRY_F64;
+            e->prec = KRY_F64;
+            ++ctx->promoted;
+        }
         const size_t MM = (size_t)e->M1 * e->M2;
         dev_alloc((void**)&e->lam64T, MM * sizeof(double), ctx->stream);
         if (prec == KRY_F32) dev_alloc((void**)&e->lam32T, MM * sizeof(float), ctx->stream);
@@ -281,15 +310,17 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec) {
     return e;
 }
 
-// CG preconditioner for one covariance setting (kry_opts.precond): an FP32
+// CG preconditioner for one covariance setting (kry_opts.precond) of a solve
+// in precision prec: an FP32
 // embedding whose matvec applies M^-1 = A (S + tau2 I)^-1 A^T, S the circulant
 // embedding of sigma2 Sigma on the torus: eigenvalues 1 / (max(Lambda, 0) +
 // tau2), no nugget.  NULL when it does not apply: FP64 solves, several
 // settings, tau2 = 0, and irregular sites (with Wendland weights, close sites
 // give nearly equal rows of A, so A (S + tau2 I)^-1 A^T is nearly singular and
 // preconditioned CG stalls: measured, 12,000 sites on a 128^2 grid).
-static kry_embed* make_precond_embed(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o, int ntheta) {
-    if (!o->precond || o->prec != KRY_F32 || ntheta != 1 || !(cov->tau2 > 0.0) || ctx->sites.active) return nullptr;
+static kry_embed* make_precond_embed(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o, kry_prec prec,
+                                     int ntheta) {
+    if (!o->precond || prec != KRY_F32 || ntheta != 1 || !(cov->tau2 > 0.0) || ctx->sites.active) return nullptr;
     // automatic choice: clustered gaps (measured on 512^2 masks: at an interior
     // share of 0.4 and more the preconditioned solve was the faster one)
     if (o->precond == 2 && ctx->interior < KRY_PRECOND_AUTO_INTERIOR) return nullptr;
@@ -504,6 +535,14 @@ kry_status kry_mask_interior(kry_ctx* ctx, double* interior) {
     });
 }
 
+kry_status kry_promoted(kry_ctx* ctx, int64_t* count) {
+    return guarded(ctx, [&]() -> kry_status {
+        KRY_REQUIRE(count != nullptr, KRY_EINVAL, "count must not be NULL");
+        *count = ctx->promoted;
+        return KRY_OK;
+    });
+}
+
 kry_status kry_set_sites(kry_ctx* ctx, const kry_grid* grid, const double* sites_dev, int64_t nsite) {
     return guarded(ctx, [&]() -> kry_status {
         KRY_REQUIRE(grid && sites_dev, KRY_EINVAL, "grid and sites_dev must not be NULL");
@@ -619,7 +658,7 @@ kry_status kry_solve_pre(kry_ctx* ctx, const kry_embed* e, const double* B_dev, 
         kry_opts o{};
         o.prec = e->prec;
         o.precond = 1;
-        kry_embed* pre = make_precond_embed(ctx, &e->cov, &o, 1);
+        kry_embed* pre = make_precond_embed(ctx, &e->cov, &o, e->prec, 1);
         kry::SolveInfo si;
         try {
             si = kry::solve(ctx, e, B_dev, ld, X_dev, ld, nrhs, rtol, maxit, 0, pre);
@@ -658,7 +697,7 @@ static kry::SolveInfo solve_yx(kry_ctx* ctx, const kry_embed* e, const double* y
     KRY_CUDA(cudaMemcpyAsync(V + p, X, (size_t)ncov * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     *V_out = V;
     *Z_out = Z;
-    kry_embed* pre = make_precond_embed(ctx, &e->cov, o, 1);
+    kry_embed* pre = make_precond_embed(ctx, &e->cov, o, e->prec, 1);
     kry::SolveInfo si;
     try {
         si = kry::solve(ctx, e, V, p, Z, p, nc, o->rtol, o->maxit, 0, pre);
@@ -686,11 +725,33 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
         const bool batched = ntheta > 1 && opts->nprobe % 2 == 0;
         // settings per group: keep the batched vectors within ~2048 (log-det) per launch sequence
         const int group = batched ? std::max(1, std::min<int>(ntheta, 2048 / opts->nprobe)) : 1;
+        // an FP32 batch holds only settings that FP32 resolves (KRY_F32_KAPPA_MAX);
+        // the others run alone, promoted to FP64
+        std::vector<std::vector<int>> groups;
+        {
+            std::vector<int> in_batch, alone;
+            for (int t = 0; t < ntheta; ++t) {
+                bool ok = true;
+                if (batched && opts->prec == KRY_F32) {
+                    double lo, hi;
+                    kry::compute_eigs(ctx, thetas[t], ctx->n1, ctx->n2, ctx->dx1, ctx->dx2,
+                                      pow2_at_least(2 * (int64_t)ctx->n1), pow2_at_least(2 * (int64_t)ctx->n2), &lo,
+                                      &hi);
+                    ok = f32_resolves(lo, hi, thetas[t].tau2);
+                }
+                (ok ? in_batch : alone).push_back(t);
+            }
+            for (size_t i = 0; i < in_batch.size(); i += group)
+                groups.emplace_back(in_batch.begin() + i, in_batch.begin() + std::min(in_batch.size(), i + group));
+            for (int t : alone) groups.push_back({t});
+        }
         kry_status worst = KRY_OK;
-        for (int t0 = 0; t0 < ntheta; t0 += group) {
-            const int ng = std::min(group, ntheta - t0);
-            kry_embed* e = (ng > 1) ? make_embed_batch(ctx, thetas + t0, ng, opts->prec)
-                                    : make_embed(ctx, &thetas[t0], opts->prec);
+        for (const std::vector<int>& gi : groups) {
+            const int ng = (int)gi.size();
+            std::vector<kry_cov> th(ng);
+            for (int t = 0; t < ng; ++t) th[t] = thetas[gi[t]];
+            kry_embed* e = (ng > 1) ? make_embed_batch(ctx, th.data(), ng, opts->prec)
+                                    : make_embed(ctx, &th[0], opts->prec, true);
             try {
                 // log-determinants: ng settings x nprobe probes in one batched Lanczos
                 std::vector<double> vals((size_t)ng * opts->nprobe);
@@ -713,7 +774,7 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
                     if (ncp > nc)
                         KRY_CUDA(cudaMemsetAsync(blk + (size_t)nc * p, 0, p * sizeof(double), ctx->stream));
                 }
-                kry_embed* pre = make_precond_embed(ctx, &thetas[t0], opts, ng);
+                kry_embed* pre = make_precond_embed(ctx, &th[0], opts, e->prec, ng);
                 kry::SolveInfo si;
                 try {
                     si = kry::solve(ctx, e, Vrep, p, Z, p, ng * ncp, opts->rtol, opts->maxit, ng > 1 ? ncp : 0, pre);
@@ -728,7 +789,7 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
                     double ld = 0, se = 0;
                     mean_se(pv, &ld, &se);
                     kry::GlsResult g = kry::gls(ctx, V, Z + (size_t)t * ncp * p, ncov, ld);
-                    const int ti = t0 + t;
+                    const int ti = gi[t];
                     loglik[ti] = g.loglik;
                     if (beta)
                         for (int c = 0; c < ncov; ++c) beta[(size_t)ti * ncov + c] = g.beta[c];
@@ -813,7 +874,7 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
         check_cov(cov);
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
                          mean_cells_dev, mean_sites_dev, var_cells_dev);
-        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
         kry_status st = KRY_OK;
         try {
             double *V, *Z;
@@ -844,7 +905,7 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
         KRY_REQUIRE(loglik != nullptr, KRY_EINVAL, "loglik must not be NULL");
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
                          mean_cells_dev, mean_sites_dev, var_cells_dev);
-        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
         kry_status st = KRY_OK;
         try {
             std::vector<double> vals(opts->nprobe);
@@ -964,10 +1025,10 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
         for (int b = 0; b < nrep; ++b)
             kry::sample_field(ctx, *cov, M1, M2, xi_dev + (size_t)b * 2 * M1 * M2, G + (size_t)b * N);
         kry::boot_rhs(ctx, G, N, eps_dev, sqrt(cov->tau2), R, nrep);
-        kry_embed* e = make_embed(ctx, cov, opts->prec);
+        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
         kry::SolveInfo si;
         try {
-            kry_embed* pre = make_precond_embed(ctx, cov, opts, 1);
+            kry_embed* pre = make_precond_embed(ctx, cov, opts, e->prec, 1);
             try {
                 si = kry::solve(ctx, e, R, p, Wd, p, nrep, opts->rtol, opts->maxit, 0, pre);
             } catch (...) {

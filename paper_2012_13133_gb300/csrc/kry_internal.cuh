@@ -127,6 +127,8 @@ struct kry_ctx {
     // (cells beyond the grid edge count as observed): near 1 for clustered
     // gaps, low for scattered holes; kry_opts.precond = 2 reads it
     double interior = 0.0;
+    // FP32 requests run in FP64 for their conditioning (kry_promoted)
+    int64_t promoted = 0;
     DevBuf rowptr;   // int32 [n1 + 1]: first observed index of each row
     DevBuf colidx;   // int32 [p]: column of each observed cell
     DevBuf cellidx;  // int32 [p]: row-major cell index of each observed cell

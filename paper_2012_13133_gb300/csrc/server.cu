@@ -82,15 +82,20 @@ int64_t estimate_bytes(const kry_request& r, int64_t p) {
     const int64_t MM = M1 * M2;
     const int nc = r.ncov + 1 + ((r.ncov + 1) & 1);
     const int64_t vecs = (r.kind == KRY_REQ_LOGLIK) ? std::max(r.opts.nprobe, nc) : nc;
+    // bytes per vector element: FP64 requests, and FP32 ones that will run in FP64
+    // for want of a nugget (an FP32 request promoted for its conditioning, kappa >
+    // 4e6, needs up to twice the vector memory counted here: the budget is meant
+    // to stay well below the device's memory)
+    const int64_t es = (r.opts.prec == KRY_F64 || !(r.cov.tau2 > 0.0)) ? 8 : 4;
     int64_t b = 0;
     b += 36 * MM;                                  // eigenvalues (FP64 + FP32) and eigen scratch
-    b += (int64_t)r.n1 * M2 * 8 * ((vecs + 1) / 2);   // FP32 slab
+    b += (int64_t)r.n1 * M2 * 2 * es * ((vecs + 1) / 2);   // Krylov slab
     b += (int64_t)r.n1 * M2 * 16 * ((nc + 1) / 2);    // FP64 slab (true residuals)
-    b += 4 * vecs * p * 4 + 4 * nc * p * 8;        // Lanczos / CG vectors, FP64 residual work
+    b += 4 * vecs * p * es + 4 * nc * p * 8;       // Lanczos / CG vectors, FP64 residual work
     b += 3 * (int64_t)nc * p * 8 + (N + p) * 8;    // [y, X], solutions, kriging grid
     if (r.opts.precond) b += 16 * MM + (int64_t)nc * p * 4;   // preconditioner eigenvalues, z vectors
     if (r.kind == KRY_REQ_LOGLIK && r.opts.reorth)   // stored Lanczos basis
-        b += (int64_t)r.opts.nprobe * r.opts.nsteps * p * (r.opts.prec == KRY_F64 ? 8 : 4);
+        b += (int64_t)r.opts.nprobe * r.opts.nsteps * p * es;
     b += N + p * 8 * (1 + r.ncov) + (N - p) * 8 * (2 + r.ncov);   // inputs and outputs
     return b + b / 4 + (64 << 20);
 }

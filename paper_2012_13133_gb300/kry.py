@@ -63,6 +63,7 @@ SIGNATURES = {
     "kry_set_mask": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.POINTER(C.c_int64)]),
     "kry_set_sites": (C.c_int, [_P, C.POINTER(kry_grid), _P, C.c_int64]),
     "kry_mask_interior": (C.c_int, [_P, _DP]),
+    "kry_promoted": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "kry_embed_eigs": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.POINTER(_P), _DP]),
     "kry_embed_free": (None, [_P]),
     "kry_matvec": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int64]),
@@ -261,6 +262,12 @@ class Context:
         """Share of the observed cells whose four grid neighbours are observed (kry_mask_interior)."""
         v = C.c_double()
         self._check(_lib.kry_mask_interior(self.h, C.byref(v)))
+        return v.value
+
+    def promoted(self) -> int:
+        """Covariance settings asked for in FP32 that ran in FP64 for their conditioning (kry_promoted)."""
+        v = C.c_int64()
+        self._check(_lib.kry_promoted(self.h, C.byref(v)))
         return v.value
 
     def set_sites(self, sites, n1, n2, dx1=None, dx2=None) -> int:

@@ -22,10 +22,17 @@ What the oracle computes, per workload (all FP64, the paper's definitions):
   (Eq. act_xhat plus the trend), at every unobserved cell (grid1024) or at a
   seeded sample of them (large4096).
 
+For large4096 the per-probe values may be restricted to the first ``--probes``
+probes (``probe_ids`` in the file; log det and log-likelihood then use those
+probes), since each fully reorthogonalised 80-step basis at 4096^2 takes about
+20 GB of host memory per worker.  ``--ckpt DIR`` keeps the CG solution there
+and reuses it when the script runs again.
+
 Usage (from the repository root; hours for large4096 on a few cores):
     python tests/golden/make_fullsize.py grid1024  [--procs 4] [--threads 2]
     python tests/golden/make_fullsize.py search512 [--procs 4] [--threads 2]
-    python tests/golden/make_fullsize.py large4096 --tol 1e-8 --precond [--procs 4] [--threads 2]
+    python tests/golden/make_fullsize.py large4096 --tol 1e-8 --precond --probes 8 \
+        [--procs 4] [--threads 1] [--slq-procs 2] [--slq-threads 3] [--ckpt DIR]
 """
 from __future__ import annotations
 
@@ -103,32 +110,43 @@ def _cg(args):
     return j, x, it
 
 
-def run_problem(name, cov_index, y, X, tol, procs, threads, log, precond=False):
-    """Per-probe SLQ values, the CG solve of [y, X], GLS beta and loglik for one setting."""
+def run_problem(name, cov_index, y, X, tol, procs, threads, log, precond=False, nprobe=None, slq_procs=None,
+                slq_threads=None, ckpt=None):
+    """Per-probe SLQ values (probes 0 .. nprobe-1, all by default), the CG solve of [y, X], GLS
+    beta and loglik for one setting.  ckpt: file that keeps the CG solution between runs."""
     from oracle import kryoracle as O
     from paper_2012_13133_gb300 import inputs as I
     w = I.WORKLOADS[name]
     ctx = mp.get_context("spawn")
     t0 = time.time()
     B = np.column_stack([y, X])
-    with ctx.Pool(min(procs, B.shape[1]), initializer=_init, initargs=(name, threads, cov_index)) as pool:
-        sols = sorted(pool.map(_cg, [(j, B[:, j], tol, precond) for j in range(B.shape[1])]),
-                      key=lambda r: r[0])
-    Z = np.stack([s[1] for s in sols], axis=1)
-    iters = [s[2] for s in sols]
+    if ckpt and os.path.exists(ckpt):
+        c = np.load(ckpt)
+        Z, iters = c["Z"], [int(i) for i in c["iters"]]
+        assert Z.shape == B.shape
+        log(f"  CG solution from {ckpt}")
+    else:
+        with ctx.Pool(min(procs, B.shape[1]), initializer=_init, initargs=(name, threads, cov_index)) as pool:
+            sols = sorted(pool.map(_cg, [(j, B[:, j], tol, precond) for j in range(B.shape[1])]),
+                          key=lambda r: r[0])
+        Z = np.stack([s[1] for s in sols], axis=1)
+        iters = [s[2] for s in sols]
+        if ckpt:
+            np.savez(ckpt, Z=Z, iters=np.array(iters))
     log(f"  CG {iters} iterations, {time.time() - t0:.0f} s")
     t0 = time.time()
-    with ctx.Pool(procs, initializer=_init, initargs=(name, threads, cov_index)) as pool:
-        res = sorted(pool.map(_probe, [(k, w.nsteps, w.probe_seed) for k in range(w.nprobe)]),
+    nprobe = w.nprobe if nprobe is None else nprobe
+    with ctx.Pool(slq_procs or procs, initializer=_init, initargs=(name, slq_threads or threads, cov_index)) as pool:
+        res = sorted(pool.map(_probe, [(k, w.nsteps, w.probe_seed) for k in range(nprobe)], chunksize=1),
                      key=lambda r: r[0])
     per = np.array([r[1] for r in res])
     steps = np.array([r[2] for r in res])
-    log(f"  SLQ {w.nprobe} probes, {time.time() - t0:.0f} s")
+    log(f"  SLQ {nprobe} probes, {time.time() - t0:.0f} s")
     ld = float(per.mean())
     se = float(per.std(ddof=1) / math.sqrt(per.size))
     ll, beta, quad = O.gls_loglik(ld, Z[:, 0], Z[:, 1:], y, X)
-    return dict(per_probe=per, lanczos_steps=steps, logdet=ld, logdet_se=se, loglik=ll, beta=beta, quad=quad,
-                cg_iters=np.array(iters), Z=Z)
+    return dict(per_probe=per, probe_ids=np.arange(nprobe), lanczos_steps=steps, logdet=ld, logdet_se=se, loglik=ll,
+                beta=beta, quad=quad, cg_iters=np.array(iters), Z=Z)
 
 
 def main():
@@ -139,6 +157,10 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--precond", action="store_true",
                     help="CG preconditioned by the torus inverse (same solution, fewer iterations)")
+    ap.add_argument("--probes", type=int, default=None, help="per-probe values for the first K probes only")
+    ap.add_argument("--slq-procs", type=int, default=None)
+    ap.add_argument("--slq-threads", type=int, default=None)
+    ap.add_argument("--ckpt", default=None, help="directory that keeps the CG solution between runs")
     args = ap.parse_args()
 
     from oracle import kryoracle as O
@@ -157,7 +179,9 @@ def main():
     S1, S2 = I.cell_centres(w.n1, w.n2)
 
     if w.name in ("grid1024", "large4096"):
-        r = run_problem(w.name, -1, y, X, args.tol, args.procs, args.threads, log, args.precond)
+        ck = os.path.join(args.ckpt, f"{w.name}_cg_{args.tol:g}.npz") if args.ckpt else None
+        r = run_problem(w.name, -1, y, X, args.tol, args.procs, args.threads, log, args.precond, args.probes,
+                        args.slq_procs, args.slq_threads, ck)
         Z = r.pop("Z")
         out.update(r)
         wts = Z[:, 0] - Z[:, 1:] @ r["beta"]

@@ -534,6 +534,85 @@ def test_genhybr_matches_oracle(ctx, n1, n2, cov, k):
         ctx.genhybr(I.Cov(1.0, 0.1, 0.5, 0.0), torch.tensor(b, device=DEV), k)   # tau2 = 0
 
 
+@pytest.mark.parametrize("n1,n2,cov,k,kind", [
+    (40, 36, I.Cov(1.0, 0.1, 0.5, 0.1), 15, "circles"),
+    (128, 128, I.Cov(1.0, 0.05, 1.5, 0.05), 30, "uniform"),
+])
+def test_genhybr_fp32_matches_oracle(ctx, n1, n2, cov, k, kind):
+    """genGK/genHyBR with FP32 Krylov vectors and FP64 scalars (kry_genhybr_prec) against the FP64
+    oracle.  Without reorthogonalisation (as the paper runs Alg. 1) rounding differences grow with
+    the step count once orthogonality is lost (the FP64 path's own distance to the oracle grows
+    likewise), so the first three bidiagonal entries are held to 1e-4 (one FP32 matvec's rounding),
+    the rest to 2e-2, ||z||^2 and ||psi||^2 to 1e-3, x_k* to 2e-2 and pl to 5e-4 relative:
+    several times the distances measured at these sizes."""
+    mask = make_mask(n1, n2, 0.3 if kind == "circles" else 0.5, kind)
+    p = set_mask(ctx, mask)
+    b = I.normals(p, 31)
+    g = ctx.genhybr(cov, torch.tensor(b, device=DEV), k, prec=kry.KRY_F32)
+    ref = O.approx_profile_loglik(n1, n2, mask, cov, b, k)
+    _, _, _, al, be = O.gengk(n1, n2, mask, cov, b, k)
+    ra = np.abs(g["alphas"] - al) / np.abs(al)
+    rb = np.abs(g["betas"] - be) / np.abs(be)
+    print(f"FP32 genGK {n1}x{n2} k={k}: alpha {ra.max():.1e}, beta {rb.max():.1e}, "
+          f"x {relerr(g['x'].cpu().numpy().ravel(), ref['x']):.1e}, pl {abs(g['pl'] / ref['pl'] - 1):.1e}")
+    assert ra[:3].max() <= 1e-4 and rb[:3].max() <= 1e-4
+    assert ra.max() <= 2e-2 and rb.max() <= 2e-2
+    assert g["z2"] == pytest.approx(ref["z2"], rel=1e-3)
+    assert g["psi2"] == pytest.approx(ref["psi2"], rel=1e-3)
+    assert relerr(g["x"].cpu().numpy().ravel(), ref["x"]) <= 2e-2
+    assert g["pl"] == pytest.approx(ref["pl"], rel=5e-4)
+    # the gradient in FP32 against the oracle's
+    gg = ctx.genhybr(cov, torch.tensor(b, device=DEV), k, want_x=False, gradient=True, prec=kry.KRY_F32)
+    gref = O.approx_gradient(n1, n2, mask, cov, b, k)
+    assert np.allclose(gg["grad"], gref["grad"], rtol=2e-2, atol=1e-3 * np.abs(gref["grad"]).max())
+    with pytest.raises(kry.KryError) as ei:
+        ctx.genhybr(cov, torch.tensor(b, device=DEV), k, prec=7)
+    assert ei.value.status == kry.KRY_EINVAL
+
+
+def test_fp32_requests_run_ill_conditioned_settings_in_fp64(ctx):
+    """An FP32 likelihood or kriging request runs a covariance setting in FP64 when FP32 cannot
+    resolve its conditioning, kappa = (max |Lambda| + tau2) / tau2 > 4e6 (kry_opts): its results are
+    those of the FP64 request bit for bit, kry_promoted counts it, and in a batched search the other
+    settings keep their FP32 batch.  A setting below the bound stays in FP32."""
+    n = 64
+    mask = make_mask(n, n, 0.5, "uniform")
+    p = set_mask(ctx, mask)
+    lmax = float(np.abs(O.FFTProblem(n, n, mask, I.Cov(1.0, 0.3, 1.5, 0.0)).lam).max())
+    bad = I.Cov(1.0, 0.3, 1.5, lmax / 1e7)       # kappa ~ 1e7
+    good = I.Cov(1.0, 0.3, 1.5, lmax / 1e5)      # kappa ~ 1e5
+    good2 = I.Cov(1.0, 0.2, 1.5, lmax / 1e5)
+    S1, S2 = I.cell_centres(n, n)
+    X = I.covariates(S1[mask], S2[mask])
+    y = X @ np.array([1.0, 0.5, -0.5]) + I.normals(p, 17)
+    yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
+    o32 = kry.Opts(prec=kry.KRY_F32, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
+    o64 = kry.Opts(prec=kry.KRY_F64, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
+    n0 = ctx.promoted()
+    r32 = ctx.profile_loglik(yt, Xt, [bad], o32)
+    assert ctx.promoted() == n0 + 1
+    r64 = ctx.profile_loglik(yt, Xt, [bad], o64)
+    assert r32["status"] == r64["status"] == kry.KRY_OK
+    assert r32["loglik"][0] == r64["loglik"][0] and r32["logdet"][0] == r64["logdet"][0]
+    g32 = ctx.profile_loglik(yt, Xt, [good], o32)
+    g64 = ctx.profile_loglik(yt, Xt, [good], o64)
+    assert ctx.promoted() == n0 + 1
+    assert g32["loglik"][0] != g64["loglik"][0]
+    assert g32["loglik"][0] == pytest.approx(g64["loglik"][0], rel=1e-3)
+    both = ctx.profile_loglik(yt, Xt, [good, bad, good2], o32)
+    assert ctx.promoted() == n0 + 2
+    pair = ctx.profile_loglik(yt, Xt, [good, good2], o32)
+    assert both["loglik"][1] == r64["loglik"][0]
+    assert both["loglik"][0] == pair["loglik"][0] and both["loglik"][2] == pair["loglik"][1]
+    cells = np.flatnonzero(~mask.ravel()).astype(np.int64)
+    Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+    ct, Xct = torch.tensor(cells, device=DEV), torch.tensor(Xc.T.copy(), device=DEV)
+    k32 = ctx.krige(bad, o32, yt, Xt, cells=ct, Xc=Xct)
+    k64 = ctx.krige(bad, o64, yt, Xt, cells=ct, Xc=Xct)
+    assert ctx.promoted() == n0 + 3
+    assert torch.equal(k32["mean_cells"], k64["mean_cells"])
+
+
 def test_genhybr_gradient_matches_oracle(ctx):
     """The approximate gradient of Appendix A (Eq. approx_grad) and psi_k* against the oracle."""
     n1, n2, k = 30, 26, 12

@@ -13,8 +13,10 @@ large4096 (4096 x 4096 grid, ~30% missing in circular gaps, anisotropic
 exponential covariance) in its launch configuration: 32 probes x 80 steps with
 partial reorthogonalisation, CG on [y, X] to 1e-6, kriging means at every
 missing cell.  Checked against the oracle: the log-likelihood, log det, beta,
-every probe's quadrature value, and the kriging means at 2048 seeded missing
-cells (the oracle's own CG weights); K v entries from dense covariance rows.
+the quadrature values of the probes the oracle stores (the first 8; each fully
+reorthogonalised 80-step basis at this size takes ~20 GB of host memory), and
+the kriging means at 2048 seeded missing cells (the oracle's own CG weights);
+K v entries from dense covariance rows.
 
 The data of both are the oracle's (its circulant-embedding sampler on the
 seeded white noise).  Expected values: tests/golden/{search512,
@@ -199,8 +201,18 @@ def test_large4096_loglik_krige_match_oracle(large):
     res = ctx.loglik_krige(W5.cov, opts, yt, Xt, cells=torch.tensor(cells, device=DEV),
                            Xc=torch.tensor(Xc.T.copy(), device=DEV))
     assert res["status"] == kry.KRY_OK
-    e_ll = rel(res["loglik"], float(gold["loglik"]))
-    e_ld = rel(res["logdet"], float(gold["logdet"]))
+    # the oracle's log det and log-likelihood average the probes it stores (probe_ids, the
+    # first K of the workload's probes): the library's log-likelihood is compared with its own
+    # log det replaced by the mean of its values on those probes (l + logdet / 2 does not
+    # depend on the probes)
+    ids = gold["probe_ids"] if "probe_ids" in gold else np.arange(W5.nprobe)
+    emb = ctx.embed(W5.cov, kry.KRY_F32)
+    _, _, per = ctx.logdet(emb, W5.nprobe, W5.nsteps, W5.probe_seed, reorth=W5.reorth)
+    emb.free()
+    assert float(per.mean()) == pytest.approx(res["logdet"], rel=1e-12)
+    ld_sub = float(per[ids].mean())
+    e_ll = rel(res["loglik"] + 0.5 * res["logdet"] - 0.5 * ld_sub, float(gold["loglik"]))
+    e_ld = rel(ld_sub, float(gold["logdet"]))
     e_b = np.linalg.norm(res["beta"] - gold["beta"]) / np.linalg.norm(gold["beta"])
     # the stored cells are a seeded sample of the missing cells, in increasing order
     pos = np.searchsorted(cells, gold["cells"])
@@ -218,8 +230,9 @@ def test_large4096_every_probe_matches_oracle(large):
     emb = ctx.embed(W5.cov, kry.KRY_F32)
     _, _, per = ctx.logdet(emb, W5.nprobe, W5.nsteps, W5.probe_seed, reorth=W5.reorth)
     emb.free()
-    err = np.abs(per - gold["per_probe"]) / np.abs(gold["per_probe"])
-    print(f"large4096 per-probe vs oracle: max {err.max():.2e}")
+    ids = gold["probe_ids"] if "probe_ids" in gold else np.arange(W5.nprobe)
+    err = np.abs(per[ids] - gold["per_probe"]) / np.abs(gold["per_probe"])
+    print(f"large4096 per-probe vs oracle ({len(ids)} probes): max {err.max():.2e}")
     assert err.max() <= TOL_LOGDET
 
 
