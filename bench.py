@@ -38,7 +38,8 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "matvec_grid1024.md")
 KERNEL_SOURCES = ["paper_2012_13133_gb300/csrc/matvec.cu", "paper_2012_13133_gb300/csrc/fft.cuh",
                   "paper_2012_13133_gb300/csrc/fft16.cuh", "paper_2012_13133_gb300/csrc/fftspec.cuh",
                   "paper_2012_13133_gb300/csrc/mvspec.cuh", "paper_2012_13133_gb300/csrc/mvspec_a.cu",
-                  "paper_2012_13133_gb300/csrc/mvspec_b.cu", "paper_2012_13133_gb300/csrc/mvspec_c.cu"]
+                  "paper_2012_13133_gb300/csrc/mvspec_b.cu", "paper_2012_13133_gb300/csrc/mvspec_c.cu",
+                  "paper_2012_13133_gb300/csrc/kry_internal.cuh"]
 
 
 def kernel_hash():
@@ -88,19 +89,29 @@ def floor_bytes_per_vector(p):
 
 
 def read_traffic():
-    """(DRAM bytes per real vector, batch width it was measured at) of the
-    matvec from the committed ncu summary, if it was taken on the current
-    kernel sources; None otherwise."""
+    """[(real vectors per launch, DRAM bytes per launch), ...] of the matvec
+    from the committed ncu summary (one entry per captured batch width), if
+    it was taken on the current kernel sources; None otherwise."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
     m = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram_bytes_per_real_vector:\s*([0-9.eE+]+)", txt)
-    n = re.search(r"measured_vectors_per_launch:\s*([0-9]+)", txt)
-    if not m or not t or not n or m.group(1) != kernel_hash():
+    pts = [(int(a), float(b)) for a, b in re.findall(r"dram_bytes_per_launch_at_(\d+)_vectors:\s*([0-9.eE+]+)", txt)]
+    if not m or not pts or m.group(1) != kernel_hash():
         return None
-    return float(t.group(1)), int(n.group(1))
+    return sorted(pts)
+
+
+def traffic_at(points, nv):
+    """DRAM bytes per launch at nv real vectors per launch: linear through the
+    captured batch widths (a launch mix of two widths averages to the line at
+    its mean width), proportional to nv from a single capture."""
+    if len(points) == 1:
+        n0, b0 = points[0]
+        return b0 * nv / n0
+    (n0, b0), (n1, b1) = points[0], points[-1]
+    return b0 + (b1 - b0) * (nv - n0) / (n1 - n0)
 
 
 class ClockSampler:
@@ -328,14 +339,12 @@ def run_gpu(args, rank, world, local_rank):
         achieved = alg / (prof32["ms"] / 1000.0) / 1e9
         measured = read_traffic()
         per_launch_vectors = prof32["vectors"] / prof32["calls"]
-        # ncu traffic per launch scaled to this run's mean batch: the per-vector
-        # part (slab, vectors, indices) grows with the batch, the eigenvalues
-        # are read once per launch
+        # ncu traffic per launch at this run's mean batch, from the captures at
+        # the CG batch (4 vectors) and the Lanczos batch (64 vectors)
         lam_bytes = 4.0 * M1 * M2
         traffic = None
         if measured is not None:
-            per_vec, nv_meas = measured
-            traffic = round((per_vec - lam_bytes / nv_meas) * per_launch_vectors + lam_bytes)
+            traffic = round(traffic_at(measured, per_launch_vectors))
         floor = floor_bytes_per_vector(p) * prof32["vectors"] + lam_bytes * prof32["calls"]
         floor_gbs = floor / (prof32["ms"] / 1000.0) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

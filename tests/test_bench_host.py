@@ -35,11 +35,26 @@ def test_committed_ncu_traffic_matches_the_current_kernel_sources():
     t = bench.read_traffic()
     if t is None:
         pytest.skip("the committed ncu summary was taken on other kernel sources")
-    per_vec, nv = t
     w = I.WORKLOADS["grid1024"]
     model = bench.model_bytes_per_vector(w.n1, w.n2, 2 * w.n1, 2 * w.n2, 524288)
-    # the measured DRAM bytes stay within 25% of the model (no wholesale re-reads)
-    assert 0.75 * model <= per_vec <= 1.25 * model and nv >= 1
+    lam = 4.0 * (2 * w.n1) * (2 * w.n2)
+    for nv, b in t:
+        # the measured DRAM bytes stay within 25% of the model (no wholesale re-reads)
+        assert nv >= 1 and 0.75 * (model * nv + lam) <= b <= 1.25 * (model * nv + lam), (nv, b)
+    # the traffic at a captured width is the captured value, and it grows with the width
+    assert bench.traffic_at(t, t[0][0]) == pytest.approx(t[0][1])
+    assert bench.traffic_at(t, t[-1][0]) == pytest.approx(t[-1][1])
+    assert bench.traffic_at(t, 2 * t[-1][0]) > t[-1][1]
+
+
+def test_traffic_interpolation_between_two_batch_widths():
+    pts = [(4, 180.0), (64, 2480.0)]
+    assert bench.traffic_at(pts, 4) == 180.0 and bench.traffic_at(pts, 64) == 2480.0
+    # a launch mix of 4- and 64-vector launches: the mean traffic is the line at the mean width
+    mix = [4] * 9 + [64]
+    mean_nv = sum(mix) / len(mix)
+    assert bench.traffic_at(pts, mean_nv) == pytest.approx(sum(bench.traffic_at(pts, v) for v in mix) / len(mix))
+    assert bench.traffic_at([(64, 2560.0)], 32) == 1280.0
 
 
 def test_model_bytes_per_vector_of_the_grid1024_matvec():
