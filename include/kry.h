@@ -86,7 +86,7 @@ typedef struct {
  * reorthogonalised (as the paper runs it for its results, Sec. 3.2); 1 =
  * partial reorthogonalisation (Sec. 3.2 leaves a scheme to the user; see
  * kry_logdet), which keeps every basis vector on the device
- * (nprobe * nsteps * p values of the embedding's precision).  precond: 0 =
+ * (nprobe * nsteps * p values: FP16 for FP32 embeddings, FP64 otherwise).  precond: 0 =
  * plain CG; 1 = CG preconditioned by M^-1 = A (S + tau2 I)^-1 A^T, S the
  * circulant embedding of sigma2 Sigma on the matvec's torus (its inverse is
  * diagonal in the same FFT basis, so M^-1 costs one more FFT matvec per
@@ -219,9 +219,13 @@ kry_status kry_matvec_noalloc(kry_ctx* ctx, const kry_embed* e, const void* v_de
  * rounding term is that of the FFT matvec (unit roundoff x log2(M1 M2)) and,
  * when one exceeds sqrt(unit roundoff) of the embedding's precision, the new
  * basis vector and the next are orthogonalised against all earlier ones (a
- * second Gram-Schmidt pass when the first cancels most of the vector); the
- * result then follows the exact-arithmetic Gauss rule, which the plain FP32
- * recurrence misses by ~1e-3 on ill-conditioned K.  *logdet = mean over
+ * second Gram-Schmidt pass when the first cancels most of the vector; for
+ * FP32 embeddings the passes read an FP16 copy of the normalised basis, whose
+ * rounding leaves components of about 2 unit roundoffs); the result then
+ * follows the exact-arithmetic Gauss rule, which the plain FP32 recurrence
+ * misses by ~1e-3 on ill-conditioned K.  The quadrature nodes are taken as
+ * max(theta_j, tau2): every eigenvalue of K, and so every Ritz value of exact
+ * arithmetic, is at least tau2.  *logdet = mean over
  * probes, *stderr_out = standard error (NULL allowed), per_probe[nprobe] the
  * per-probe values (host, NULL allowed).  Synchronises the stream. */
 kry_status kry_logdet(kry_ctx* ctx, const kry_embed* e, int32_t nprobe, int32_t nsteps,

@@ -10,6 +10,7 @@
 // Vectors are FP32 (or FP64 for FP64 embeddings); every dot product is
 // accumulated in FP64 per block and reduced in a fixed order by one small
 // kernel, so results do not depend on scheduling.
+#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -228,6 +229,27 @@ __device__ __forceinline__ void store_vec(T* __restrict__ dst, const T (&in)[VW]
     }
 }
 
+// VW elements of the reorthogonalisation store as T: the store is T itself,
+// or FP16 (VW = 4: one 8-byte access).
+template <typename T, typename Sq, int VW>
+__device__ __forceinline__ void load_as(const Sq* __restrict__ src, T (&out)[VW]) {
+    if constexpr (std::is_same<Sq, T>::value) {
+        load_vec<T, VW>(src, out);
+    } else if constexpr (VW == 4) {
+        const uint2 q = *reinterpret_cast<const uint2*>(src);
+        __half2 h[2];
+        memcpy(h, &q, 8);
+        const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+        out[0] = (T)a.x;
+        out[1] = (T)a.y;
+        out[2] = (T)b.x;
+        out[3] = (T)b.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) out[e] = (T)__half2float(src[e]);
+    }
+}
+
 // ------------------------------------------------------------------ Lanczos
 
 #define KRY_MAX_STEPS 256
@@ -332,7 +354,10 @@ __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, 
 // exceeds sqrt(eps) (eps = unit roundoff of the vectors), the new vector and
 // the one after it are orthogonalised against every stored basis vector
 // (classical Gram-Schmidt, repeated once when it cancels most of the vector)
-// and their estimates reset to eps.  The rounding term uses
+// and their estimates reset to what the pass leaves: eps, or for FP32 vectors,
+// whose basis is stored in FP16 (2^-11 relative rounding, half the traffic of
+// an FP32 store), the FP16 rounding of a removed component of size sqrt(eps),
+// about 2 eps.  The rounding term uses
 // eps_round = eps log2(M1 M2): the local error of a step is that of the FFT
 // matvec, which grows with the log of the transform size.  With eps alone,
 // FP32 runs on smooth long-range covariances (512^2 grid, range >= 0.1)
@@ -345,7 +370,7 @@ __global__ void k_lanczos_beta(LanczosState S, const double* __restrict__ part, 
 // Estimates for q_{j+1} from ||w||^2 partials (before any reorthogonalisation);
 // sets flag[k] when w is to be reorthogonalised.
 __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int nblk, int nsteps, int j,
-                            double eps, double eps_round) {
+                            double eps, double eps_round, double omega_reset) {
     const int k = blockIdx.x;   // one block per vector
     const double s = block_sum(part + (int64_t)k * nblk, nblk);
     if (threadIdx.x != 0) return;
@@ -379,7 +404,7 @@ __global__ void k_pro_omega(LanczosState S, const double* __restrict__ part, int
     S.pre2[k] = s;
     S.force[k] = f && !S.force[k];   // the vector after a reorthogonalised one is reorthogonalised too
     if (f)
-        for (int i = 0; i <= j; ++i) on[i] = eps;
+        for (int i = 0; i <= j; ++i) on[i] = omega_reset;
 }
 
 // "Twice is enough" (Kahan; Parlett, The Symmetric Eigenvalue Problem, 1980,
@@ -396,14 +421,14 @@ __global__ void k_reorth_again(LanczosState S, const double* __restrict__ part, 
     S.pre2[k] = s;
 }
 
-// Partial dot products W_i^T w (i = 0..j) of each flagged vector, 8 basis
-// vectors per sweep over the block's slice of w, VW elements per access.
-// Products and per-thread sums are in the basis precision T (a coefficient only
-// needs a few correct digits: it removes a component of size <= sqrt(eps)), the
-// block sums in FP64.  dpart rows are [nvec][nsteps + 8][nblk]: a sweep's rows
+// Partial dot products W_i^T w (i = 0..j) of each flagged vector against the
+// basis store Q (T, or FP16 for FP32 vectors), 8 basis vectors per sweep over
+// the block's slice of w, VW elements per access.  Products and per-thread sums
+// are in the vector precision T (a coefficient only needs a few correct digits:
+// it removes a component of size <= sqrt(eps)), the block sums in FP64.  dpart rows are [nvec][nsteps + 8][nblk]: a sweep's rows
 // past j (zeros) stay in the vector's padding.
-template <typename T, int VW>
-__global__ void k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ Wn, int nvec, int64_t p, int j,
+template <typename T, typename Sq, int VW>
+__global__ void k_reorth_dots(const Sq* __restrict__ Q, const T* __restrict__ Wn, int nvec, int64_t p, int j,
                               const int* __restrict__ flag, int nsteps, double* __restrict__ dpart) {
     const int k = blockIdx.y;
     if (!flag[k]) return;
@@ -419,7 +444,7 @@ __global__ void k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ Wn,
             for (int a = 0; a < 8; ++a)
                 if (i0 + a <= j) {
                     T qv[VW];
-                    load_vec<T, VW>(Q + ((int64_t)(i0 + a) * nvec + k) * p + xv * VW, qv);
+                    load_as<T, Sq, VW>(Q + ((int64_t)(i0 + a) * nvec + k) * p + xv * VW, qv);
 #pragma unroll
                     for (int e = 0; e < VW; ++e) acc[a] += qv[e] * wv[e];
                 }
@@ -432,25 +457,53 @@ __global__ void k_reorth_dots(const T* __restrict__ Q, const T* __restrict__ Wn,
     }
 }
 
-// coef_i = s_i (q_i^T w) = s_i^2 (W_i^T w), summed over the partials in a fixed order.
-__global__ void k_reorth_coef(LanczosState S, const double* __restrict__ dpart, int nblk, int nsteps, int j) {
+// coef_i = s_i (q_i^T w) = s_i^2 (W_i^T w) for a store of the unnormalised W_i,
+// or (q_i^T w) / sqrt(p) = (H_i^T w) / p for the FP16 store H_i = sqrt(p) q_i
+// (hscale = 1 / p, else 0), summed over the partials in a fixed order.
+__global__ void k_reorth_coef(LanczosState S, const double* __restrict__ dpart, int nblk, int nsteps, int j,
+                              double hscale) {
     const int k = blockIdx.x;
     if (!S.flag[k]) return;
     for (int i = 0; i <= j; ++i) {
         const double d = block_sum(dpart + ((int64_t)k * (nsteps + 8) + i) * nblk, nblk);
         if (threadIdx.x == 0) {
             const double si = S.s_hist[(int64_t)k * nsteps + i];
-            S.coef[(int64_t)k * nsteps + i] = si * si * d;
+            S.coef[(int64_t)k * nsteps + i] = hscale > 0.0 ? hscale * d : si * si * d;
         }
         __syncthreads();
+    }
+}
+
+// H = FP16(sqrt(p) s_k W_k) for every vector k: the new basis vector,
+// normalised and scaled to entries of order one, for the reorthogonalisation
+// store.
+template <int VW>
+__global__ void k_store_half(const float* __restrict__ W, const double* __restrict__ s, double sqrtp,
+                             __half* __restrict__ H, int64_t p) {
+    const int k = blockIdx.y;
+    const float sc = (float)(s[k] * sqrtp);
+    const int64_t off = (int64_t)k * p;
+    const int64_t nv = p / VW;
+    for (int64_t xv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xv < nv; xv += (int64_t)gridDim.x * blockDim.x) {
+        float w[VW];
+        load_vec<float, VW>(W + off + xv * VW, w);
+        if constexpr (VW == 4) {
+            __half2 h[2] = {__floats2half2_rn(sc * w[0], sc * w[1]), __floats2half2_rn(sc * w[2], sc * w[3])};
+            uint2 q;
+            memcpy(&q, h, 8);
+            *reinterpret_cast<uint2*>(H + off + xv * VW) = q;
+        } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) H[off + xv * VW + e] = __float2half_rn(sc * w[e]);
+        }
     }
 }
 
 // w -= sum_i coef_i W_i (in the basis precision) for flagged vectors, VW
 // elements per access; partial ||w||^2 replaces the update's so that beta_j is
 // the norm after reorthogonalisation.
-template <typename T, int VW>
-__global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int nvec, int64_t p, int j,
+template <typename T, typename Sq, int VW>
+__global__ void k_reorth_apply(const Sq* __restrict__ Q, T* __restrict__ Wn, int nvec, int64_t p, int j,
                                LanczosState S, int nsteps, double* __restrict__ part) {
     const int k = blockIdx.y;
     if (!S.flag[k]) return;
@@ -467,7 +520,7 @@ __global__ void k_reorth_apply(const T* __restrict__ Q, T* __restrict__ Wn, int 
 #pragma unroll 4
         for (int i = 0; i <= j; ++i) {
             T qv[VW];
-            load_vec<T, VW>(Q + ((int64_t)i * nvec + k) * p + xv * VW, qv);
+            load_as<T, Sq, VW>(Q + ((int64_t)i * nvec + k) * p + xv * VW, qv);
 #pragma unroll
             for (int e = 0; e < VW; ++e) proj[e] += c[i] * qv[e];
         }
@@ -570,16 +623,27 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     const size_t vbytes = (size_t)nvec * p * sizeof(T);
     ctx->work[0].ensure(vbytes);
     T* U = ctx->work[0].as<T>();
-    T* Q = nullptr;   // basis store with reorthogonalisation
+    T* Q = nullptr;   // FP64 basis store with reorthogonalisation
     T* W[3] = {nullptr, nullptr, nullptr};
-    if (reorth) {
+    // FP32 with reorthogonalisation: the three-term recurrence runs on three
+    // rotating FP32 vectors, and every basis vector is also kept, normalised,
+    // in an FP16 store for the Gram-Schmidt passes (half the traffic and memory
+    // of an FP32 store; k_store_half)
+    const bool hstore = reorth && !dbl;
+    __half* H = nullptr;
+    if (reorth && dbl) {
         ctx->work[1].ensure(vbytes * nsteps);
         Q = ctx->work[1].as<T>();
+    } else if (hstore) {
+        ctx->work[1].ensure((size_t)nvec * p * sizeof(__half) * nsteps);
+        H = ctx->work[1].as<__half>();
+        ctx->work[2].ensure(3 * vbytes);
+        for (int b = 0; b < 3; ++b) W[b] = ctx->work[2].as<T>() + (size_t)b * nvec * p;
     } else {
         for (int b = 1; b < 4; ++b) ctx->work[b].ensure(vbytes);
         for (int b = 0; b < 3; ++b) W[b] = ctx->work[b + 1].as<T>();
     }
-    auto basis = [&](int i) -> T* { return reorth ? Q + (size_t)i * nvec * p : W[i % 3]; };
+    auto basis = [&](int i) -> T* { return Q ? Q + (size_t)i * nvec * p : W[i % 3]; };
     const int nred = std::max(nblkC, RED_BLOCKS);
     ctx->work[4].ensure((size_t)nvec * nred * sizeof(double));
     double* part = ctx->work[4].as<double>();
@@ -613,6 +677,10 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     // is dominated by the FFT matvec, whose error grows like log2 of the
     // transform size (eps log2(M1 M2) ||K||, not eps ||K||)
     const double eps_round = eps * std::log2((double)e->M1 * (double)e->M2);
+    // what a Gram-Schmidt pass leaves of q_i^T w: rounding of order eps, or, with
+    // the FP16 store, the FP16 rounding (2^-11) of a removed component of size
+    // up to sqrt(eps)
+    const double omega_reset = hstore ? std::max(eps, std::sqrt(eps) * 4.8828125e-4) : eps;
 
     const int tb = 256;
     k_lanczos_init<<<(nvec + tb - 1) / tb, tb, 0, ctx->stream>>>(S, nvec, nsteps, 1.0 / sqrt((double)p));
@@ -620,6 +688,48 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
     dim3 gp((unsigned)std::min<int64_t>((p + 255) / 256, 1024), nvec);
     k_probes<T><<<gp, 256, 0, ctx->stream>>>(basis(0), p, nprobe, seed);
     KRY_CHECK_LAUNCH();
+    constexpr int VW = 16 / sizeof(T);   // 16-byte accesses when every vector start is 16-byte aligned
+    const dim3 gu(RED_BLOCKS, nvec);
+    const double sqrtp = sqrt((double)p);
+    auto store_half = [&](int i) {   // H_i from basis(i) and its scale s_cur
+        if constexpr (sizeof(T) == 4) {
+            if (p % VW == 0)
+                k_store_half<VW><<<gu, 256, 0, ctx->stream>>>(basis(i), S.s_cur, sqrtp, H + (size_t)i * nvec * p, p);
+            else
+                k_store_half<1><<<gu, 256, 0, ctx->stream>>>(basis(i), S.s_cur, sqrtp, H + (size_t)i * nvec * p, p);
+            KRY_CHECK_LAUNCH();
+        }
+    };
+    // Gram-Schmidt dot products and update against the basis store
+    auto reorth_dots = [&](T* Wn, int j) {
+        if constexpr (sizeof(T) == 4) {
+            if (p % VW == 0)
+                k_reorth_dots<T, __half, VW><<<gu, 256, 0, ctx->stream>>>(H, Wn, nvec, p, j, S.flag, nsteps, dpart);
+            else
+                k_reorth_dots<T, __half, 1><<<gu, 256, 0, ctx->stream>>>(H, Wn, nvec, p, j, S.flag, nsteps, dpart);
+        } else {
+            if (p % VW == 0)
+                k_reorth_dots<T, T, VW><<<gu, 256, 0, ctx->stream>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+            else
+                k_reorth_dots<T, T, 1><<<gu, 256, 0, ctx->stream>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
+        }
+        KRY_CHECK_LAUNCH();
+    };
+    auto reorth_apply = [&](T* Wn, int j) {
+        if constexpr (sizeof(T) == 4) {
+            if (p % VW == 0)
+                k_reorth_apply<T, __half, VW><<<gu, 256, 0, ctx->stream>>>(H, Wn, nvec, p, j, S, nsteps, part);
+            else
+                k_reorth_apply<T, __half, 1><<<gu, 256, 0, ctx->stream>>>(H, Wn, nvec, p, j, S, nsteps, part);
+        } else {
+            if (p % VW == 0)
+                k_reorth_apply<T, T, VW><<<gu, 256, 0, ctx->stream>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+            else
+                k_reorth_apply<T, T, 1><<<gu, 256, 0, ctx->stream>>>(Q, Wn, nvec, p, j, S, nsteps, part);
+        }
+        KRY_CHECK_LAUNCH();
+    };
+    if (hstore) store_half(0);
     auto step = [&](int j) {
         cudaStream_t st = ctx->stream;
         T* Wc = basis(j);
@@ -629,43 +739,31 @@ static void lanczos_logdet(kry_ctx* ctx, const kry_embed* e, int nvec, int nprob
         KRY_CHECK_LAUNCH();
         if (j == nsteps - 1) return;
         T* Wn = basis(j + 1);
-        dim3 gu(RED_BLOCKS, nvec);
-        constexpr int VW = 16 / sizeof(T);   // 16-byte accesses when every vector start is 16-byte aligned
         if (p % VW == 0)
             k_lanczos_update<T, VW><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
         else
             k_lanczos_update<T, 1><<<gu, 256, 0, st>>>(U, Wc, Wp, Wn, p, S, nsteps, j, part);
         KRY_CHECK_LAUNCH();
         if (reorth) {
-            k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps, eps_round);
+            k_pro_omega<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nsteps, j, eps, eps_round, omega_reset);
             KRY_CHECK_LAUNCH();
-            if (p % VW == 0)
-                k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
-            else
-                k_reorth_dots<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
-            KRY_CHECK_LAUNCH();
+            reorth_dots(Wn, j);
             for (int pass = 0; pass < 2; ++pass) {
                 if (pass == 1) {
                     // second Gram-Schmidt pass for vectors that lost most of their norm
                     k_reorth_again<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS);
                     KRY_CHECK_LAUNCH();
-                    if (p % VW == 0)
-                        k_reorth_dots<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
-                    else
-                        k_reorth_dots<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S.flag, nsteps, dpart);
-                    KRY_CHECK_LAUNCH();
+                    reorth_dots(Wn, j);
                 }
-                k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j);
+                k_reorth_coef<<<nvec, FIN_THREADS, 0, st>>>(S, dpart, RED_BLOCKS, nsteps, j,
+                                                            hstore ? 1.0 / (double)p : 0.0);
                 KRY_CHECK_LAUNCH();
-                if (p % VW == 0)
-                    k_reorth_apply<T, VW><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
-                else
-                    k_reorth_apply<T, 1><<<gu, 256, 0, st>>>(Q, Wn, nvec, p, j, S, nsteps, part);
-                KRY_CHECK_LAUNCH();
+                reorth_apply(Wn, j);
             }
         }
         k_lanczos_beta<<<nvec, FIN_THREADS, 0, st>>>(S, part, RED_BLOCKS, nvec, nsteps, j);
         KRY_CHECK_LAUNCH();
+        if (hstore) store_half(j + 1);
     };
     step(0);
     if (nsteps > 1)

@@ -95,7 +95,7 @@ int64_t estimate_bytes(const kry_request& r, int64_t p) {
     b += 3 * (int64_t)nc * p * 8 + (N + p) * 8;    // [y, X], solutions, kriging grid
     if (r.opts.precond) b += 16 * MM + (int64_t)nc * p * 4;   // preconditioner eigenvalues, z vectors
     if (r.kind == KRY_REQ_LOGLIK && r.opts.reorth)   // stored Lanczos basis
-        b += (int64_t)r.opts.nprobe * r.opts.nsteps * p * es;
+        b += (int64_t)r.opts.nprobe * r.opts.nsteps * p * (es == 4 ? 2 : 8) + 3 * vecs * p * es;   // FP16 store in FP32
     b += N + p * 8 * (1 + r.ncov) + (N - p) * 8 * (2 + r.ncov);   // inputs and outputs
     return b + b / 4 + (64 << 20);
 }
