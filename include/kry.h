@@ -63,7 +63,9 @@ typedef enum {
     KRY_EUNSUPPORTED = 8  /* valid request outside the supported sizes */
 } kry_status;
 
-typedef enum { KRY_F32 = 0, KRY_F64 = 1 } kry_prec;
+/* KRY_AUTO (kry_opts only; embeddings take KRY_F32 or KRY_F64): FP32 for each
+ * covariance setting FP32 resolves, FP64 for the others (see kry_opts). */
+typedef enum { KRY_F32 = 0, KRY_F64 = 1, KRY_AUTO = 2 } kry_prec;
 
 /* Regular grid on the unit square (Sec. 4 layout): n1 x n2 cells of size dx1 x dx2. */
 typedef struct {
@@ -99,13 +101,17 @@ typedef struct {
  * (kry_mask_interior; on 512^2 masks that is where the preconditioned solve
  * was the faster one).  The result does not depend on it beyond the CG
  * tolerance.
- * prec = KRY_F32 in kry_profile_loglik, kry_krige, kry_loglik_krige and
- * kry_bootstrap_var: FP32 vectors and matvecs with FP64 scalars, for each
- * covariance setting whose conditioning FP32 resolves, kappa = (max |Lambda|
- * + tau2) / tau2 <= 4e6 (every eigenvalue of K lies in [tau2, max |Lambda| +
- * tau2]; FP32 CG stalls as kappa u32 nears one, u32 = 2^-24).  A setting
- * above that bound, or with tau2 = 0, runs in FP64 instead, alone
- * (kry_promoted counts them).  In FP32 the log-determinant wants reorth = 1:
+ * prec: KRY_F32 runs FP32 vectors and matvecs with FP64 scalars (CG
+ * convergence is still judged on the FP64 true residual, and a solve that
+ * stalls returns KRY_ENOCONV); KRY_F64 runs FP64 throughout.  KRY_AUTO, in
+ * kry_profile_loglik, kry_krige, kry_loglik_krige and kry_bootstrap_var,
+ * runs FP32 for each covariance setting whose conditioning FP32 resolves,
+ * kappa = (max |Lambda| + tau2) / tau2 <= 4e6 (every eigenvalue of K lies in
+ * [tau2, max |Lambda| + tau2]; FP32 CG stalls as kappa u32 nears one, u32 =
+ * 2^-24), and FP64 for a setting above that bound or with tau2 = 0, alone
+ * (kry_promoted counts them).  FP64 costs far more on large ill-conditioned
+ * grids: a 2000-request serving stream that took 615 s on one slot in FP32
+ * took 2418 s with KRY_AUTO.  In FP32 the log-determinant wants reorth = 1:
  * without it the FP32 quadrature drifts as kappa grows (measured 8.6e-4
  * relative at kappa 3.3e5 on a 1024^2 grid, 5.6e-3 on 256^2 with the same
  * range in cells), while with it, or in FP64 either way, it stays within
@@ -143,7 +149,7 @@ kry_status kry_set_mask(kry_ctx* ctx, const kry_grid* grid, const uint8_t* mask_
  * kry_opts.precond = 2.  (No counterpart in the paper.) */
 kry_status kry_mask_interior(kry_ctx* ctx, double* interior);
 
-/* Number of covariance settings that calls on ctx asked for in FP32 and ran in
+/* Number of covariance settings that calls on ctx with prec = KRY_AUTO ran in
  * FP64 because FP32 would not resolve their conditioning (kry_opts, prec),
  * counted since kry_create. */
 kry_status kry_promoted(kry_ctx* ctx, int64_t* count);

@@ -28,8 +28,8 @@
 // 1024^2 (relative residual 1.6e-4) and 1.3e7 on 2048^2 (0.57).  The FP32
 // log-det with partial reorthogonalisation stayed within 1.2e-5 of the FP64
 // one throughout.  Above 4e6 (kappa u32 = 0.24), likelihood, kriging and
-// bootstrap calls asked for in FP32 run that setting in FP64 instead (counted
-// by kry_promoted).
+// bootstrap calls with prec = KRY_AUTO run that setting in FP64 instead of
+// FP32 (counted by kry_promoted).
 #define KRY_F32_KAPPA_MAX 4.0e6
 
 namespace kry {
@@ -272,8 +272,8 @@ static bool f32_resolves(double lam_lo, double lam_hi, double tau2) {
     return tau2 > 0.0 && (lmax + tau2) / tau2 <= KRY_F32_KAPPA_MAX;
 }
 
-// promote: an FP32 request whose conditioning FP32 cannot resolve gets an FP64
-// embedding (and counts in ctx->promoted).
+// promote (prec = KRY_AUTO in kry_opts): an FP32 request whose conditioning
+// FP32 cannot resolve gets an FP64 embedding (and counts in ctx->promoted).
 static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, bool promote = false) {
     check_cov(cov);
     require_mask(ctx);
@@ -308,6 +308,13 @@ static kry_embed* make_embed(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, bo
         throw;
     }
     return e;
+}
+
+// The precision a kry_opts call starts from (KRY_AUTO starts from FP32), and
+// its embedding: KRY_AUTO promotes a setting FP32 does not resolve to FP64.
+static kry_prec base_prec(const kry_opts* o) { return o->prec == KRY_AUTO ? KRY_F32 : o->prec; }
+static kry_embed* make_embed_opts(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o) {
+    return make_embed(ctx, cov, base_prec(o), o->prec == KRY_AUTO);
 }
 
 // CG preconditioner for one covariance setting (kry_opts.precond) of a solve
@@ -678,7 +685,7 @@ kry_status kry_solve_pre(kry_ctx* ctx, const kry_embed* e, const double* B_dev, 
 static void check_opts(const kry_opts* o) {
     KRY_REQUIRE(o != nullptr && o->precond >= 0 && o->precond <= 2, KRY_EINVAL, "opts->precond must be 0, 1 or 2");
     KRY_REQUIRE(o != nullptr, KRY_EINVAL, "opts is NULL");
-    KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64, KRY_EINVAL, "opts->prec invalid");
+    KRY_REQUIRE(o->prec == KRY_F32 || o->prec == KRY_F64 || o->prec == KRY_AUTO, KRY_EINVAL, "opts->prec invalid");
     KRY_REQUIRE(o->nprobe >= 1 && o->nsteps >= 1, KRY_EINVAL, "need nprobe >= 1 and nsteps >= 1");
     KRY_REQUIRE(o->rtol > 0 && o->maxit >= 1, KRY_EINVAL, "need rtol > 0 and maxit >= 1");
     KRY_REQUIRE(o->reorth == 0 || o->reorth == 1, KRY_EINVAL, "opts->reorth must be 0 or 1");
@@ -732,7 +739,7 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
             std::vector<int> in_batch, alone;
             for (int t = 0; t < ntheta; ++t) {
                 bool ok = true;
-                if (batched && opts->prec == KRY_F32) {
+                if (batched && opts->prec == KRY_AUTO) {
                     double lo, hi;
                     kry::compute_eigs(ctx, thetas[t], ctx->n1, ctx->n2, ctx->dx1, ctx->dx2,
                                       pow2_at_least(2 * (int64_t)ctx->n1), pow2_at_least(2 * (int64_t)ctx->n2), &lo,
@@ -750,8 +757,8 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
             const int ng = (int)gi.size();
             std::vector<kry_cov> th(ng);
             for (int t = 0; t < ng; ++t) th[t] = thetas[gi[t]];
-            kry_embed* e = (ng > 1) ? make_embed_batch(ctx, th.data(), ng, opts->prec)
-                                    : make_embed(ctx, &th[0], opts->prec, true);
+            kry_embed* e = (ng > 1) ? make_embed_batch(ctx, th.data(), ng, base_prec(opts))
+                                    : make_embed_opts(ctx, &th[0], opts);
             try {
                 // log-determinants: ng settings x nprobe probes in one batched Lanczos
                 std::vector<double> vals((size_t)ng * opts->nprobe);
@@ -874,7 +881,7 @@ kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts, con
         check_cov(cov);
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
                          mean_cells_dev, mean_sites_dev, var_cells_dev);
-        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
+        kry_embed* e = make_embed_opts(ctx, cov, opts);
         kry_status st = KRY_OK;
         try {
             double *V, *Z;
@@ -905,7 +912,7 @@ kry_status kry_loglik_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* op
         KRY_REQUIRE(loglik != nullptr, KRY_EINVAL, "loglik must not be NULL");
         check_krige_args(ctx, y_dev, X_dev, ncov, cells_dev, Xc_dev, ncell, sites_dev, Xs_dev, nsite,
                          mean_cells_dev, mean_sites_dev, var_cells_dev);
-        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
+        kry_embed* e = make_embed_opts(ctx, cov, opts);
         kry_status st = KRY_OK;
         try {
             std::vector<double> vals(opts->nprobe);
@@ -1025,7 +1032,7 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
         for (int b = 0; b < nrep; ++b)
             kry::sample_field(ctx, *cov, M1, M2, xi_dev + (size_t)b * 2 * M1 * M2, G + (size_t)b * N);
         kry::boot_rhs(ctx, G, N, eps_dev, sqrt(cov->tau2), R, nrep);
-        kry_embed* e = make_embed(ctx, cov, opts->prec, true);
+        kry_embed* e = make_embed_opts(ctx, cov, opts);
         kry::SolveInfo si;
         try {
             kry_embed* pre = make_precond_embed(ctx, cov, opts, e->prec, 1);

@@ -82,11 +82,11 @@ int64_t estimate_bytes(const kry_request& r, int64_t p) {
     const int64_t MM = M1 * M2;
     const int nc = r.ncov + 1 + ((r.ncov + 1) & 1);
     const int64_t vecs = (r.kind == KRY_REQ_LOGLIK) ? std::max(r.opts.nprobe, nc) : nc;
-    // bytes per vector element: FP64 requests, and FP32 ones that will run in FP64
-    // for want of a nugget (an FP32 request promoted for its conditioning, kappa >
-    // 4e6, needs up to twice the vector memory counted here: the budget is meant
-    // to stay well below the device's memory)
-    const int64_t es = (r.opts.prec == KRY_F64 || !(r.cov.tau2 > 0.0)) ? 8 : 4;
+    // bytes per vector element: FP64 requests, and KRY_AUTO ones that will run in
+    // FP64 for want of a nugget (a KRY_AUTO request promoted for its
+    // conditioning, kappa > 4e6, needs up to twice the vector memory counted
+    // here: the budget is meant to stay well below the device's memory)
+    const int64_t es = (r.opts.prec == KRY_F64 || (r.opts.prec == KRY_AUTO && !(r.cov.tau2 > 0.0))) ? 8 : 4;
     int64_t b = 0;
     b += 36 * MM;                                  // eigenvalues (FP64 + FP32) and eigen scratch
     b += (int64_t)r.n1 * M2 * 2 * es * ((vecs + 1) / 2);   // Krylov slab

@@ -176,7 +176,8 @@ def main():
     if args.objective == "paper":
         res = fit_paper(ctx, yt, Xt, start, np.zeros(X.shape[1]), k=args.k)
     else:
-        opts = kry.Opts(prec=kry.KRY_F32, nprobe=16, nsteps=40, seed=w.probe_seed, rtol=1e-8, maxit=20000,
+        # FP32 where it resolves K, FP64 for settings the trajectory reaches that it does not
+        opts = kry.Opts(prec=kry.KRY_AUTO, nprobe=16, nsteps=40, seed=w.probe_seed, rtol=1e-8, maxit=20000,
                         reorth=1)
         res = fit_marginal(ctx, yt, Xt, start, opts)
     torch.cuda.synchronize()

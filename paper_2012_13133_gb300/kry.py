@@ -21,6 +21,7 @@ KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ENOTPSD, KRY_ENOCONV, KRY_ENAN, KRY_ETIMEOUT
 STATUS_NAMES = ["KRY_OK", "KRY_EINVAL", "KRY_ENOMEM", "KRY_ENOTPSD", "KRY_ENOCONV", "KRY_ENAN", "KRY_ETIMEOUT",
                 "KRY_ECUDA", "KRY_EUNSUPPORTED"]
 KRY_F32, KRY_F64 = 0, 1
+KRY_AUTO = 2   # kry_opts only: FP32 where it resolves K, FP64 for the other settings
 
 
 class KryError(RuntimeError):

@@ -67,7 +67,7 @@ def test_binding_structs_and_enums_match_the_header(libpath, tmp_path):
         lines.append(f'printf("{s} size %zu\\n", sizeof({s}));')
         for f in fields:
             lines.append(f'printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
-    enums = [n for n in kry.STATUS_NAMES] + ["KRY_F32", "KRY_F64"]
+    enums = [n for n in kry.STATUS_NAMES] + ["KRY_F32", "KRY_F64", "KRY_AUTO"]
     for e in enums:
         lines.append(f'printf("enum {e} %d\\n", (int){e});')
     lines += ["return 0;", "}"]
@@ -88,6 +88,7 @@ def test_binding_structs_and_enums_match_the_header(libpath, tmp_path):
     for i, e in enumerate(kry.STATUS_NAMES):
         assert got[("enum", e)] == i, e
     assert got[("enum", "KRY_F32")] == kry.KRY_F32 and got[("enum", "KRY_F64")] == kry.KRY_F64
+    assert got[("enum", "KRY_AUTO")] == kry.KRY_AUTO
 
 
 def test_binding_refuses_host_and_strided_tensors(libpath):

@@ -570,11 +570,12 @@ def test_genhybr_fp32_matches_oracle(ctx, n1, n2, cov, k, kind):
     assert ei.value.status == kry.KRY_EINVAL
 
 
-def test_fp32_requests_run_ill_conditioned_settings_in_fp64(ctx):
-    """An FP32 likelihood or kriging request runs a covariance setting in FP64 when FP32 cannot
-    resolve its conditioning, kappa = (max |Lambda| + tau2) / tau2 > 4e6 (kry_opts): its results are
-    those of the FP64 request bit for bit, kry_promoted counts it, and in a batched search the other
-    settings keep their FP32 batch.  A setting below the bound stays in FP32."""
+def test_auto_precision_runs_ill_conditioned_settings_in_fp64(ctx):
+    """A likelihood or kriging request with prec = KRY_AUTO runs a covariance setting in FP64 when
+    FP32 cannot resolve its conditioning, kappa = (max |Lambda| + tau2) / tau2 > 4e6 (kry_opts): its
+    results are those of the FP64 request bit for bit, kry_promoted counts it, and in a batched
+    search the other settings keep their FP32 batch.  A setting below the bound stays in FP32, and
+    prec = KRY_F32 stays in FP32 whatever the setting."""
     n = 64
     mask = make_mask(n, n, 0.5, "uniform")
     p = set_mask(ctx, mask)
@@ -586,14 +587,21 @@ def test_fp32_requests_run_ill_conditioned_settings_in_fp64(ctx):
     X = I.covariates(S1[mask], S2[mask])
     y = X @ np.array([1.0, 0.5, -0.5]) + I.normals(p, 17)
     yt, Xt = torch.tensor(y, device=DEV), torch.tensor(X.T.copy(), device=DEV)
-    o32 = kry.Opts(prec=kry.KRY_F32, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
+    o32 = kry.Opts(prec=kry.KRY_AUTO, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
     o64 = kry.Opts(prec=kry.KRY_F64, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
+    of32 = kry.Opts(prec=kry.KRY_F32, nprobe=8, nsteps=30, seed=5, rtol=1e-7, maxit=20000, reorth=1)
     n0 = ctx.promoted()
+    try:   # explicit FP32 is not promoted (its CG may stop short of rtol at this conditioning)
+        ld_f32 = ctx.profile_loglik(yt, Xt, [bad], of32)["logdet"][0]
+    except kry.KryError:
+        ld_f32 = None
+    assert ctx.promoted() == n0
     r32 = ctx.profile_loglik(yt, Xt, [bad], o32)
     assert ctx.promoted() == n0 + 1
     r64 = ctx.profile_loglik(yt, Xt, [bad], o64)
     assert r32["status"] == r64["status"] == kry.KRY_OK
     assert r32["loglik"][0] == r64["loglik"][0] and r32["logdet"][0] == r64["logdet"][0]
+    assert ld_f32 is None or ld_f32 != r64["logdet"][0]
     g32 = ctx.profile_loglik(yt, Xt, [good], o32)
     g64 = ctx.profile_loglik(yt, Xt, [good], o64)
     assert ctx.promoted() == n0 + 1
