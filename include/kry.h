@@ -286,8 +286,9 @@ kry_status kry_profile_loglik(kry_ctx* ctx, const double* y_dev, const double* X
  * cells_dev: ncell int64 row-major cell indices; Xc_dev: ncell x ncov FP64
  * column-major; sites_dev: nsite x 2 FP64 row-major coordinates; Xs_dev: nsite x
  * ncov.  Outputs (device, FP64): mean_cells_dev[ncell], mean_sites_dev[nsite],
- * var_cells_dev[ncell] (NULL skips the variances).  beta_out (host, ncov, may be
- * NULL).  Synchronises the stream. */
+ * var_cells_dev[ncell] (NULL skips the variances; their solves K^-1 c_t run 32
+ * targets at a time, preconditioned as the [y, X] solve when opts->precond
+ * applies).  beta_out (host, ncov, may be NULL).  Synchronises the stream. */
 kry_status kry_krige(kry_ctx* ctx, const kry_cov* cov, const kry_opts* opts,
                      const double* y_dev, const double* X_dev, int32_t ncov,
                      const int64_t* cells_dev, const double* Xc_dev, int64_t ncell,

@@ -49,7 +49,7 @@ void krige_launch_cells(kry_ctx* ctx, const double* grid, const int64_t* cells, 
 void krige_launch_sites(kry_ctx* ctx, const kry_cov& cov, const double* sites, int64_t nsite, const double* Xs,
                         int ncov, const double* beta_dev, const double* w, double* mean);
 bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
-                     double rtol, int maxit);
+                     double rtol, int maxit, const kry_embed* pre);
 }  // namespace kry
 
 std::atomic<unsigned long long> g_kry_launches{0};
@@ -843,8 +843,17 @@ static kry_status krige_from_solution(kry_ctx* ctx, kry_embed* e, const kry_cov&
     }
     kry::krige_launch_sites(ctx, cov, sites_dev, nsite, Xs_dev, ncov, bdev, w, mean_sites_dev);
     bool vok = true;
-    if (var_cells_dev && ncell > 0)
-        vok = kry::krige_variances(ctx, e, cells_dev, ncell, var_cells_dev, opts->rtol, opts->maxit);
+    if (var_cells_dev && ncell > 0) {
+        // the targets' cross-covariance solves, preconditioned like [y, X] when opts asks for it
+        kry_embed* pre = make_precond_embed(ctx, &cov, opts, e->prec, 1);
+        try {
+            vok = kry::krige_variances(ctx, e, cells_dev, ncell, var_cells_dev, opts->rtol, opts->maxit, pre);
+        } catch (...) {
+            free_embed(pre);
+            throw;
+        }
+        free_embed(pre);
+    }
     int* hbad = reinterpret_cast<int*>(ctx->host_pinned);
     KRY_CUDA(cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     KRY_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -1715,7 +1715,7 @@ void resid_weights(kry_ctx* ctx, const double* Z, int ncov, const double* beta_d
 
 // Simple-kriging variances at target cells, nb targets per batch of solves.
 bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int64_t ncell, double* var,
-                     double rtol, int maxit) {
+                     double rtol, int maxit, const kry_embed* pre) {
     const int64_t p = ctx->p;
     cudaStream_t st = ctx->stream;
     const int nb = 32;
@@ -1731,7 +1731,7 @@ bool krige_variances(kry_ctx* ctx, const kry_embed* e, const int64_t* cells, int
         k_cross_cols<<<g, 256, 0, st>>>(cells, t0, ctx->cellidx.as<int>(), p, ctx->n2, (int64_t)ctx->n1 * ctx->n2, cp,
                                          cbuf.as<double>());
         KRY_CHECK_LAUNCH();
-        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit, 0);
+        SolveInfo si = solve(ctx, e, cbuf.as<double>(), p, sbuf.as<double>(), p, k, rtol, maxit, 0, pre);
         ok = ok && si.converged;
         k_var_final<<<k, 256, 0, st>>>(cbuf.as<double>(), sbuf.as<double>(), p, e->cov.sigma2, var, t0);
         KRY_CHECK_LAUNCH();

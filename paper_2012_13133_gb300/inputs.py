@@ -139,6 +139,14 @@ def mask_mixed(n1: int, n2: int, frac_missing: float, seed: int):
     return m
 
 
+def variance_cells(w: Workload, mask):
+    """The workload's kriging-variance targets: n_var_cells of the unobserved cells, a seeded
+    choice (var_seed), as sorted flat row-major indices."""
+    miss = np.flatnonzero(~np.asarray(mask, bool).ravel())
+    k = min(int(w.extra["n_var_cells"]), miss.size)
+    return np.sort(np.random.default_rng(w.extra["var_seed"]).choice(miss, k, replace=False)).astype(np.int64)
+
+
 def make_mask(w: Workload):
     if w.mask == "full":
         return mask_full(w.n1, w.n2)

@@ -64,6 +64,8 @@ def main():
     ap.add_argument("--bootstrap", type=int, default=0,
                     help="time the parametric-bootstrap kriging MSE with this many replicates at all missing cells")
     ap.add_argument("--precond", type=int, default=0, help="kry_opts.precond for the CG solves (1: torus inverse)")
+    ap.add_argument("--variances", type=int, default=0,
+                    help="time exact simple-kriging variances at the first K of the workload's variance cells")
     ap.add_argument("--solves", action="store_true",
                     help="time CG on [y, X] with and without the torus-inverse preconditioner")
     args = ap.parse_args()
@@ -77,6 +79,21 @@ def main():
         ctx.genhybr(w.cov, b, 2)
         g, t = timed(lambda: ctx.genhybr(w.cov, b, args.genhybr))
         out.update({"k": args.genhybr, "genhybr_s": t, "pl": g["pl"], "z2": g["z2"], "psi2": g["psi2"]})
+    elif args.variances:
+        cells = I.variance_cells(w, mask)[:args.variances]
+        Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])
+        opts = kry.Opts(prec=kry.KRY_F32, rtol=w.cg_tol, maxit=30000, precond=args.precond)
+        ct, xt = torch.tensor(cells, device=dev), torch.tensor(Xc.T.copy(), device=dev)
+        emb = ctx.embed(w.cov, kry.KRY_F32)
+        ctx.autotune(emb, 4)
+        ctx.autotune(emb, 32)
+        emb.free()
+        res, t = timed(lambda: ctx.krige(w.cov, opts, y, X, cells=ct, Xc=xt, variances=True))
+        v = res["var_cells"].cpu().numpy()
+        n_all = int(w.extra.get("n_var_cells", cells.size))
+        out.update({"variance_cells": int(cells.size), "krige_with_variances_s": t, "status": int(res["status"]),
+                    "precond": args.precond, "mean_var": float(v.mean()), "min_var": float(v.min()),
+                    "max_var": float(v.max()), "of_cells": n_all})
     elif args.bootstrap:
         nrep = args.bootstrap
         M1, M2, _ = ctx.sample_size(w.cov)

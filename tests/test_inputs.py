@@ -80,3 +80,19 @@ def test_data_noise_is_seeded_and_shaped():
     xi2, eps2 = I.data_noise(8, 16, 10, 3)
     assert np.array_equal(xi, xi2) and np.array_equal(eps, eps2)
     assert not np.array_equal(eps, I.normals(10, 3))       # the nugget noise is a separate stream
+
+
+def test_variance_cells_are_a_seeded_sorted_choice_of_missing_cells():
+    w = I.WORKLOADS["large4096"]
+    n = 64
+    mask = np.ones((n, n), bool)
+    mask[10:30, 10:40] = False
+    small = I.Workload("v", n, n, w.cov, "full", 0.0, 0, 0, extra={"n_var_cells": 100, "var_seed": 6})
+    c1 = I.variance_cells(small, mask)
+    c2 = I.variance_cells(small, mask)
+    assert np.array_equal(c1, c2) and c1.dtype == np.int64 and c1.size == 100
+    assert np.all(np.diff(c1) > 0) and not mask.ravel()[c1].any()
+    # fewer missing cells than asked for: all of them
+    mask[:] = True
+    mask[0, :5] = False
+    assert np.array_equal(I.variance_cells(small, mask), np.arange(5))
