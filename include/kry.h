@@ -365,12 +365,17 @@ kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, in
  * against the FP64 oracle, pl agrees to 4e-5 (40 x 36 grid, k = 15), 4e-7
  * (128^2, k = 30) and 8e-4 (1024^2, k = 50), and with the FP64 path to
  * 1.1e-4 at 4096^2 (k = 50), where it runs 6.6 times faster (0.18 s vs
- * 1.17 s).  Library scratch: (2k + 6) n1 n2 floats (FP32) or doubles
- * (FP64).  Arguments, outputs and errors as for kry_genhybr, plus
- * KRY_EINVAL for another prec.  Synchronises the stream. */
-kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, const double* b_dev, int32_t k,
-                            double* x_dev, double* alphas, double* betas, double* z2, double* psi2, double* pl,
-                            double* grad, double* psi_dev);
+ * 1.17 s).  reorth = 1 (beyond the paper) reorthogonalises each new u
+ * against u_1..u_i (Euclidean, U^T U = tau2 I) and each new w against
+ * v_1..v_i (Sigma inner product, through the stored Sigma v_j), by two
+ * classical Gram-Schmidt passes, which keeps the recurrence on the exact
+ * bidiagonal at O(k^2 n) extra work and (k + 1) n1 n2 more scratch.
+ * Library scratch: (2k + 6) n1 n2 floats (FP32) or doubles (FP64), (3k + 7)
+ * with reorth.  Arguments, outputs and errors as for kry_genhybr, plus
+ * KRY_EINVAL for another prec or reorth.  Synchronises the stream. */
+kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, int32_t reorth, const double* b_dev,
+                            int32_t k, double* x_dev, double* alphas, double* betas, double* z2, double* psi2,
+                            double* pl, double* grad, double* psi_dev);
 
 /* Parametric-bootstrap MSE of the kriging prediction of the latent field at
  * grid cells (Sec. 3.5, Eq. bootstrap_uq), theta and beta known: replicate b

@@ -1068,17 +1068,18 @@ kry_status kry_bootstrap_var(kry_ctx* ctx, const kry_cov* cov, const kry_opts* o
     });
 }
 
-kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, const double* b_dev, int32_t k,
-                            double* x_dev, double* alphas, double* betas, double* z2, double* psi2, double* pl,
-                            double* grad, double* psi_dev) {
+kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, int32_t reorth, const double* b_dev,
+                            int32_t k, double* x_dev, double* alphas, double* betas, double* z2, double* psi2,
+                            double* pl, double* grad, double* psi_dev) {
     return guarded(ctx, [&]() -> kry_status {
         check_cov(cov);
         require_mask(ctx);
         KRY_REQUIRE(prec == KRY_F32 || prec == KRY_F64, KRY_EINVAL, "prec must be KRY_F32 or KRY_F64");
+        KRY_REQUIRE(reorth == 0 || reorth == 1, KRY_EINVAL, "reorth must be 0 or 1");
         KRY_REQUIRE(!ctx->sites.active, KRY_EUNSUPPORTED, "genHyBR needs an observation mask (kry_set_mask)");
         KRY_REQUIRE(b_dev != nullptr, KRY_EINVAL, "b_dev must not be NULL");
         KRY_REQUIRE(k >= 1 && k <= 4096, KRY_EINVAL, "k must be in [1, 4096]");
-        kry::genhybr(ctx, *cov, prec, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
+        kry::genhybr(ctx, *cov, prec, reorth != 0, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
         return KRY_OK;
     });
 }
@@ -1086,7 +1087,7 @@ kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, con
 kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, int32_t k, double* x_dev,
                        double* alphas, double* betas, double* z2, double* psi2, double* pl, double* grad,
                        double* psi_dev) {
-    return kry_genhybr_prec(ctx, cov, KRY_F64, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
+    return kry_genhybr_prec(ctx, cov, KRY_F64, 0, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
 }
 
 kry_status kry_bccb_logdet(kry_ctx* ctx, const kry_cov* cov, double* logdet, double* dlogdet_drange) {

@@ -118,7 +118,52 @@ __global__ void k_gk_combine(const T* __restrict__ V, const double* __restrict__
     }
 }
 
+// Reorthogonalisation (optional; the paper runs Alg. 1 without it): the new u
+// against U (Euclidean, U^T U = tau^2 I) and the new w against V (Sigma inner
+// product, V^T Sigma V = I, through the stored Sigma V), two classical
+// Gram-Schmidt passes each.
+//   part[j][b] = block b's FP64 partial of A_j^T x (j < m; A_j = A + j stride)
+template <typename T>
+__global__ void k_mdot(const T* __restrict__ A, int64_t stride, int m, const T* __restrict__ x, int64_t n,
+                       double* __restrict__ part) {
+    __shared__ double sh[256];
+    for (int j = 0; j < m; ++j) {
+        double s = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            s += (double)A[(int64_t)j * stride + i] * (double)x[i];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = sh[0];
+        __syncthreads();
+    }
+}
+
+//   c[j] = scale * sum_b part[j][b]  (one thread per j, fixed order)
+__global__ void k_mdot_finish(const double* __restrict__ part, int nb, int m, double scale, double* __restrict__ c) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)j * nb + b];
+    c[j] = scale * s;
+}
+
+//   x -= sum_j c[j] B_j  (FP64 accumulation, j in a fixed order)
+template <typename T>
+__global__ void k_maxpy(const T* __restrict__ B, int64_t stride, int m, const double* __restrict__ c,
+                        T* __restrict__ x, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += c[j] * (double)B[(int64_t)j * stride + i];
+        x[i] = (T)((double)x[i] - s);
+    }
+}
+
 const int NB = 256;
+const int NBR = 128;   // blocks of k_mdot
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
 
@@ -152,9 +197,24 @@ double sigma_full(kry_ctx* ctx, const kry_embed* e, const T* w, T* sw, double* d
 
 namespace {
 
+// x -= B (scale A^T x), twice (classical Gram-Schmidt, repeated), for the m
+// columns of A and B (stride apart); part and c are FP64 scratch of m NBR and m.
 template <typename T>
-void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double* x_out, double* alphas, double* betas,
-               double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+void project_out(kry_ctx* ctx, const T* A, const T* B, int64_t stride, int m, double scale, T* x, int64_t n,
+                 double* part, double* c) {
+    for (int pass = 0; pass < 2; ++pass) {
+        k_mdot<T><<<NBR, 256, 0, ctx->stream>>>(A, stride, m, x, n, part);
+        KRY_CHECK_LAUNCH();
+        k_mdot_finish<<<(m + 127) / 128, 128, 0, ctx->stream>>>(part, NBR, m, scale, c);
+        KRY_CHECK_LAUNCH();
+        k_maxpy<T><<<grid_for(n), 256, 0, ctx->stream>>>(B, stride, m, c, x, n);
+        KRY_CHECK_LAUNCH();
+    }
+}
+
+template <typename T>
+void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, bool reorth, double* x_out, double* alphas,
+               double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
     constexpr kry_prec prec = sizeof(T) == 8 ? KRY_F64 : KRY_F32;
     const int n1 = ctx->n1, n2 = ctx->n2;
     const int64_t N = (int64_t)n1 * n2, p = ctx->p;
@@ -175,20 +235,29 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
     corr.sigma2 = 1.0;
     corr.tau2 = 0.0;
     const double tau2 = cov.tau2, tau = sqrt(tau2);
-    // scratch: partials, pass C partials (at most 8192), k coefficients (FP64);
-    // then V [k+1][N], SV, W, X (whole grid) and U [k+1][p], T (observed) as T
+    // scratch: partials, pass C partials (at most 8192), k coefficients, and
+    // with reorthogonalisation its partials and coefficients (FP64); then V
+    // [k+1][N], SV, W, X (whole grid), U [k+1][p], T (observed) and with
+    // reorthogonalisation the Sigma v_j [k+1][N] as T
     int nds = 0;
-    const size_t nd = 2 * NB + 8192 + (size_t)k + 1;
-    ctx->gk.ensure(nd * sizeof(double) + ((size_t)(k + 4) * N + (size_t)(k + 2) * p) * sizeof(T));
+    const size_t nr = reorth ? (size_t)(k + 1) * (NBR + 1) : 0;
+    const size_t nd = 2 * NB + 8192 + (size_t)k + 1 + nr;
+    ctx->gk.ensure(nd * sizeof(double) +
+                   ((size_t)(k + 4) * N + (size_t)(k + 2) * p + (reorth ? (size_t)(k + 1) * N : 0)) * sizeof(T));
     double* part = ctx->gk.as<double>();
     double* dots = part + 2 * NB;
     double* zdev = dots + 8192;
+    double* rpart = zdev + k + 1;
+    double* rc = rpart + (reorth ? (size_t)(k + 1) * NBR : 0);
     T* V = reinterpret_cast<T*>(part + nd);
     T* SV = V + (size_t)(k + 1) * N;
     T* W = SV + N;
     T* X = W + N;
     T* U = X + N;
     T* Tt = U + (size_t)(k + 1) * p;
+    T* SVh = reorth ? Tt + p : nullptr;
+    // Sigma v_i: the history's slot i with reorthogonalisation, else one buffer
+    auto svp = [&](int i) -> T* { return reorth ? SVh + (size_t)i * N : SV; };
 
     kry_embed* e = make_embed_internal(ctx, &corr, prec);
     try {
@@ -208,12 +277,12 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
         KRY_CUDA(cudaMemsetAsync(W, 0, N * sizeof(T), ctx->stream));
         k_gk_scatter_add<T><<<grid_for(p), 256, 0, ctx->stream>>>(U, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
         KRY_CHECK_LAUNCH();
-        double a2 = sigma_full<T>(ctx, e, W, SV, dots, nds);
+        double a2 = sigma_full<T>(ctx, e, W, svp(0), dots, nds);
         KRY_REQUIRE(a2 > 0.0 && isfinite(a2), KRY_ENAN, "alpha_1 is not positive");
         al[0] = sqrt(a2);
         k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[0], V, N);
         KRY_CHECK_LAUNCH();
-        k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[0], SV, N);
+        k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(svp(0), 1.0 / al[0], svp(0), N);
         KRY_CHECK_LAUNCH();
         // A step whose beta or alpha falls below 1e-13 of the first one ends the bidiagonalization:
         // the Krylov space then holds the solution (an exact breakdown up to rounding), and the
@@ -225,8 +294,10 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
             T* vi = V + (size_t)i * N;
             T* vn = V + (size_t)(i + 1) * N;
             // t = A Sigma v_i - alpha_i u_i, beta_{i+1} = ||t|| / tau, u_{i+1} = t / beta_{i+1}
-            k_gk_gather<T, T, T><<<grid_for(p), 256, 0, ctx->stream>>>(SV, ctx->cellidx.as<int>(), ui, al[i], Tt, p);
+            k_gk_gather<T, T, T><<<grid_for(p), 256, 0, ctx->stream>>>(svp(i), ctx->cellidx.as<int>(), ui, al[i], Tt,
+                                                                      p);
             KRY_CHECK_LAUNCH();
+            if (reorth) project_out<T>(ctx, U, U, p, i + 1, 1.0 / tau2, Tt, p, rpart, rc);
             be[i + 1] = sqrt(sum_sq<T>(ctx, Tt, p, part)) / tau;
             KRY_REQUIRE(isfinite(be[i + 1]), KRY_ENAN, "genGK: beta is NaN/Inf");
             if (!(be[i + 1] > 1e-13 * beta1)) {
@@ -241,7 +312,8 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
             KRY_CHECK_LAUNCH();
             k_gk_scatter_add<T><<<grid_for(p), 256, 0, ctx->stream>>>(un, ctx->cellidx.as<int>(), 1.0 / tau2, W, p);
             KRY_CHECK_LAUNCH();
-            a2 = sigma_full<T>(ctx, e, W, SV, dots, nds);
+            if (reorth) project_out<T>(ctx, SVh, V, N, i + 1, 1.0, W, N, rpart, rc);
+            a2 = sigma_full<T>(ctx, e, W, svp(i + 1), dots, nds);
             KRY_REQUIRE(isfinite(a2), KRY_ENAN, "genGK: alpha is NaN/Inf");
             if (!(a2 > 1e-26 * al[0] * al[0])) {
                 keff = i + 1;
@@ -250,7 +322,7 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
             al[i + 1] = sqrt(a2);
             k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(W, 1.0 / al[i + 1], vn, N);
             KRY_CHECK_LAUNCH();
-            k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(SV, 1.0 / al[i + 1], SV, N);
+            k_scale_copy<T, T><<<grid_for(N), 256, 0, ctx->stream>>>(svp(i + 1), 1.0 / al[i + 1], svp(i + 1), N);
             KRY_CHECK_LAUNCH();
         }
         // projected Tikhonov problem: (B^T B + I / sigma^2) z = B^T beta1 e1, B (k+1) x k lower
@@ -318,12 +390,13 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, double*
 
 }  // namespace
 
-void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, const double* b, int k, double* x_out, double* alphas,
-             double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, bool reorth, const double* b, int k, double* x_out,
+             double* alphas, double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad,
+             double* psi_out) {
     if (prec == KRY_F32)
-        genhybr_t<float>(ctx, cov, b, k, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
+        genhybr_t<float>(ctx, cov, b, k, reorth, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
     else
-        genhybr_t<double>(ctx, cov, b, k, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
+        genhybr_t<double>(ctx, cov, b, k, reorth, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
 }
 
 }  // namespace kry

@@ -96,8 +96,8 @@ SIGNATURES = {
     "kry_launch_count": (C.c_uint64, []),
     "kry_bccb_logdet": (C.c_int, [_P, C.POINTER(kry_cov), _DP, _DP]),
     "kry_genhybr": (C.c_int, [_P, C.POINTER(kry_cov), _P, C.c_int32, _P, _DP, _DP, _DP, _DP, _DP, _DP, _P]),
-    "kry_genhybr_prec": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, _P, C.c_int32, _P, _DP, _DP, _DP, _DP, _DP, _DP,
-                                   _P]),
+    "kry_genhybr_prec": (C.c_int, [_P, C.POINTER(kry_cov), C.c_int, C.c_int32, _P, C.c_int32, _P, _DP, _DP, _DP, _DP,
+                                   _DP, _DP, _P]),
     "kry_bootstrap_var": (C.c_int, [_P, C.POINTER(kry_cov), C.POINTER(kry_opts), C.c_int32, C.c_int32, C.c_int32,
                                     _P, _P, _P, C.c_int64, _P]),
 }
@@ -441,11 +441,12 @@ class Context:
                          allow=(KRY_ENOCONV,))
         return var, st
 
-    def genhybr(self, cov, b, k, want_x=True, gradient=False, prec=KRY_F64):
+    def genhybr(self, cov, b, k, want_x=True, gradient=False, prec=KRY_F64, reorth=0):
         """genHyBR with k genGK steps.  b: (p,) float64 CUDA = y - X beta.  Returns dict(x (n1 x n2
         float64 CUDA or None), alphas, betas (k+1 each), z2, psi2, pl, and with gradient=True
         grad (d pl / d lambda^2, d range, d lambda_e^2) and psi (p,) float64 CUDA).  prec=KRY_F32:
-        FP32 Krylov vectors and matvec, FP64 scalars (kry_genhybr_prec)."""
+        FP32 Krylov vectors and matvec, FP64 scalars; reorth=1: reorthogonalised bidiagonalization
+        (kry_genhybr_prec)."""
         b = b.contiguous()
         x = self.torch.empty((self.n1, self.n2), dtype=self.torch.float64, device=b.device) if want_x else None
         psi = self.torch.empty_like(b) if gradient else None
@@ -453,7 +454,7 @@ class Context:
         al, be = np.zeros(k + 1), np.zeros(k + 1)
         z2, psi2, pl = C.c_double(), C.c_double(), C.c_double()
         pb = _dev((b, F64, self.p, "b"))
-        self._check(_lib.kry_genhybr_prec(self.h, C.byref(make_cov(cov)), prec, pb, k, _ptr(x), _np_dp(al),
+        self._check(_lib.kry_genhybr_prec(self.h, C.byref(make_cov(cov)), prec, reorth, pb, k, _ptr(x), _np_dp(al),
                                           _np_dp(be), C.byref(z2), C.byref(psi2), C.byref(pl), _np_dp(grad),
                                           _ptr(psi)))
         return dict(x=x, alphas=al, betas=be, z2=z2.value, psi2=psi2.value, pl=pl.value, grad=grad, psi=psi)

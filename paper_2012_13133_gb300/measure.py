@@ -61,6 +61,8 @@ def main():
     ap.add_argument("--workload", required=True, choices=["search512", "large4096", "tiny32", "grid1024"])
     ap.add_argument("--bccb", action="store_true", help="time the BCCB log-det and its range derivative")
     ap.add_argument("--genhybr", type=int, default=0, help="time genHyBR (Alg. 1 + Eq. prof_lik) with k steps")
+    ap.add_argument("--gk-prec", default="f64", choices=["f64", "f32"], help="genHyBR vector precision")
+    ap.add_argument("--gk-reorth", action="store_true", help="genHyBR with reorthogonalisation")
     ap.add_argument("--bootstrap", type=int, default=0,
                     help="time the parametric-bootstrap kriging MSE with this many replicates at all missing cells")
     ap.add_argument("--precond", type=int, default=0, help="kry_opts.precond for the CG solves (1: torus inverse)")
@@ -76,9 +78,12 @@ def main():
     out = {"workload": args.workload, "grid": [w.n1, w.n2], "p": p}
     if args.genhybr:
         b = (y - X.T @ torch.tensor(w.beta, device=dev, dtype=torch.float64)).contiguous()
-        ctx.genhybr(w.cov, b, 2)
-        g, t = timed(lambda: ctx.genhybr(w.cov, b, args.genhybr))
-        out.update({"k": args.genhybr, "genhybr_s": t, "pl": g["pl"], "z2": g["z2"], "psi2": g["psi2"]})
+        gp = kry.KRY_F32 if args.gk_prec == "f32" else kry.KRY_F64
+        gr = 1 if args.gk_reorth else 0
+        ctx.genhybr(w.cov, b, 2, prec=gp, reorth=gr)
+        g, t = timed(lambda: ctx.genhybr(w.cov, b, args.genhybr, prec=gp, reorth=gr))
+        out.update({"k": args.genhybr, "prec": args.gk_prec, "reorth": gr, "genhybr_s": t, "pl": g["pl"],
+                    "z2": g["z2"], "psi2": g["psi2"]})
     elif args.variances:
         cells = I.variance_cells(w, mask)[:args.variances]
         Xc = I.covariates(S1.ravel()[cells], S2.ravel()[cells])

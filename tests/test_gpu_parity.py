@@ -597,6 +597,35 @@ def test_genhybr_fp32_matches_oracle(ctx, n1, n2, cov, k, kind):
     assert ei.value.status == kry.KRY_EINVAL
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_genhybr_reorthogonalised_matches_oracle(ctx, prec):
+    """genGK with reorthogonalisation (kry_genhybr_prec, reorth = 1) against the oracle's
+    reorthogonalised Alg. 1 at k = 40 on a 128^2 grid, where the plain recurrence has lost
+    orthogonality: the reorthogonalised recurrence follows the exact bidiagonal, so FP64 agrees to
+    1e-8 and FP32 to its own rounding (1e-4 on the bidiagonal, z, psi and x_k*, 1e-5 on pl)."""
+    n, k = 128, 40
+    cov = I.Cov(1.0, 0.1, 1.5, 0.05)
+    mask = make_mask(n, n, 0.5, "uniform")
+    p = set_mask(ctx, mask)
+    b = I.normals(p, 43)
+    kp = kry.KRY_F64 if prec == "f64" else kry.KRY_F32
+    g = ctx.genhybr(cov, torch.tensor(b, device=DEV), k, prec=kp, reorth=1)
+    ref = O.approx_profile_loglik(n, n, mask, cov, b, k, reorth=True)
+    _, _, _, al, be = O.gengk(n, n, mask, cov, b, k, reorth=True)
+    tol, tol_pl = (1e-8, 1e-10) if prec == "f64" else (1e-4, 1e-5)
+    ra = np.max(np.abs(g["alphas"] - al) / np.abs(al))
+    rb = np.max(np.abs(g["betas"] - be) / np.abs(be))
+    ex = relerr(g["x"].cpu().numpy().ravel(), ref["x"])
+    print(f"reorthogonalised genGK {prec}: alpha {ra:.1e}, beta {rb:.1e}, x {ex:.1e}, pl {abs(g['pl'] / ref['pl'] - 1):.1e}")
+    assert ra <= tol and rb <= tol and ex <= tol
+    assert g["z2"] == pytest.approx(ref["z2"], rel=tol)
+    assert g["psi2"] == pytest.approx(ref["psi2"], rel=tol)
+    assert g["pl"] == pytest.approx(ref["pl"], rel=tol_pl)
+    with pytest.raises(kry.KryError) as ei:
+        ctx.genhybr(cov, torch.tensor(b, device=DEV), k, prec=kp, reorth=2)
+    assert ei.value.status == kry.KRY_EINVAL
+
+
 def test_auto_precision_runs_ill_conditioned_settings_in_fp64(ctx):
     """A likelihood or kriging request with prec = KRY_AUTO runs a covariance setting in FP64 when
     FP32 cannot resolve its conditioning, kappa = (max |Lambda| + tau2) / tau2 > 4e6 (kry_opts): its
