@@ -12,6 +12,7 @@
 #include <set>
 #include <vector>
 
+#include "gengk.cuh"
 #include "kry_internal.cuh"
 
 // Interior share of the mask from which kry_opts.precond = 2 preconditions CG.
@@ -1079,7 +1080,8 @@ kry_status kry_genhybr_prec(kry_ctx* ctx, const kry_cov* cov, kry_prec prec, int
         KRY_REQUIRE(!ctx->sites.active, KRY_EUNSUPPORTED, "genHyBR needs an observation mask (kry_set_mask)");
         KRY_REQUIRE(b_dev != nullptr, KRY_EINVAL, "b_dev must not be NULL");
         KRY_REQUIRE(k >= 1 && k <= 4096, KRY_EINVAL, "k must be in [1, 4096]");
-        kry::genhybr(ctx, *cov, prec, reorth != 0, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad, psi_dev);
+        kry::genhybr_opt(ctx, *cov, prec, reorth != 0, b_dev, k, x_dev, alphas, betas, z2, psi2, pl, grad,
+                         psi_dev);
         return KRY_OK;
     });
 }

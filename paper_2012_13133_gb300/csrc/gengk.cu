@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "gengk.cuh"
 #include "kry_internal.cuh"
 
 namespace kry {
@@ -390,13 +391,18 @@ void genhybr_t(kry_ctx* ctx, const kry_cov& cov, const double* b, int k, bool re
 
 }  // namespace
 
-void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, bool reorth, const double* b, int k, double* x_out,
-             double* alphas, double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad,
-             double* psi_out) {
+void genhybr_opt(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, bool reorth, const double* b, int k, double* x_out,
+                 double* alphas, double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad,
+                 double* psi_out) {
     if (prec == KRY_F32)
         genhybr_t<float>(ctx, cov, b, k, reorth, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
     else
         genhybr_t<double>(ctx, cov, b, k, reorth, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
+}
+
+void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, const double* b, int k, double* x_out, double* alphas,
+             double* betas, double* z2_out, double* psi2_out, double* pl_out, double* grad, double* psi_out) {
+    genhybr_opt(ctx, cov, prec, false, b, k, x_out, alphas, betas, z2_out, psi2_out, pl_out, grad, psi_out);
 }
 
 }  // namespace kry

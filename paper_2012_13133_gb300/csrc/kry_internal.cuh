@@ -279,10 +279,8 @@ void free_embed_internal(kry_embed* e);
 // genHyBR with k genGK steps (Sec. 3.2, Alg. 1; Eq. prof_lik): b = y - X beta on the
 // observed cells; x_out (whole grid, may be NULL), alphas/betas[k+1] (host, may be NULL).
 // prec KRY_F32: FP32 Krylov vectors and matvec, FP64 scalars and reductions.
-// reorth: reorthogonalise each new u against U and v against V (twice).
-void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, bool reorth, const double* b, int k, double* x_out,
-             double* alphas, double* betas, double* z2, double* psi2, double* pl, double* grad = nullptr,
-             double* psi_out = nullptr);
+void genhybr(kry_ctx* ctx, const kry_cov& cov, kry_prec prec, const double* b, int k, double* x_out, double* alphas,
+             double* betas, double* z2, double* psi2, double* pl, double* grad = nullptr, double* psi_out = nullptr);
 
 // BCCB approximation of log det Sigma (no nugget) on the mask's grid and, if
 // deriv, of its range derivative (Sec. 3.3, Appendix A).
